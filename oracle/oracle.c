@@ -1,0 +1,843 @@
+/*
+ * oracle.c -- CPU oracle for the entropy-stable DG Euler solver with buoyancy.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the CPU
+ * baseline of the benchmark; never by the library.  It shares no code with
+ * the CUDA path.
+ *
+ * Everything here follows the method's definition step by step, in the order
+ * of the paper:
+ *   Section 2, Eq. (Eq:euler): conserved variables (rho, rho u, E), pressure
+ *       P = (gamma-1)(E - |U|^2/(2 rho) - rho phi), geopotential phi = g z,
+ *       Coriolis term Omega x U on the left-hand side.
+ *   Section 3, Eq. (nm:semi): dq/dt = h - volume term - surface term on
+ *       tensor-product LGL nodes with collocated quadrature.  The volume term is
+ *       written in the equivalent metric-averaged form
+ *         vol_i = -(1/J_i) sum_d sum_l Dt^{(d)}_{il} H^d(q_i, q_l),
+ *         Dt = 2D - W^{-1}B  (zero diagonal),
+ *       with n = {{Ja^d}}_{il}, and the surface term as
+ *         surf_i = -(s / (J_i w_end)) F*(q-, q+, nhat),  s = |Ja^d|.
+ *       Every ordered node pair (i, l) is evaluated: no symmetry is used.
+ *   Section 4.1: the averages {{a}}, log mean <a>_log = (a+ - a-)/(log a+ - log a-),
+ *       jump [[a]], the momentum flux with p* and the non-symmetric gravity part
+ *       1/2 rho_hat [[phi]], rho_hat = {{b}} <rho>_log / b-, b = rho/(2p).
+ *       The log mean for nearly equal arguments uses the artanh series of the
+ *       efficient formulation the paper adopts.
+ *   Section 3 (last paragraph): Carpenter-Kennedy five-stage fourth-order
+ *       low-storage Runge-Kutta.
+ *   Section 5.1, Eq. (smooth-rb-ic): cosine potential-temperature bubble.
+ *
+ * Readings where the paper points elsewhere (its Eq. 76 and Eq. A.1 citations,
+ * the RK coefficients, the bubble background) are stated next to the code.
+ */
+#include <tgmath.h>
+#include <stdlib.h>
+#include <string.h>
+#include "oracle.h"
+
+#ifndef REAL
+#define REAL double
+#endif
+typedef REAL real;
+
+#define MAXQ 16
+#define NV 5
+
+/* ------------------------------------------------------------------------ */
+/* LGL basis (Section 3: (N+1)^3 tensor-product Legendre-Gauss-Lobatto nodes) */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int N, Nq, np;
+  real xi[MAXQ], w[MAXQ];
+  real D[MAXQ][MAXQ];   /* nodal differentiation matrix */
+  real Dt[MAXQ][MAXQ];  /* 2D - W^{-1} B, zero diagonal */
+} basis_t;
+
+/* Legendre polynomial L_N and L_{N-1} at x by the three-term recurrence. */
+static void legendre_pair(int N, long double x, long double* LN, long double* LNm1) {
+  long double p0 = 1.0L, p1 = x;
+  if (N == 0) { *LN = 1.0L; *LNm1 = 0.0L; return; }
+  for (int k = 1; k < N; k++) {
+    long double p2 = ((2.0L * k + 1.0L) * x * p1 - (long double)k * p0) / (k + 1.0L);
+    p0 = p1;
+    p1 = p2;
+  }
+  *LN = p1;
+  *LNm1 = p0;
+}
+
+/* Nodes: -1, +1 and the roots of L'_N (Newton on L'_N, with L''_N taken from
+ * Legendre's equation); weights 2 / (N (N+1) L_N(x)^2); D from the standard
+ * Lagrange-derivative formula on LGL points. */
+static int build_basis(int N, basis_t* B) {
+  if (N < 1 || N + 1 > MAXQ) return -1;
+  int Nq = N + 1;
+  long double x[MAXQ], LN[MAXQ];
+  const long double pi = 3.141592653589793238462643383279502884L;
+  x[0] = -1.0L;
+  x[N] = 1.0L;
+  for (int k = 1; k < N; k++) {
+    long double t = -cosl(pi * k / N);
+    for (int it = 0; it < 200; it++) {
+      long double L, Lm1;
+      legendre_pair(N, t, &L, &Lm1);
+      long double dL = N * (t * L - Lm1) / (t * t - 1.0L);            /* L'_N */
+      long double d2L = (2.0L * t * dL - N * (N + 1.0L) * L) / (1.0L - t * t); /* L''_N */
+      long double dt = dL / d2L;
+      t -= dt;
+      if (fabsl(dt) < 1e-19L) break;
+    }
+    x[k] = t;
+  }
+  for (int k = 0; k < Nq; k++) {
+    long double Lm1;
+    legendre_pair(N, x[k], &LN[k], &Lm1);
+  }
+  B->N = N;
+  B->Nq = Nq;
+  B->np = Nq * Nq * Nq;
+  for (int i = 0; i < Nq; i++) {
+    B->xi[i] = (real)x[i];
+    B->w[i] = (real)(2.0L / (N * (N + 1.0L) * LN[i] * LN[i]));
+  }
+  for (int i = 0; i < Nq; i++)
+    for (int l = 0; l < Nq; l++) {
+      long double d;
+      if (i != l) d = LN[i] / (LN[l] * (x[i] - x[l]));
+      else if (i == 0) d = -N * (N + 1.0L) / 4.0L;
+      else if (i == N) d = N * (N + 1.0L) / 4.0L;
+      else d = 0.0L;
+      B->D[i][l] = (real)d;
+    }
+  /* Dt = 2D - W^{-1}B with B = diag(-1, 0, ..., 0, 1); its diagonal is zero
+   * exactly (2 D_00 = -N(N+1)/2 = -1/w_0), so it is set to zero. */
+  for (int i = 0; i < Nq; i++)
+    for (int l = 0; l < Nq; l++) B->Dt[i][l] = (i == l) ? (real)0 : 2 * B->D[i][l];
+  return 0;
+}
+
+int or_lgl(int N, double* xi, double* w, double* D, double* Dt) {
+  basis_t B;
+  if (build_basis(N, &B)) return -1;
+  int Nq = B.Nq;
+  for (int i = 0; i < Nq; i++) {
+    if (xi) xi[i] = (double)B.xi[i];
+    if (w) w[i] = (double)B.w[i];
+    for (int l = 0; l < Nq; l++) {
+      if (D) D[i * Nq + l] = (double)B.D[i][l];
+      if (Dt) Dt[i * Nq + l] = (double)B.Dt[i][l];
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Context: mesh, geometry (Kopriva curl-form metrics), physics              */
+/* ------------------------------------------------------------------------ */
+
+struct or_ctx {
+  or_mesh mesh;
+  or_phys phys;
+  basis_t B;
+  int E, np;
+  real* x;   /* [E][3][np] */
+  real* J;   /* [E][np] */
+  real* Ja;  /* [E][3][3][np] */
+};
+
+static int node_i(const basis_t* B, int n, int d) {
+  int Nq = B->Nq;
+  if (d == 0) return n % Nq;
+  if (d == 1) return (n / Nq) % Nq;
+  return n / (Nq * Nq);
+}
+
+static int node_with(const basis_t* B, int n, int d, int m) {
+  int Nq = B->Nq;
+  int ijk[3] = {n % Nq, (n / Nq) % Nq, n / (Nq * Nq)};
+  ijk[d] = m;
+  return ijk[0] + Nq * (ijk[1] + Nq * ijk[2]);
+}
+
+/* derivative of a nodal field along reference direction d using D */
+static void dref(const basis_t* B, int d, const real* f, real* out) {
+  for (int n = 0; n < B->np; n++) {
+    int a = node_i(B, n, d);
+    real s = 0;
+    for (int m = 0; m < B->Nq; m++) s += B->D[a][m] * f[node_with(B, n, d, m)];
+    out[n] = s;
+  }
+}
+
+/* Node positions: uniform box element mapped trilinearly, then the smooth warp
+ *   x += a Lx sin(2 pi y'/Ly) sin(2 pi z'/Lz), y += a Ly sin(2 pi z'/Lz) sin(2 pi x'/Lx),
+ *   z += a Lz sin(2 pi x'/Lx) sin(2 pi y'/Ly),
+ * all three displacements evaluated at the unwarped point (x', y', z' measured
+ * from the box origin). */
+static void element_coords(const or_ctx* c, int e, real* X /* [3][np] */) {
+  const or_mesh* m = &c->mesh;
+  const basis_t* B = &c->B;
+  int K[3] = {m->kx, m->ky, m->kz};
+  int eidx[3] = {e % m->kx, (e / m->kx) % m->ky, e / (m->kx * m->ky)};
+  const real pi = (real)3.141592653589793238462643383279502884L;
+  for (int n = 0; n < B->np; n++) {
+    real r[3], L[3];
+    for (int d = 0; d < 3; d++) {
+      real xi = B->xi[node_i(B, n, d)];
+      L[d] = (real)m->hi[d] - (real)m->lo[d];
+      r[d] = L[d] * ((real)eidx[d] + (1 + xi) / 2) / (real)K[d];  /* offset from lo */
+    }
+    real out[3] = {r[0], r[1], r[2]};
+    if (m->warp != 0.0) {
+      real a = (real)m->warp;
+      real s0 = sin(2 * pi * r[0] / L[0]), s1 = sin(2 * pi * r[1] / L[1]),
+           s2 = sin(2 * pi * r[2] / L[2]);
+      out[0] += a * L[0] * s1 * s2;
+      out[1] += a * L[1] * s2 * s0;
+      out[2] += a * L[2] * s0 * s1;
+    }
+    for (int d = 0; d < 3; d++) X[d * B->np + n] = (real)m->lo[d] + out[d];
+  }
+}
+
+/* Conservative curl-form metric terms (Kopriva 2006):
+ *   Ja^d_n = -xhat_d . curl_xi( X_l grad_xi X_m ),  (n, m, l) cyclic,
+ * and J = X_xi . (X_eta x X_zeta), all derivatives by D. */
+static void element_metrics(const or_ctx* c, const real* X, real* J, real* Ja) {
+  const basis_t* B = &c->B;
+  int np = B->np;
+  real *dX = malloc(sizeof(real) * 9 * np), *V = malloc(sizeof(real) * 3 * np),
+       *t1 = malloc(sizeof(real) * np), *t2 = malloc(sizeof(real) * np);
+  for (int comp = 0; comp < 3; comp++)
+    for (int d = 0; d < 3; d++) dref(B, d, X + comp * np, dX + (comp * 3 + d) * np);
+  /* dX[comp][d] = d X_comp / d xi_d */
+  for (int n = 0; n < np; n++) {
+    real a0 = dX[(0 * 3 + 0) * np + n], a1 = dX[(1 * 3 + 0) * np + n], a2 = dX[(2 * 3 + 0) * np + n];
+    real b0 = dX[(0 * 3 + 1) * np + n], b1 = dX[(1 * 3 + 1) * np + n], b2 = dX[(2 * 3 + 1) * np + n];
+    real c0 = dX[(0 * 3 + 2) * np + n], c1 = dX[(1 * 3 + 2) * np + n], c2 = dX[(2 * 3 + 2) * np + n];
+    J[n] = a0 * (b1 * c2 - b2 * c1) + a1 * (b2 * c0 - b0 * c2) + a2 * (b0 * c1 - b1 * c0);
+  }
+  for (int comp = 0; comp < 3; comp++) {
+    int mm = (comp + 1) % 3, ll = (comp + 2) % 3;
+    for (int d = 0; d < 3; d++)
+      for (int n = 0; n < np; n++) V[d * np + n] = X[ll * np + n] * dX[(mm * 3 + d) * np + n];
+    /* curl components: (d1 V2 - d2 V1, d2 V0 - d0 V2, d0 V1 - d1 V0) */
+    for (int d = 0; d < 3; d++) {
+      int p = (d + 1) % 3, q = (d + 2) % 3;
+      dref(B, p, V + q * np, t1);
+      dref(B, q, V + p * np, t2);
+      for (int n = 0; n < np; n++) Ja[(d * 3 + comp) * np + n] = -(t1[n] - t2[n]);
+    }
+  }
+  free(dX);
+  free(V);
+  free(t1);
+  free(t2);
+}
+
+or_ctx* or_create(const or_mesh* mesh, int N, const or_phys* phys) {
+  or_ctx* c = calloc(1, sizeof(or_ctx));
+  if (!c) return NULL;
+  if (build_basis(N, &c->B)) { free(c); return NULL; }
+  c->mesh = *mesh;
+  c->phys = *phys;
+  c->np = c->B.np;
+  c->E = mesh->kx * mesh->ky * mesh->kz;
+  c->x = malloc(sizeof(real) * (size_t)c->E * 3 * c->np);
+  c->J = malloc(sizeof(real) * (size_t)c->E * c->np);
+  c->Ja = malloc(sizeof(real) * (size_t)c->E * 9 * c->np);
+  for (int e = 0; e < c->E; e++) {
+    element_coords(c, e, c->x + (size_t)e * 3 * c->np);
+    element_metrics(c, c->x + (size_t)e * 3 * c->np, c->J + (size_t)e * c->np,
+                    c->Ja + (size_t)e * 9 * c->np);
+  }
+  return c;
+}
+
+void or_free(or_ctx* c) {
+  if (!c) return;
+  free(c->x);
+  free(c->J);
+  free(c->Ja);
+  free(c);
+}
+
+int or_nelem(const or_ctx* c) { return c->E; }
+
+int or_geometry(const or_ctx* c, double* x, double* J, double* Ja) {
+  size_t np = c->np, E = c->E;
+  for (size_t k = 0; k < E * 3 * np; k++) if (x) x[k] = (double)c->x[k];
+  for (size_t k = 0; k < E * np; k++) if (J) J[k] = (double)c->J[k];
+  for (size_t k = 0; k < E * 9 * np; k++) if (Ja) Ja[k] = (double)c->Ja[k];
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pointwise physics                                                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { real rho, u[3], p, b, phi; } prim_t;
+
+/* Section 2: P = (gamma-1)(E - |U|^2/(2 rho) - rho phi); b = rho/(2p). */
+static prim_t primitives(const real* q, real phi, real gamma) {
+  prim_t s;
+  s.rho = q[0];
+  for (int k = 0; k < 3; k++) s.u[k] = q[1 + k] / q[0];
+  real ke = (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / (2 * q[0]);
+  s.p = (gamma - 1) * (q[4] - ke - q[0] * phi);
+  s.b = s.rho / (2 * s.p);
+  s.phi = phi;
+  return s;
+}
+
+/* Section 4.1: <a>_log = (a+ - a-)/(log a+ - log a-).  For nearly equal
+ * arguments (u = f^2 < 1e-4, f = (a-b)/(a+b)) the quotient is evaluated with the
+ * artanh series log(a/b) = 2 f (1 + u/3 + u^2/5 + ...), i.e.
+ *   <a>_log = (a+b) / (2 + 2u/3 + 2u^2/5 + 2u^3/7 + ...),
+ * truncated where the next term is below the working precision. */
+static real logmean(real a, real b) {
+  real f = (a - b) / (a + b);
+  real u = f * f;
+  if (u < (real)1e-4) {
+    int K = (sizeof(real) > sizeof(double)) ? 6 : 4;  /* terms u^0 .. u^(K-1) */
+    real s = 0;
+    for (int k = K - 1; k >= 0; k--) s = s * u + (real)2 / (real)(2 * k + 1);
+    return (a + b) / s;
+  }
+  return (a - b) / (log(a) - log(b));
+}
+
+double or_logmean(double a, double b) { return (double)logmean((real)a, (real)b); }
+
+/* Entropy variables for eta = -rho s/(gamma-1), s = ln p - gamma ln rho, with the
+ * geopotential inside E:  v = ((gamma - s)/(gamma-1) - b|u|^2 + 2 b phi, 2 b u, -2 b). */
+static void entropy_vars(const real* q, real phi, real gamma, real* v) {
+  prim_t s = primitives(q, phi, gamma);
+  real ent = log(s.p) - gamma * log(s.rho);
+  real u2 = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
+  v[0] = (gamma - ent) / (gamma - 1) - s.b * u2 + 2 * s.b * phi;
+  for (int k = 0; k < 3; k++) v[1 + k] = 2 * s.b * s.u[k];
+  v[4] = -2 * s.b;
+}
+
+/* Two-point entropy-conservative flux in direction n (Section 4.1 and the
+ * Eq. 76 it cites).  Reading used here (the Chandrashekar-type flux in
+ * b = rho/(2p), whose momentum part the paper prints):
+ *   F^rho = <rho>_log u_n,                u_n = {{u}} . n
+ *   F^m   = F^rho {{u}} + p* n,           p* = {{rho}} / (2 {{b}})
+ *   F^E   = F^rho (1/(2 (gamma-1) <b>_log) + u- . u+ / 2 + {{phi}}) + p* u_n
+ * and the non-symmetric gravity part for the node on the "-" side,
+ *   G = 1/2 rho_hat [[phi]] n,  rho_hat = {{b}} <rho>_log / b-.
+ * "-" is node a (the node being updated), "+" is node b. */
+static void ec_flux(const prim_t* A, const prim_t* Bp, const real* n, real gamma, real* F,
+                    real* G) {
+  real rho_log = logmean(A->rho, Bp->rho);
+  real b_log = logmean(A->b, Bp->b);
+  real ubar[3], un = 0, uu = 0;
+  for (int k = 0; k < 3; k++) {
+    ubar[k] = (A->u[k] + Bp->u[k]) / 2;
+    un += ubar[k] * n[k];
+    uu += A->u[k] * Bp->u[k];
+  }
+  real rho_avg = (A->rho + Bp->rho) / 2, b_avg = (A->b + Bp->b) / 2;
+  real pstar = rho_avg / (2 * b_avg);
+  real phi_avg = (A->phi + Bp->phi) / 2;
+  F[0] = rho_log * un;
+  for (int k = 0; k < 3; k++) F[1 + k] = F[0] * ubar[k] + pstar * n[k];
+  F[4] = F[0] * (1 / (2 * (gamma - 1) * b_log) + uu / 2 + phi_avg) + pstar * un;
+  real rho_hat = b_avg * rho_log / A->b;
+  real g = rho_hat * (Bp->phi - A->phi) / 2;
+  for (int k = 0; k < 3; k++) G[k] = g * n[k];
+}
+
+void or_entropy_vars(const double* q, double phi, double gamma, double* v) {
+  real qq[NV], vv[NV];
+  for (int k = 0; k < NV; k++) qq[k] = (real)q[k];
+  entropy_vars(qq, (real)phi, (real)gamma, vv);
+  for (int k = 0; k < NV; k++) v[k] = (double)vv[k];
+}
+
+void or_ec_flux(const double* qa, double phia, const double* qb, double phib, const double* n,
+                double gamma, double* F, double* G) {
+  real qa_[NV], qb_[NV], n_[3], F_[NV], G_[3];
+  for (int k = 0; k < NV; k++) { qa_[k] = (real)qa[k]; qb_[k] = (real)qb[k]; }
+  for (int k = 0; k < 3; k++) n_[k] = (real)n[k];
+  prim_t A = primitives(qa_, (real)phia, (real)gamma);
+  prim_t B = primitives(qb_, (real)phib, (real)gamma);
+  ec_flux(&A, &B, n_, (real)gamma, F_, G_);
+  for (int k = 0; k < NV; k++) F[k] = (double)F_[k];
+  for (int k = 0; k < 3; k++) G[k] = (double)G_[k];
+}
+
+/* Matrix dissipation (the paper's Eq. A.1 citation; Roe-like diagonalisation).
+ * Reading used here: D = R |Lambda| T R^T built at the averaged state
+ *   rho_hat = <rho>_log, u = {{u}}, p_hat = {{rho}}/(2{{b}}), a = sqrt(gamma p_hat/rho_hat),
+ *   H = a^2/(gamma-1) + |u|^2/2 + phi,
+ * with right eigenvectors of the normal flux Jacobian
+ *   r1 = (1, u - a n, H - a u_n), r2 = (1, u, |u|^2/2 + phi), r3,4 = (0, t_k, u . t_k),
+ *   r5 = (1, u + a n, H + a u_n),
+ * eigenvalues (u_n - a, u_n, u_n, u_n, u_n + a) and the entropy scaling
+ *   T = diag(rho/(2 gamma), rho (gamma-1)/gamma, p, p, rho/(2 gamma)),
+ * for which R T R^T = dq/dv.  t_1, t_2 complete nhat to an orthonormal basis. */
+static void eigensystem(const prim_t* M, const prim_t* P, real phi, const real* nh, real gamma,
+                        real R[NV][NV], real* lam, real* T) {
+  real rho_hat = logmean(M->rho, P->rho);
+  real u[3], un = 0, u2 = 0;
+  for (int k = 0; k < 3; k++) {
+    u[k] = (M->u[k] + P->u[k]) / 2;
+    un += u[k] * nh[k];
+    u2 += u[k] * u[k];
+  }
+  real p_hat = ((M->rho + P->rho) / 2) / (2 * ((M->b + P->b) / 2));
+  real a = sqrt(gamma * p_hat / rho_hat);
+  real H = a * a / (gamma - 1) + u2 / 2 + phi;
+  /* tangents */
+  int imin = 0;
+  for (int k = 1; k < 3; k++) if (fabs(nh[k]) < fabs(nh[imin])) imin = k;
+  real e[3] = {0, 0, 0};
+  e[imin] = 1;
+  real t1[3] = {e[1] * nh[2] - e[2] * nh[1], e[2] * nh[0] - e[0] * nh[2], e[0] * nh[1] - e[1] * nh[0]};
+  real tn = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+  for (int k = 0; k < 3; k++) t1[k] /= tn;
+  real t2[3] = {nh[1] * t1[2] - nh[2] * t1[1], nh[2] * t1[0] - nh[0] * t1[2], nh[0] * t1[1] - nh[1] * t1[0]};
+  real ut1 = u[0] * t1[0] + u[1] * t1[1] + u[2] * t1[2];
+  real ut2 = u[0] * t2[0] + u[1] * t2[1] + u[2] * t2[2];
+  /* columns of R */
+  real col[NV][NV] = {
+      {1, u[0] - a * nh[0], u[1] - a * nh[1], u[2] - a * nh[2], H - a * un},
+      {1, u[0], u[1], u[2], u2 / 2 + phi},
+      {0, t1[0], t1[1], t1[2], ut1},
+      {0, t2[0], t2[1], t2[2], ut2},
+      {1, u[0] + a * nh[0], u[1] + a * nh[1], u[2] + a * nh[2], H + a * un}};
+  for (int r = 0; r < NV; r++)
+    for (int k = 0; k < NV; k++) R[r][k] = col[k][r];
+  lam[0] = un - a;
+  lam[1] = lam[2] = lam[3] = un;
+  lam[4] = un + a;
+  T[0] = T[4] = rho_hat / (2 * gamma);
+  T[1] = rho_hat * (gamma - 1) / gamma;
+  T[2] = T[3] = p_hat;
+}
+
+static void dissipation_matrix(const prim_t* M, const prim_t* P, real phi, const real* nh,
+                               real gamma, real Dm[NV][NV]) {
+  real R[NV][NV], lam[NV], T[NV];
+  eigensystem(M, P, phi, nh, gamma, R, lam, T);
+  for (int r = 0; r < NV; r++)
+    for (int c = 0; c < NV; c++) {
+      real s = 0;
+      for (int k = 0; k < NV; k++) s += R[r][k] * fabs(lam[k]) * T[k] * R[c][k];
+      Dm[r][c] = s;
+    }
+}
+
+/* Interface flux F* = F#(q-, q+; nhat) - 1/2 D [[v]]  (Section 3: "the same
+ * entropy-conserving flux in addition to the matrix dissipation").  phi is
+ * continuous across a face, so the gravity part vanishes there. */
+static void es_flux(const real* qm, const real* qp, real phi, const real* nh, real gamma,
+                    int dissipation, real* Fs) {
+  prim_t M = primitives(qm, phi, gamma), P = primitives(qp, phi, gamma);
+  real G[3];
+  ec_flux(&M, &P, nh, gamma, Fs, G);
+  for (int k = 0; k < 3; k++) Fs[1 + k] += G[k];
+  if (!dissipation) return;
+  real vm[NV], vp[NV], jv[NV], Dm[NV][NV];
+  entropy_vars(qm, phi, gamma, vm);
+  entropy_vars(qp, phi, gamma, vp);
+  for (int k = 0; k < NV; k++) jv[k] = vp[k] - vm[k];
+  dissipation_matrix(&M, &P, phi, nh, gamma, Dm);
+  for (int r = 0; r < NV; r++) {
+    real s = 0;
+    for (int c = 0; c < NV; c++) s += Dm[r][c] * jv[c];
+    Fs[r] -= s / 2;
+  }
+}
+
+void or_es_flux(const double* qm, const double* qp, double phi, const double* nhat, double gamma,
+                int dissipation, double* Fstar) {
+  real a[NV], b[NV], n[3], F[NV];
+  for (int k = 0; k < NV; k++) { a[k] = (real)qm[k]; b[k] = (real)qp[k]; }
+  for (int k = 0; k < 3; k++) n[k] = (real)nhat[k];
+  es_flux(a, b, (real)phi, n, (real)gamma, dissipation, F);
+  for (int k = 0; k < NV; k++) Fstar[k] = (double)F[k];
+}
+
+void or_dissipation_matrix(const double* qm, const double* qp, double phi, const double* nhat,
+                           double gamma, double* Dmat) {
+  real a[NV], b[NV], n[3], Dm[NV][NV];
+  for (int k = 0; k < NV; k++) { a[k] = (real)qm[k]; b[k] = (real)qp[k]; }
+  for (int k = 0; k < 3; k++) n[k] = (real)nhat[k];
+  prim_t M = primitives(a, (real)phi, (real)gamma), P = primitives(b, (real)phi, (real)gamma);
+  dissipation_matrix(&M, &P, (real)phi, n, (real)gamma, Dm);
+  for (int r = 0; r < NV; r++)
+    for (int c = 0; c < NV; c++) Dmat[r * NV + c] = (double)Dm[r][c];
+}
+
+void or_eigensystem(const double* qm, const double* qp, double phi, const double* nhat,
+                    double gamma, double* R, double* lam, double* T) {
+  real a[NV], b[NV], n[3], R_[NV][NV], l_[NV], T_[NV];
+  for (int k = 0; k < NV; k++) { a[k] = (real)qm[k]; b[k] = (real)qp[k]; }
+  for (int k = 0; k < 3; k++) n[k] = (real)nhat[k];
+  prim_t M = primitives(a, (real)phi, (real)gamma), P = primitives(b, (real)phi, (real)gamma);
+  eigensystem(&M, &P, (real)phi, n, (real)gamma, R_, l_, T_);
+  for (int r = 0; r < NV; r++) {
+    lam[r] = (double)l_[r];
+    T[r] = (double)T_[r];
+    for (int c = 0; c < NV; c++) R[r * NV + c] = (double)R_[r][c];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Semi-discrete right-hand side, Eq. (nm:semi)                              */
+/* ------------------------------------------------------------------------ */
+
+static real node_phi(const or_ctx* c, int e, int n) {
+  return (real)c->phys.g * c->x[((size_t)e * 3 + 2) * c->np + n];
+}
+
+/* neighbour across face (d, side) of element e; -1 at a wall */
+static int neighbour(const or_ctx* c, int e, int d, int side) {
+  const or_mesh* m = &c->mesh;
+  int K[3] = {m->kx, m->ky, m->kz};
+  int idx[3] = {e % m->kx, (e / m->kx) % m->ky, e / (m->kx * m->ky)};
+  idx[d] += side ? 1 : -1;
+  if (idx[d] < 0 || idx[d] >= K[d]) {
+    if (!m->periodic[d]) return -1;
+    idx[d] = (idx[d] + K[d]) % K[d];
+  }
+  return idx[0] + m->kx * (idx[1] + m->ky * idx[2]);
+}
+
+int or_rhs_parts(const or_ctx* c, const double* qd, double* vol_out, double* surf_out,
+                 double* src_out) {
+  const basis_t* B = &c->B;
+  int np = c->np, Nq = B->Nq, N = B->N;
+  real gamma = (real)c->phys.gamma;
+  size_t tot = (size_t)c->E * NV * np;
+  real* q = malloc(sizeof(real) * tot);
+  for (size_t k = 0; k < tot; k++) q[k] = (real)qd[k];
+  real* vol = calloc(tot, sizeof(real));
+  real* surf = calloc(tot, sizeof(real));
+  real* src = calloc(tot, sizeof(real));
+  prim_t* pr = malloc(sizeof(prim_t) * (size_t)c->E * np);
+  for (int e = 0; e < c->E; e++)
+    for (int n = 0; n < np; n++) {
+      real qn[NV];
+      for (int v = 0; v < NV; v++) qn[v] = q[((size_t)e * NV + v) * np + n];
+      pr[(size_t)e * np + n] = primitives(qn, node_phi(c, e, n), gamma);
+    }
+
+  for (int e = 0; e < c->E; e++) {
+    const real* Ja = c->Ja + (size_t)e * 9 * np;
+    const real* J = c->J + (size_t)e * np;
+    /* volume term: every ordered pair (i, l) along each reference direction */
+    for (int i = 0; i < np; i++) {
+      real acc[NV] = {0, 0, 0, 0, 0};
+      for (int d = 0; d < 3; d++) {
+        int a = node_i(B, i, d);
+        for (int m = 0; m < Nq; m++) {
+          if (m == a) continue;
+          int l = node_with(B, i, d, m);
+          real n[3], F[NV], G[3];
+          for (int k = 0; k < 3; k++) n[k] = (Ja[(d * 3 + k) * np + i] + Ja[(d * 3 + k) * np + l]) / 2;
+          ec_flux(&pr[(size_t)e * np + i], &pr[(size_t)e * np + l], n, gamma, F, G);
+          for (int k = 0; k < 3; k++) F[1 + k] += G[k];
+          for (int v = 0; v < NV; v++) acc[v] += B->Dt[a][m] * F[v];
+        }
+      }
+      for (int v = 0; v < NV; v++) vol[((size_t)e * NV + v) * np + i] = -acc[v] / J[i];
+    }
+    /* surface term: faces of this element, own metric, neighbour or mirror state */
+    for (int d = 0; d < 3; d++)
+      for (int side = 0; side < 2; side++) {
+        int nb = neighbour(c, e, d, side);
+        int own_end = side ? N : 0, nb_end = side ? 0 : N;
+        for (int i = 0; i < np; i++) {
+          if (node_i(B, i, d) != own_end) continue;
+          real jn[3], s = 0;
+          for (int k = 0; k < 3; k++) {
+            jn[k] = Ja[(d * 3 + k) * np + i];
+            s += jn[k] * jn[k];
+          }
+          s = sqrt(s);
+          real nh[3];
+          for (int k = 0; k < 3; k++) nh[k] = (side ? 1 : -1) * jn[k] / s;
+          real qm[NV], qp[NV];
+          for (int v = 0; v < NV; v++) qm[v] = q[((size_t)e * NV + v) * np + i];
+          if (nb >= 0) {
+            int l = node_with(B, i, d, nb_end);
+            for (int v = 0; v < NV; v++) qp[v] = q[((size_t)nb * NV + v) * np + l];
+          } else {
+            /* reflecting wall: mirror state (rho, U - 2 (U . nhat) nhat, E) */
+            real Un = qm[1] * nh[0] + qm[2] * nh[1] + qm[3] * nh[2];
+            qp[0] = qm[0];
+            for (int k = 0; k < 3; k++) qp[1 + k] = qm[1 + k] - 2 * Un * nh[k];
+            qp[4] = qm[4];
+          }
+          real Fs[NV];
+          es_flux(qm, qp, node_phi(c, e, i), nh, gamma, c->phys.dissipation, Fs);
+          for (int v = 0; v < NV; v++)
+            surf[((size_t)e * NV + v) * np + i] -= s / (J[i] * B->w[own_end]) * Fs[v];
+        }
+      }
+    /* source h: Coriolis -f zhat x U with f = f0 + beta (y - y0) */
+    for (int i = 0; i < np; i++) {
+      real y = c->x[((size_t)e * 3 + 1) * np + i];
+      real f = (real)c->phys.f0 + (real)c->phys.beta * (y - (real)c->phys.y0);
+      src[((size_t)e * NV + 1) * np + i] = f * q[((size_t)e * NV + 2) * np + i];
+      src[((size_t)e * NV + 2) * np + i] = -f * q[((size_t)e * NV + 1) * np + i];
+    }
+  }
+  for (size_t k = 0; k < tot; k++) {
+    if (vol_out) vol_out[k] = (double)vol[k];
+    if (surf_out) surf_out[k] = (double)surf[k];
+    if (src_out) src_out[k] = (double)src[k];
+  }
+  free(q);
+  free(vol);
+  free(surf);
+  free(src);
+  free(pr);
+  return 0;
+}
+
+int or_rhs(const or_ctx* c, const double* qd, double* rhs) {
+  size_t tot = (size_t)c->E * NV * c->np;
+  double* v = malloc(sizeof(double) * tot);
+  double* s = malloc(sizeof(double) * tot);
+  double* h = malloc(sizeof(double) * tot);
+  or_rhs_parts(c, qd, v, s, h);
+  /* sum in the working precision of the build */
+  for (size_t k = 0; k < tot; k++) rhs[k] = (double)((real)v[k] + (real)s[k] + (real)h[k]);
+  free(v);
+  free(s);
+  free(h);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Time stepping: Carpenter & Kennedy (1994) 5-stage 4th-order 2N-storage RK  */
+/* ------------------------------------------------------------------------ */
+
+static const long double LSRK_A[5] = {0.0L, -567301805773.0L / 1357537059087.0L,
+                                      -2404267990393.0L / 2016746695238.0L,
+                                      -3550918686646.0L / 2091501179385.0L,
+                                      -1275806237668.0L / 842570457699.0L};
+static const long double LSRK_B[5] = {
+    1432997174477.0L / 9575080441755.0L, 5161836677717.0L / 13612068292357.0L,
+    1720146321549.0L / 2090206949498.0L, 3134564353537.0L / 4481467310338.0L,
+    2277821191437.0L / 14882151754819.0L};
+static const long double LSRK_C[5] = {0.0L, 1432997174477.0L / 9575080441755.0L,
+                                      2526269341429.0L / 6820363962896.0L,
+                                      2006345519317.0L / 3224310063776.0L,
+                                      2802321613138.0L / 2924317926251.0L};
+
+void or_lsrk_coeffs(double* A, double* B, double* c) {
+  for (int s = 0; s < 5; s++) {
+    if (A) A[s] = (double)LSRK_A[s];
+    if (B) B[s] = (double)LSRK_B[s];
+    if (c) c[s] = (double)LSRK_C[s];
+  }
+}
+
+/* dq <- A_s dq + dt rhs(q);  q <- q + B_s dq, s = 1..5.  With REAL = long double
+ * the state is carried in long double across all steps. */
+int or_lsrk_steps(const or_ctx* c, double* qd, double dt, int nsteps) {
+  size_t tot = (size_t)c->E * NV * c->np;
+  real* q = malloc(sizeof(real) * tot);
+  real* dq = calloc(tot, sizeof(real));
+  double* qs = malloc(sizeof(double) * tot);
+  double *v = malloc(sizeof(double) * tot), *s = malloc(sizeof(double) * tot),
+         *h = malloc(sizeof(double) * tot);
+  for (size_t k = 0; k < tot; k++) q[k] = (real)qd[k];
+  for (int step = 0; step < nsteps; step++)
+    for (int st = 0; st < 5; st++) {
+      for (size_t k = 0; k < tot; k++) qs[k] = (double)q[k];
+      or_rhs_parts(c, qs, v, s, h);
+      for (size_t k = 0; k < tot; k++) {
+        real r = (real)v[k] + (real)s[k] + (real)h[k];
+        dq[k] = (real)LSRK_A[st] * dq[k] + (real)dt * r;
+        q[k] = q[k] + (real)LSRK_B[st] * dq[k];
+      }
+    }
+  for (size_t k = 0; k < tot; k++) qd[k] = (double)q[k];
+  free(q);
+  free(dq);
+  free(qs);
+  free(v);
+  free(s);
+  free(h);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial states                                                            */
+/* ------------------------------------------------------------------------ */
+
+static real cp_of(const or_phys* p) { return (real)p->gamma * (real)p->R / ((real)p->gamma - 1); }
+
+/* Section 5.1, Eq. (smooth-rb-ic): theta = theta0 + amp (1 + cos(pi r/rc))/2 for
+ * r <= rc, over an isentropic (constant theta0) hydrostatic background:
+ *   Exner pi = 1 - g z/(cp theta0), p = p0 pi^(cp/R), T = theta pi, rho = p/(R T),
+ *   u = 0, E = p/(gamma-1) + rho g z.
+ * The pressure is left unperturbed (the background reading of the bubble). */
+int or_init_bubble(const or_ctx* c, double theta0, double amp, const double* centre,
+                   double radius, double* q) {
+  const or_phys* ph = &c->phys;
+  real cp = cp_of(ph), R = (real)ph->R, g = (real)ph->g, gamma = (real)ph->gamma;
+  const real pi = (real)3.141592653589793238462643383279502884L;
+  int np = c->np;
+  for (int e = 0; e < c->E; e++)
+    for (int n = 0; n < np; n++) {
+      real X[3];
+      for (int d = 0; d < 3; d++) X[d] = c->x[((size_t)e * 3 + d) * np + n];
+      real r2 = 0;
+      for (int d = 0; d < 3; d++) r2 += (X[d] - (real)centre[d]) * (X[d] - (real)centre[d]);
+      real r = sqrt(r2);
+      real dth = (r <= (real)radius) ? (real)amp * (1 + cos(pi * r / (real)radius)) / 2 : 0;
+      real ex = 1 - g * X[2] / (cp * (real)theta0);
+      real p = (real)ph->p0 * pow(ex, cp / R);
+      real T = ((real)theta0 + dth) * ex;
+      real rho = p / (R * T);
+      q[((size_t)e * NV + 0) * np + n] = (double)rho;
+      q[((size_t)e * NV + 1) * np + n] = 0;
+      q[((size_t)e * NV + 2) * np + n] = 0;
+      q[((size_t)e * NV + 3) * np + n] = 0;
+      q[((size_t)e * NV + 4) * np + n] = (double)(p / (gamma - 1) + rho * g * X[2]);
+    }
+  return 0;
+}
+
+/* Isothermal rest state: rho = rho_s exp(-g z/(R T)), p = rho R T, u = 0. */
+int or_init_isothermal(const or_ctx* c, double T, double rho_surface, double* q) {
+  const or_phys* ph = &c->phys;
+  real R = (real)ph->R, g = (real)ph->g, gamma = (real)ph->gamma;
+  int np = c->np;
+  for (int e = 0; e < c->E; e++)
+    for (int n = 0; n < np; n++) {
+      real z = c->x[((size_t)e * 3 + 2) * np + n];
+      real rho = (real)rho_surface * exp(-g * z / (R * (real)T));
+      real p = rho * R * (real)T;
+      q[((size_t)e * NV + 0) * np + n] = (double)rho;
+      for (int k = 1; k < 4; k++) q[((size_t)e * NV + k) * np + n] = 0;
+      q[((size_t)e * NV + 4) * np + n] = (double)(p / (gamma - 1) + rho * g * z);
+    }
+  return 0;
+}
+
+/* Synthetic stand-in for the baroclinic channel (the benchmark's own balanced
+ * jet formulas are not reproduced here).  Isothermal columns with a scale height
+ * that steps across the channel,
+ *   ln p = ln p0 - z / H(y),  H(y) = H0 + dH (1 - tanh((y - yc)/delta))/2,
+ * hydrostatic rho = p/(g H), geostrophic u = -(dp/dy)/(f rho) = -g z H'(y)/(f H),
+ * plus a Gaussian zonal-wind perturbation of 1 m/s. */
+int or_init_channel(const or_ctx* c, double* q) {
+  const or_phys* ph = &c->phys;
+  real g = (real)ph->g, gamma = (real)ph->gamma;
+  const real H0 = 7500, dH = 120, delta = 600e3, yc = 3000e3;
+  const real xp = 2000e3, yp = 2500e3, Lp = 600e3, up = 1;
+  int np = c->np;
+  for (int e = 0; e < c->E; e++)
+    for (int n = 0; n < np; n++) {
+      real X = c->x[((size_t)e * 3 + 0) * np + n];
+      real Y = c->x[((size_t)e * 3 + 1) * np + n];
+      real Z = c->x[((size_t)e * 3 + 2) * np + n];
+      real th = tanh((Y - yc) / delta);
+      real H = H0 + dH * (1 - th) / 2;
+      real dHdy = -dH * (1 - th * th) / (2 * delta);
+      real f = (real)ph->f0 + (real)ph->beta * (Y - (real)ph->y0);
+      real p = (real)ph->p0 * exp(-Z / H);
+      real rho = p / (g * H);
+      real u = -g * Z * dHdy / (f * H);
+      u += up * exp(-((X - xp) * (X - xp) + (Y - yp) * (Y - yp)) / (Lp * Lp));
+      q[((size_t)e * NV + 0) * np + n] = (double)rho;
+      q[((size_t)e * NV + 1) * np + n] = (double)(rho * u);
+      q[((size_t)e * NV + 2) * np + n] = 0;
+      q[((size_t)e * NV + 3) * np + n] = 0;
+      q[((size_t)e * NV + 4) * np + n] = (double)(p / (gamma - 1) + rho * u * u / 2 + rho * g * Z);
+    }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+
+static real quad_weight(const basis_t* B, int n) {
+  return B->w[node_i(B, n, 0)] * B->w[node_i(B, n, 1)] * B->w[node_i(B, n, 2)];
+}
+
+/* sum_K int_K rho dV, sum_K int_K E dV, and the entropy sum_K int_K eta dV with
+ * eta = -rho s/(gamma-1) (the conservation monitors of Section 5.2). */
+int or_integrals(const or_ctx* c, const double* q, double* out3) {
+  real m = 0, en = 0, ent = 0, gamma = (real)c->phys.gamma;
+  int np = c->np;
+  for (int e = 0; e < c->E; e++)
+    for (int n = 0; n < np; n++) {
+      real qn[NV];
+      for (int v = 0; v < NV; v++) qn[v] = (real)q[((size_t)e * NV + v) * np + n];
+      real wJ = quad_weight(&c->B, n) * c->J[(size_t)e * np + n];
+      prim_t s = primitives(qn, node_phi(c, e, n), gamma);
+      m += wJ * qn[0];
+      en += wJ * qn[4];
+      ent += wJ * (-qn[0] * (log(s.p) - gamma * log(s.rho)) / (gamma - 1));
+    }
+  out3[0] = (double)m;
+  out3[1] = (double)en;
+  out3[2] = (double)ent;
+  return 0;
+}
+
+/* dS/dt = sum_e sum_i J_i w_i v_i . rhs_i */
+double or_entropy_rate(const or_ctx* c, const double* q, const double* rhs) {
+  real s = 0, gamma = (real)c->phys.gamma;
+  int np = c->np;
+  for (int e = 0; e < c->E; e++)
+    for (int n = 0; n < np; n++) {
+      real qn[NV], v[NV];
+      for (int k = 0; k < NV; k++) qn[k] = (real)q[((size_t)e * NV + k) * np + n];
+      entropy_vars(qn, node_phi(c, e, n), gamma, v);
+      real wJ = quad_weight(&c->B, n) * c->J[(size_t)e * np + n];
+      for (int k = 0; k < NV; k++) s += wJ * v[k] * (real)rhs[((size_t)e * NV + k) * np + n];
+    }
+  return (double)s;
+}
+
+/* Time step: dt = C min over elements and nodes of dmin_e / (|u| + c), with
+ * dmin_e the element's shortest corner-to-corner edge times (xi_1 - xi_0)/2. */
+double or_cfl_dt(const or_ctx* c, const double* q, double C) {
+  const basis_t* B = &c->B;
+  int np = c->np, N = B->N;
+  real gamma = (real)c->phys.gamma, best = -1;
+  real frac = (B->xi[1] - B->xi[0]) / 2;
+  for (int e = 0; e < c->E; e++) {
+    const real* X = c->x + (size_t)e * 3 * np;
+    real hmin = -1;
+    for (int d = 0; d < 3; d++)
+      for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) {
+          int ij0[3], ij1[3];
+          int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+          ij0[d] = 0;
+          ij1[d] = N;
+          ij0[o1] = ij1[o1] = a * N;
+          ij0[o2] = ij1[o2] = b * N;
+          int n0 = ij0[0] + B->Nq * (ij0[1] + B->Nq * ij0[2]);
+          int n1 = ij1[0] + B->Nq * (ij1[1] + B->Nq * ij1[2]);
+          real l2 = 0;
+          for (int k = 0; k < 3; k++) l2 += (X[k * np + n1] - X[k * np + n0]) * (X[k * np + n1] - X[k * np + n0]);
+          real len = sqrt(l2);
+          if (hmin < 0 || len < hmin) hmin = len;
+        }
+    for (int n = 0; n < np; n++) {
+      real qn[NV];
+      for (int v = 0; v < NV; v++) qn[v] = (real)q[((size_t)e * NV + v) * np + n];
+      prim_t s = primitives(qn, node_phi(c, e, n), gamma);
+      real sp = sqrt(s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]) + sqrt(gamma * s.p / s.rho);
+      real cand = hmin * frac / sp;
+      if (best < 0 || cand < best) best = cand;
+    }
+  }
+  return (double)((real)C * best);
+}
