@@ -48,6 +48,7 @@ def _lib(precision: str = "double"):
                 getattr(lib, fn).argtypes = [C.c_void_p, _D, _D, _D]
             lib.or_rhs.argtypes = [C.c_void_p, _D, _D]
             lib.or_rhs_parts.argtypes = [C.c_void_p, _D, _D, _D, _D]
+            lib.or_rhs_scale.argtypes = [C.c_void_p, _D, _D]
             lib.or_lsrk_coeffs.argtypes = [_D, _D, _D]
             lib.or_lsrk_steps.argtypes = [C.c_void_p, _D, C.c_double, C.c_int]
             lib.or_init_bubble.argtypes = [C.c_void_p, C.c_double, C.c_double, _D, C.c_double, _D]
@@ -188,6 +189,13 @@ class Oracle:
         v, s, h = (np.zeros(self.shape()) for _ in range(3))
         self.lib.or_rhs_parts(self._h, _p(q), _p(v), _p(s), _p(h))
         return v, s, h
+
+    def rhs_scale(self, q):
+        """Per-node magnitude of the cancelling terms (see or_rhs_scale)."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        out = np.zeros(self.shape())
+        self.lib.or_rhs_scale(self._h, _p(q), _p(out))
+        return out
 
     def steps(self, q, dt, nsteps):
         q = np.array(q, dtype=np.float64, order="C", copy=True)

@@ -218,10 +218,15 @@ static void element_metrics(const or_ctx* c, const real* X, real* J, real* Ja) {
     real c0 = dX[(0 * 3 + 2) * np + n], c1 = dX[(1 * 3 + 2) * np + n], c2 = dX[(2 * 3 + 2) * np + n];
     J[n] = a0 * (b1 * c2 - b2 * c1) + a1 * (b2 * c0 - b0 * c2) + a2 * (b0 * c1 - b1 * c0);
   }
+  /* X_l grad X_m is formed with X_l measured from the element's first node:
+   * curl(c grad X_m) = 0 exactly for a constant c (the tensor-product derivative
+   * matrices commute), so the metric is unchanged while the round-off no longer
+   * grows with the distance from the coordinate origin. */
   for (int comp = 0; comp < 3; comp++) {
     int mm = (comp + 1) % 3, ll = (comp + 2) % 3;
+    real x0 = X[ll * np];
     for (int d = 0; d < 3; d++)
-      for (int n = 0; n < np; n++) V[d * np + n] = X[ll * np + n] * dX[(mm * 3 + d) * np + n];
+      for (int n = 0; n < np; n++) V[d * np + n] = (X[ll * np + n] - x0) * dX[(mm * 3 + d) * np + n];
     /* curl components: (d1 V2 - d2 V1, d2 V0 - d0 V2, d0 V1 - d1 V0) */
     for (int d = 0; d < 3; d++) {
       int p = (d + 1) % 3, q = (d + 2) % 3;
@@ -598,6 +603,62 @@ int or_rhs_parts(const or_ctx* c, const double* qd, double* vol_out, double* sur
   free(vol);
   free(surf);
   free(src);
+  free(pr);
+  return 0;
+}
+
+/* Magnitude of the terms that cancel in the right-hand side:
+ *   scale_i = (1/J_i) [ sum_d sum_l |Dt_il| |H^d(q_i, q_l)| + sum_faces s/w |F*| ],
+ * componentwise.  A round-off floor for comparing two FP64 evaluations of the
+ * RHS is a small multiple of 1e-16 times this. */
+int or_rhs_scale(const or_ctx* c, const double* qd, double* out) {
+  const basis_t* B = &c->B;
+  int np = c->np, Nq = B->Nq, N = B->N;
+  real gamma = (real)c->phys.gamma;
+  size_t tot = (size_t)c->E * NV * np;
+  real* q = malloc(sizeof(real) * tot);
+  for (size_t k = 0; k < tot; k++) q[k] = (real)qd[k];
+  for (size_t k = 0; k < tot; k++) out[k] = 0;
+  prim_t* pr = malloc(sizeof(prim_t) * (size_t)c->E * np);
+  for (int e = 0; e < c->E; e++)
+    for (int n = 0; n < np; n++) {
+      real qn[NV];
+      for (int v = 0; v < NV; v++) qn[v] = q[((size_t)e * NV + v) * np + n];
+      pr[(size_t)e * np + n] = primitives(qn, node_phi(c, e, n), gamma);
+    }
+  for (int e = 0; e < c->E; e++) {
+    const real* Ja = c->Ja + (size_t)e * 9 * np;
+    const real* J = c->J + (size_t)e * np;
+    for (int i = 0; i < np; i++) {
+      real acc[NV] = {0, 0, 0, 0, 0};
+      for (int d = 0; d < 3; d++) {
+        int a = node_i(B, i, d);
+        for (int m = 0; m < Nq; m++) {
+          if (m == a) continue;
+          int l = node_with(B, i, d, m);
+          real n[3], F[NV], G[3];
+          for (int k = 0; k < 3; k++) n[k] = (Ja[(d * 3 + k) * np + i] + Ja[(d * 3 + k) * np + l]) / 2;
+          ec_flux(&pr[(size_t)e * np + i], &pr[(size_t)e * np + l], n, gamma, F, G);
+          for (int k = 0; k < 3; k++) F[1 + k] = fabs(F[1 + k]) + fabs(G[k]);
+          for (int v = 0; v < NV; v++) acc[v] += fabs(B->Dt[a][m]) * fabs(F[v]);
+        }
+      }
+      for (int d = 0; d < 3; d++)
+        for (int side = 0; side < 2; side++) {
+          if (node_i(B, i, d) != (side ? N : 0)) continue;
+          real s = 0;
+          for (int k = 0; k < 3; k++) s += Ja[(d * 3 + k) * np + i] * Ja[(d * 3 + k) * np + i];
+          s = sqrt(s);
+          /* |F*| bounded by the flux of the node's own state along the normal */
+          real nh[3], F[NV], G[3];
+          for (int k = 0; k < 3; k++) nh[k] = Ja[(d * 3 + k) * np + i] / s;
+          ec_flux(&pr[(size_t)e * np + i], &pr[(size_t)e * np + i], nh, gamma, F, G);
+          for (int v = 0; v < NV; v++) acc[v] += s / B->w[0] * fabs(F[v]);
+        }
+      for (int v = 0; v < NV; v++) out[((size_t)e * NV + v) * np + i] = (double)(acc[v] / J[i]);
+    }
+  }
+  free(q);
   free(pr);
   return 0;
 }

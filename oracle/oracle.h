@@ -56,6 +56,7 @@ int     or_geometry(const or_ctx* c, double* x, double* J, double* Ja);
  * and source contributions separately (each may be NULL). */
 int or_rhs(const or_ctx* c, const double* q, double* rhs);
 int or_rhs_parts(const or_ctx* c, const double* q, double* vol, double* surf, double* src);
+int or_rhs_scale(const or_ctx* c, const double* q, double* out);
 
 /* Carpenter-Kennedy five-stage fourth-order 2N-storage RK. */
 void or_lsrk_coeffs(double* A, double* B, double* c);
