@@ -52,6 +52,7 @@ typedef struct {
   real xi[MAXQ], w[MAXQ];
   real D[MAXQ][MAXQ];   /* nodal differentiation matrix */
   real Dt[MAXQ][MAXQ];  /* 2D - W^{-1} B, zero diagonal */
+  long double xl[MAXQ], Dl[MAXQ][MAXQ];  /* extended-precision copies for the geometry */
 } basis_t;
 
 /* Legendre polynomial L_N and L_{N-1} at x by the three-term recurrence. */
@@ -98,6 +99,7 @@ static int build_basis(int N, basis_t* B) {
   B->Nq = Nq;
   B->np = Nq * Nq * Nq;
   for (int i = 0; i < Nq; i++) {
+    B->xl[i] = x[i];
     B->xi[i] = (real)x[i];
     B->w[i] = (real)(2.0L / (N * (N + 1.0L) * LN[i] * LN[i]));
   }
@@ -108,6 +110,7 @@ static int build_basis(int N, basis_t* B) {
       else if (i == 0) d = -N * (N + 1.0L) / 4.0L;
       else if (i == N) d = N * (N + 1.0L) / 4.0L;
       else d = 0.0L;
+      B->Dl[i][l] = d;
       B->D[i][l] = (real)d;
     }
   /* Dt = 2D - W^{-1}B with B = diag(-1, 0, ..., 0, 1); its diagonal is zero
@@ -160,12 +163,20 @@ static int node_with(const basis_t* B, int n, int d, int m) {
   return ijk[0] + Nq * (ijk[1] + Nq * ijk[2]);
 }
 
+/* The geometry is evaluated in long double and rounded once to the working
+ * precision.  The curl form differentiates the node positions twice, so
+ * position round-off (relative to the element size) is amplified by roughly
+ * N^4; in extended precision the rounded metric terms are those of the exact
+ * positions, identical on both sides of every face, and the right-hand side's
+ * rounding floor is set by the flux arithmetic alone. */
+typedef long double greal;
+
 /* derivative of a nodal field along reference direction d using D */
-static void dref(const basis_t* B, int d, const real* f, real* out) {
+static void dref(const basis_t* B, int d, const greal* f, greal* out) {
   for (int n = 0; n < B->np; n++) {
     int a = node_i(B, n, d);
-    real s = 0;
-    for (int m = 0; m < B->Nq; m++) s += B->D[a][m] * f[node_with(B, n, d, m)];
+    greal s = 0;
+    for (int m = 0; m < B->Nq; m++) s += B->Dl[a][m] * f[node_with(B, n, d, m)];
     out[n] = s;
   }
 }
@@ -175,47 +186,47 @@ static void dref(const basis_t* B, int d, const real* f, real* out) {
  *   z += a Lz sin(2 pi x'/Lx) sin(2 pi y'/Ly),
  * all three displacements evaluated at the unwarped point (x', y', z' measured
  * from the box origin). */
-static void element_coords(const or_ctx* c, int e, real* X /* [3][np] */) {
+static void element_coords(const or_ctx* c, int e, greal* X /* [3][np] */) {
   const or_mesh* m = &c->mesh;
   const basis_t* B = &c->B;
   int K[3] = {m->kx, m->ky, m->kz};
   int eidx[3] = {e % m->kx, (e / m->kx) % m->ky, e / (m->kx * m->ky)};
-  const real pi = (real)3.141592653589793238462643383279502884L;
+  const greal pi = 3.141592653589793238462643383279502884L;
   for (int n = 0; n < B->np; n++) {
-    real r[3], L[3];
+    greal r[3], L[3];
     for (int d = 0; d < 3; d++) {
-      real xi = B->xi[node_i(B, n, d)];
-      L[d] = (real)m->hi[d] - (real)m->lo[d];
-      r[d] = L[d] * ((real)eidx[d] + (1 + xi) / 2) / (real)K[d];  /* offset from lo */
+      greal xi = B->xl[node_i(B, n, d)];
+      L[d] = (greal)m->hi[d] - (greal)m->lo[d];
+      r[d] = L[d] * ((greal)eidx[d] + (1 + xi) / 2) / (greal)K[d];  /* offset from lo */
     }
-    real out[3] = {r[0], r[1], r[2]};
+    greal out[3] = {r[0], r[1], r[2]};
     if (m->warp != 0.0) {
-      real a = (real)m->warp;
-      real s0 = sin(2 * pi * r[0] / L[0]), s1 = sin(2 * pi * r[1] / L[1]),
-           s2 = sin(2 * pi * r[2] / L[2]);
+      greal a = (greal)m->warp;
+      greal s0 = sin(2 * pi * r[0] / L[0]), s1 = sin(2 * pi * r[1] / L[1]),
+            s2 = sin(2 * pi * r[2] / L[2]);
       out[0] += a * L[0] * s1 * s2;
       out[1] += a * L[1] * s2 * s0;
       out[2] += a * L[2] * s0 * s1;
     }
-    for (int d = 0; d < 3; d++) X[d * B->np + n] = (real)m->lo[d] + out[d];
+    for (int d = 0; d < 3; d++) X[d * B->np + n] = (greal)m->lo[d] + out[d];
   }
 }
 
 /* Conservative curl-form metric terms (Kopriva 2006):
  *   Ja^d_n = -xhat_d . curl_xi( X_l grad_xi X_m ),  (n, m, l) cyclic,
  * and J = X_xi . (X_eta x X_zeta), all derivatives by D. */
-static void element_metrics(const or_ctx* c, const real* X, real* J, real* Ja) {
+static void element_metrics(const or_ctx* c, const greal* X, greal* J, greal* Ja) {
   const basis_t* B = &c->B;
   int np = B->np;
-  real *dX = malloc(sizeof(real) * 9 * np), *V = malloc(sizeof(real) * 3 * np),
-       *t1 = malloc(sizeof(real) * np), *t2 = malloc(sizeof(real) * np);
+  greal *dX = malloc(sizeof(greal) * 9 * np), *V = malloc(sizeof(greal) * 3 * np),
+        *t1 = malloc(sizeof(greal) * np), *t2 = malloc(sizeof(greal) * np);
   for (int comp = 0; comp < 3; comp++)
     for (int d = 0; d < 3; d++) dref(B, d, X + comp * np, dX + (comp * 3 + d) * np);
   /* dX[comp][d] = d X_comp / d xi_d */
   for (int n = 0; n < np; n++) {
-    real a0 = dX[(0 * 3 + 0) * np + n], a1 = dX[(1 * 3 + 0) * np + n], a2 = dX[(2 * 3 + 0) * np + n];
-    real b0 = dX[(0 * 3 + 1) * np + n], b1 = dX[(1 * 3 + 1) * np + n], b2 = dX[(2 * 3 + 1) * np + n];
-    real c0 = dX[(0 * 3 + 2) * np + n], c1 = dX[(1 * 3 + 2) * np + n], c2 = dX[(2 * 3 + 2) * np + n];
+    greal a0 = dX[(0 * 3 + 0) * np + n], a1 = dX[(1 * 3 + 0) * np + n], a2 = dX[(2 * 3 + 0) * np + n];
+    greal b0 = dX[(0 * 3 + 1) * np + n], b1 = dX[(1 * 3 + 1) * np + n], b2 = dX[(2 * 3 + 1) * np + n];
+    greal c0 = dX[(0 * 3 + 2) * np + n], c1 = dX[(1 * 3 + 2) * np + n], c2 = dX[(2 * 3 + 2) * np + n];
     J[n] = a0 * (b1 * c2 - b2 * c1) + a1 * (b2 * c0 - b0 * c2) + a2 * (b0 * c1 - b1 * c0);
   }
   /* X_l grad X_m is formed with X_l measured from the element's first node:
@@ -224,7 +235,7 @@ static void element_metrics(const or_ctx* c, const real* X, real* J, real* Ja) {
    * grows with the distance from the coordinate origin. */
   for (int comp = 0; comp < 3; comp++) {
     int mm = (comp + 1) % 3, ll = (comp + 2) % 3;
-    real x0 = X[ll * np];
+    greal x0 = X[ll * np];
     for (int d = 0; d < 3; d++)
       for (int n = 0; n < np; n++) V[d * np + n] = (X[ll * np + n] - x0) * dX[(mm * 3 + d) * np + n];
     /* curl components: (d1 V2 - d2 V1, d2 V0 - d0 V2, d0 V1 - d1 V0) */
@@ -252,11 +263,18 @@ or_ctx* or_create(const or_mesh* mesh, int N, const or_phys* phys) {
   c->x = malloc(sizeof(real) * (size_t)c->E * 3 * c->np);
   c->J = malloc(sizeof(real) * (size_t)c->E * c->np);
   c->Ja = malloc(sizeof(real) * (size_t)c->E * 9 * c->np);
+  greal *X = malloc(sizeof(greal) * 3 * c->np), *Jg = malloc(sizeof(greal) * c->np),
+        *Jag = malloc(sizeof(greal) * 9 * c->np);
   for (int e = 0; e < c->E; e++) {
-    element_coords(c, e, c->x + (size_t)e * 3 * c->np);
-    element_metrics(c, c->x + (size_t)e * 3 * c->np, c->J + (size_t)e * c->np,
-                    c->Ja + (size_t)e * 9 * c->np);
+    element_coords(c, e, X);
+    element_metrics(c, X, Jg, Jag);
+    for (int k = 0; k < 3 * c->np; k++) c->x[(size_t)e * 3 * c->np + k] = (real)X[k];
+    for (int k = 0; k < c->np; k++) c->J[(size_t)e * c->np + k] = (real)Jg[k];
+    for (int k = 0; k < 9 * c->np; k++) c->Ja[(size_t)e * 9 * c->np + k] = (real)Jag[k];
   }
+  free(X);
+  free(Jg);
+  free(Jag);
   return c;
 }
 
@@ -865,40 +883,33 @@ double or_entropy_rate(const or_ctx* c, const double* q, const double* rhs) {
   return (double)s;
 }
 
-/* Time step: dt = C min over elements and nodes of dmin_e / (|u| + c), with
- * dmin_e the element's shortest corner-to-corner edge times (xi_1 - xi_0)/2. */
+/* Time step from the contravariant wave speeds of every node,
+ *   dt = C (xi_1 - xi_0) / max_{e, n, d} (|u . Ja^d| + c |Ja^d|) / J,
+ * i.e. C times the smallest LGL spacing in reference coordinates over the
+ * largest reference-space signal speed.  On an affine element of edge h this is
+ * C h (xi_1 - xi_0) / (2 (|u_d| + c)), the familiar node-spacing CFL rule; on
+ * the warped meshes it follows the local compression of the elements. */
 double or_cfl_dt(const or_ctx* c, const double* q, double C) {
   const basis_t* B = &c->B;
-  int np = c->np, N = B->N;
-  real gamma = (real)c->phys.gamma, best = -1;
-  real frac = (B->xi[1] - B->xi[0]) / 2;
-  for (int e = 0; e < c->E; e++) {
-    const real* X = c->x + (size_t)e * 3 * np;
-    real hmin = -1;
-    for (int d = 0; d < 3; d++)
-      for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++) {
-          int ij0[3], ij1[3];
-          int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
-          ij0[d] = 0;
-          ij1[d] = N;
-          ij0[o1] = ij1[o1] = a * N;
-          ij0[o2] = ij1[o2] = b * N;
-          int n0 = ij0[0] + B->Nq * (ij0[1] + B->Nq * ij0[2]);
-          int n1 = ij1[0] + B->Nq * (ij1[1] + B->Nq * ij1[2]);
-          real l2 = 0;
-          for (int k = 0; k < 3; k++) l2 += (X[k * np + n1] - X[k * np + n0]) * (X[k * np + n1] - X[k * np + n0]);
-          real len = sqrt(l2);
-          if (hmin < 0 || len < hmin) hmin = len;
-        }
+  int np = c->np;
+  real gamma = (real)c->phys.gamma, lam_max = 0;
+  for (int e = 0; e < c->E; e++)
     for (int n = 0; n < np; n++) {
       real qn[NV];
       for (int v = 0; v < NV; v++) qn[v] = (real)q[((size_t)e * NV + v) * np + n];
       prim_t s = primitives(qn, node_phi(c, e, n), gamma);
-      real sp = sqrt(s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]) + sqrt(gamma * s.p / s.rho);
-      real cand = hmin * frac / sp;
-      if (best < 0 || cand < best) best = cand;
+      real cs = sqrt(gamma * s.p / s.rho);
+      real J = c->J[(size_t)e * np + n];
+      for (int d = 0; d < 3; d++) {
+        real un = 0, a2 = 0;
+        for (int k = 0; k < 3; k++) {
+          real ja = c->Ja[(((size_t)e * 3 + d) * 3 + k) * np + n];
+          un += s.u[k] * ja;
+          a2 += ja * ja;
+        }
+        real lam = (fabs(un) + cs * sqrt(a2)) / J;
+        if (lam > lam_max) lam_max = lam;
+      }
     }
-  }
-  return (double)((real)C * best);
+  return (double)((real)C * (B->xi[1] - B->xi[0]) / lam_max);
 }
