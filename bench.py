@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark of the ES-DG Euler + buoyancy hot path on GB300.
+
+Workload: rising thermal bubble on 32 x 32 x 32 hexahedra at N = 4 (4,096,000
+LGL nodes) on the smoothly warped 1000 m cube (periodic x, y; walls z), 0.5 K
+cosine bubble, dt from CFL 0.5.  A step is one LSRK(5,4) time step: five
+stages, each one interface-flux launch and one volume launch with the RK update
+fused in.  Metric: DOF-updates per second per RK stage = nodes * 5 * steps / s.
+
+The JSON line reports the FP64 path as the headline and the mixed-precision
+path (FP32 pairs, FP64 state) next to it; the roofline object is the FP64
+volume kernel's achieved algorithmic FLOP rate (events around every volume
+launch of the timed region) against the FP64 vector peak; e2e is the same
+metric through the C ABI with pinned host buffers copied in and out every step.
+
+Multi-GPU (torchrun): every rank advances its own replica (ensemble members are
+independent, no data-path collective); value = all ranks' DOF-updates / max time.
+
+--impl reference times the CPU oracle (single-threaded C, as it stands) on a
+bounded sample of the same workload (8 x 8 x 8 elements, same N, mesh and
+physics), one LSRK step per timed step.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(K=(32, 32, 32), N=4, lo=(0.0, 0.0, 0.0), hi=(1000.0, 1000.0, 1000.0),
+                periodic=(1, 1, 0), warp=0.05, theta0=300.0, amp=0.5,
+                centre=(500.0, 500.0, 350.0), radius=250.0, cfl=0.5)
+WORKLOAD_NAME = "rising_bubble_32x32x32_N4_warped"
+SAMPLE_K = (8, 8, 8)
+METRIC = "DOF-updates/s per RK stage"
+UNIT = "DOF-updates/s"
+
+# Algorithmic work of the volume kernel (counted from the formulas, FMA = 2):
+# per unordered node pair 100 flops (averages 9, two log means 22, p* 2, u_n 5,
+# F_rho 1, F_m 9, F_E 14, gravity and its partner 13, accumulation into both
+# nodes 26); per node 45 flops (primitive recovery 20, epilogue and RK update 25).
+FLOPS_PER_PAIR = 100
+FLOPS_PER_NODE = 45
+# Algorithmic bytes of the interface kernel per face node (FP64): two traces
+# (2 x 40 B), face geometry (40 B) and the flux write (40 B); RK state traffic
+# is fused into the volume kernel.
+FACE_BYTES_PER_NODE = {"fp64": 160, "mixed": 140}
+
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2     # 2 DFMA / clk / SM -> 1.258 TFLOP/s
+FP32_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2   # 128 FFMA / clk / SM -> 80.5 TFLOP/s
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def pairs_per_element(N):
+    Nq = N + 1
+    return 3 * Nq * Nq * Nq * (Nq - 1) // 2
+
+
+def volume_flops(E, N):
+    return E * (pairs_per_element(N) * FLOPS_PER_PAIR + (N + 1) ** 3 * FLOPS_PER_NODE)
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ our GPU arm --
+
+def run_gpu_arm(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_2605_16684_gb300 import _build, _lib
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    _build.build()
+    w = WORKLOAD
+    stream = torch.cuda.current_stream()
+    results = {}
+    sampler = None
+    for prec in ("fp64", "mixed"):
+        s = _lib.Solver(*w["K"], w["N"], lo=w["lo"], hi=w["hi"], periodic=w["periodic"],
+                        warp=w["warp"], precision=prec, stream=stream)
+        info = s.info()
+        s.init_bubble(w["theta0"], w["amp"], w["centre"], w["radius"])
+        dt = s.cfl_dt(w["cfl"])
+        # warm-up steps through the same stage launches as the timed region
+        for _ in range(args.warmup):
+            for st in range(5):
+                s.launch(0)
+                s.launch(2, st, dt)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)]
+              for _ in range(5 * args.steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if prec == "fp64":
+            sampler = ClockSampler(local)
+            time.sleep(0.3)
+        t0.record(stream)
+        k = 0
+        for _ in range(args.steps):
+            for st in range(5):
+                ev[k][0].record(stream)
+                s.launch(0)
+                ev[k][1].record(stream)
+                s.launch(2, st, dt)
+                ev[k][2].record(stream)
+                k += 1
+        t1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if prec == "fp64" else None
+        ms = t0.elapsed_time(t1)
+        t_face = sum(e[0].elapsed_time(e[1]) for e in ev) / len(ev)
+        t_vol = sum(e[1].elapsed_time(e[2]) for e in ev) / len(ev)
+        if dist is not None:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        # e2e: the C-ABI call with host buffers, copies inside the timed region
+        qh = torch.empty(s.shape(), dtype=torch.float64, pin_memory=True)
+        s.get_state(qh)
+        e2e_steps = max(1, min(args.steps, 5))
+        s.set_state(qh)
+        s.step(dt, 1)
+        s.get_state(qh)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        te = time.perf_counter()
+        for _ in range(e2e_steps):
+            s.set_state(qh)
+            s.step(dt, 1)
+            s.get_state(qh)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - te
+        if dist is not None:
+            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        q = qh.numpy()
+        finite = bool(np.isfinite(q).all())
+        ndof = info.ndof
+        results[prec] = dict(ms=ms, t_face=t_face, t_vol=t_vol, ndof=ndof, dt=dt,
+                             e2e_s=te, e2e_steps=e2e_steps, clocks=clocks, finite=finite,
+                             state_bytes=ndof * 5 * 8, E=info.nelem)
+        s.close()
+        del qh
+    return results
+
+
+def cpu_sample(seconds_target=10.0):
+    """The oracle, as it stands, single-threaded, on a bounded sample."""
+    import oracle as O
+    w = WORKLOAD
+    o = O.Oracle(*SAMPLE_K, w["N"], lo=w["lo"], hi=w["hi"], periodic=w["periodic"], warp=w["warp"])
+    q = o.bubble(w["theta0"], w["amp"], w["centre"], w["radius"])
+    dt = o.cfl_dt(q, w["cfl"])
+    ndof = o.E * o.np
+    t = time.perf_counter()
+    stages = 0
+    while True:
+        q = o.steps(q, dt, 1)
+        stages += 5
+        el = time.perf_counter() - t
+        if el >= seconds_target:
+            break
+    return dict(value=ndof * stages / el, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{SAMPLE_K[0]}x{SAMPLE_K[1]}x{SAMPLE_K[2]} elements of the same warped "
+                       f"bubble at N={w['N']} ({ndof} nodes), {stages // 5} LSRK steps, "
+                       f"single-threaded C oracle in FP64, {el:.1f} s")
+
+
+def config_block(extra=None):
+    w = WORKLOAD
+    c = {"workload": WORKLOAD_NAME, "elements": w["K"][0] * w["K"][1] * w["K"][2], "N": w["N"],
+         "dof": w["K"][0] * w["K"][1] * w["K"][2] * (w["N"] + 1) ** 3,
+         "mesh": "1000 m cube, warp 0.05 L, periodic x/y, walls z",
+         "initial_state": "0.5 K cosine bubble r=250 m at (500,500,350) m over theta0=300 K",
+         "dt": "CFL 0.5", "step": "one LSRK(5,4) step = 5 stages x (interface + volume/RK)",
+         "l2": "working set ~1 GB per stage > 129 MB L2 (no flush needed)",
+         "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def main_ours(args):
+    dist = None
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    res = run_gpu_arm(args, rank, world, dist)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = measured_peaks()
+    r64, r32 = res["fp64"], res["mixed"]
+    w = WORKLOAD
+    stage_updates = r64["ndof"] * 5 * args.steps
+    value = world * stage_updates / (r64["ms"] * 1e-3)
+    value32 = world * r32["ndof"] * 5 * args.steps / (r32["ms"] * 1e-3)
+    vflops = volume_flops(r64["E"], w["N"])
+    achieved = vflops / (r64["t_vol"] * 1e-3)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block({"precision": "fp64"}),
+        "roofline": {"bound": "alu", "kernel": "volume (flux differencing + lift + RK), FP64",
+                     "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK, "traffic": None,
+                     "peak_source": "152 SMs x 2 DFMA/clk x 2070 MHz (recipe's 1.25 TFLOP/s FP64)",
+                     "flops_per_launch": vflops, "ms_per_launch": r64["t_vol"]},
+        "kernels_ms_per_stage": {"fp64": {"interface": r64["t_face"], "volume_rk": r64["t_vol"]},
+                                 "mixed": {"interface": r32["t_face"], "volume_rk": r32["t_vol"]}},
+        "mixed": {"value": value32, "unit": UNIT, "dtype": "f32 pairs, f64 state",
+                  "ms_per_step": r32["ms"] / args.steps,
+                  "volume_fp32_tflops": vflops / (r32["t_vol"] * 1e-3) / 1e12,
+                  "volume_fp32_frac": vflops / (r32["t_vol"] * 1e-3) / FP32_PEAK,
+                  "speedup_vs_fp64": value32 / value,
+                  "e2e": {"value": world * r32["ndof"] * 5 * r32["e2e_steps"] / r32["e2e_s"],
+                          "unit": UNIT}},
+        "e2e": {"value": world * r64["ndof"] * 5 * r64["e2e_steps"] / r64["e2e_s"], "unit": UNIT,
+                "h2d_bytes_per_step": r64["state_bytes"], "d2h_bytes_per_step": r64["state_bytes"],
+                "steps": r64["e2e_steps"]},
+        "gpu_launches": 10 * args.steps,
+        "clocks": r64["clocks"],
+        "finite": r64["finite"] and r32["finite"],
+        "peaks_source": peak_src,
+    }
+    if not args.no_cpu_baseline and world >= 1:
+        out["cpu_baseline"] = cpu_sample(args.cpu_seconds)
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle as O
+    w = WORKLOAD
+    o = O.Oracle(*SAMPLE_K, w["N"], lo=w["lo"], hi=w["hi"], periodic=w["periodic"], warp=w["warp"])
+    q = o.bubble(w["theta0"], w["amp"], w["centre"], w["radius"])
+    dt = o.cfl_dt(q, w["cfl"])
+    for _ in range(args.warmup):
+        q = o.steps(q, dt, 1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        q = o.steps(q, dt, 1)
+    el = time.perf_counter() - t
+    ndof = o.E * o.np
+    value = ndof * 5 * args.steps / el
+    sample = (f"{SAMPLE_K[0]}x{SAMPLE_K[1]}x{SAMPLE_K[2]} elements of the 32^3 workload's warped "
+              f"bubble at N={w['N']} ({ndof} nodes), one LSRK step per timed step, "
+              f"single-threaded C oracle in FP64")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_block({"precision": "fp64", "sample": sample}),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

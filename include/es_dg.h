@@ -1,0 +1,155 @@
+/*
+ * es_dg.h -- C ABI of the GB300 entropy-stable DG Euler + buoyancy library.
+ *
+ * The library evaluates the semi-discrete right-hand side of the entropy-stable
+ * discontinuous Galerkin method (Section 3, Eq. (nm:semi)) on structured boxes
+ * of curvilinear hexahedra with (N+1)^3 LGL nodes, and advances it with the
+ * Carpenter-Kennedy five-stage fourth-order low-storage Runge-Kutta scheme.
+ * All arithmetic runs in CUDA kernels on one GPU; the host only launches.
+ *
+ * Conventions
+ *   - Every function returns int: ES_DG_OK (0), a negative error code, or (for
+ *     es_dg_batch_poll only) ES_DG_PENDING (> 0).  es_dg_strerror() names it.
+ *   - State layout q[e][v][n] in double: v = 0..4 is rho, rho u, rho v, rho w, E
+ *     (E includes rho g z, Section 2); n = i + Nq (j + Nq k) with Nq = N + 1;
+ *     e = ex + Kx (ey + Ky ez).  Element ex spans
+ *     [lo_x + ex (hi_x - lo_x)/Kx, lo_x + (ex+1)(hi_x - lo_x)/Kx] before warping.
+ *   - The caller owns every pointer it passes; the library copies in and out.
+ *     "on_device" = 1 means the pointer is device memory of the handle's GPU,
+ *     0 means host memory (pageable or pinned).
+ *   - A handle is not thread-safe; calls on one handle are ordered on its stream
+ *     and return before the GPU work finishes unless stated otherwise.
+ *   - Precision changes only internal arithmetic; the interface is always double.
+ */
+#ifndef ES_DG_H
+#define ES_DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ES_DG_OK = 0,
+  ES_DG_PENDING = 1,     /* es_dg_batch_poll: request not finished yet */
+  ES_DG_EINVAL = -1,     /* bad argument */
+  ES_DG_ENOMEM = -2,     /* device allocation failed or over budget */
+  ES_DG_ECUDA = -3,      /* a CUDA call failed */
+  ES_DG_ENAN = -4,       /* non-finite or non-physical state detected */
+  ES_DG_ETIMEOUT = -5,   /* a bounded device wait ran out */
+  ES_DG_EBUSY = -6,      /* server queue full */
+  ES_DG_ECANCELED = -7   /* request cancelled */
+};
+
+typedef enum {
+  ES_DG_FP64 = 0,        /* all arithmetic in FP64 */
+  ES_DG_FP32_MIXED = 1   /* flux pairs and derivative sums in FP32; state,
+                            RK accumulation, pressure and energy recovery in FP64 */
+} es_dg_precision;
+
+/* Structured box of Kx x Ky x Kz hexahedra.  periodic[d] = 1 joins the two d
+ * faces, 0 makes them reflecting walls.  warp > 0 displaces every node by
+ *   x += warp Lx sin(2 pi y'/Ly) sin(2 pi z'/Lz), y += warp Ly sin(2 pi z'/Lz) sin(2 pi x'/Lx),
+ *   z += warp Lz sin(2 pi x'/Lx) sin(2 pi y'/Ly)   (primes: offsets from lo, all
+ * evaluated at the unwarped point). */
+typedef struct {
+  int kx, ky, kz;
+  double lo[3], hi[3];
+  int periodic[3];
+  double warp;
+} es_dg_mesh;
+
+/* Gas, gravity and rotation constants (Section 2).  gamma = cp/cv, g the
+ * gravitational acceleration (phi = g z), R the gas constant, p0 the reference
+ * pressure of the initial states, Coriolis parameter f = f0 + beta (y - y0)
+ * about z.  dissipation = 1 adds matrix dissipation to the interface flux
+ * (Section 3), 0 keeps it entropy-conservative.  NULL selects gamma = 1.4,
+ * g = 9.81, R = 287, p0 = 1e5, f0 = beta = y0 = 0, dissipation = 1. */
+typedef struct {
+  double gamma, g, R, p0, f0, beta, y0;
+  int dissipation;
+} es_dg_physics;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns device memory of at least `bytes` or NULL; free releases it.  NULL
+ * allocator = cudaMalloc / cudaFree. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* ctx;
+} es_dg_allocator;
+
+typedef struct es_dg es_dg_t;
+
+typedef struct {
+  int N, Nq, np;           /* order, nodes per direction, nodes per element */
+  int nelem;               /* elements */
+  long long ndof;          /* nodes = nelem * np (the paper counts DOF this way) */
+  long long nfaces;        /* interior, periodic and wall faces */
+  size_t device_bytes;     /* device memory held by the handle */
+  int precision;
+} es_dg_info_t;
+
+/* Create a solver on the current CUDA device.  `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream).  Builds node coordinates, curl-form
+ * metric terms (Kopriva), face normals and the LGL operators on the device.
+ * N in 1..7.  On error *out is NULL. */
+int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,
+                 const es_dg_physics* physics, const es_dg_allocator* allocator,
+                 void* cuda_stream, es_dg_t** out);
+void es_dg_destroy(es_dg_t* h);
+int es_dg_get_info(const es_dg_t* h, es_dg_info_t* info);
+
+/* Copy the state in or out (layout above, nelem*5*np doubles). */
+int es_dg_set_state(es_dg_t* h, const double* q, int on_device);
+int es_dg_get_state(es_dg_t* h, double* q, int on_device);
+
+/* Rising-bubble initial state on the device (Section 5.1, Eq. (smooth-rb-ic)):
+ * isentropic background theta0, cosine theta perturbation of amplitude amp
+ * (K) and radius `radius` about `centre`; pressure unperturbed; u = 0. */
+int es_dg_init_bubble(es_dg_t* h, double theta0, double amp, const double centre[3],
+                      double radius);
+/* Synthetic baroclinic-channel state (balanced zonal jet of isothermal columns
+ * plus a 1 m/s Gaussian wind perturbation; see the oracle for the formulas). */
+int es_dg_init_channel(es_dg_t* h);
+
+/* One evaluation of the right-hand side dq/dt of Eq. (nm:semi) at state q
+ * (not the handle's state), written to rhs.  Both pointers host or both device
+ * per on_device.  Synchronous when on_device = 0. */
+int es_dg_rhs(es_dg_t* h, const double* q, double* rhs, int on_device);
+
+/* Time step of the handle's state from the contravariant signal speeds,
+ *   dt = C (xi_1 - xi_0) / max over nodes and directions d of
+ *        (|u . Ja^d| + c |Ja^d|) / J,
+ * which on an affine element of edge h is C h (xi_1 - xi_0) / (2 (|u_d| + c)).
+ * Synchronous.  -ES_DG_ENAN if the state has a non-positive pressure. */
+int es_dg_cfl_dt(es_dg_t* h, double C, double* dt);
+
+/* Advance the handle's state by nsteps LSRK(5,4) steps of size dt (Section 3).
+ * Asynchronous on the handle's stream; each stage is one interface-flux launch
+ * and one volume launch with the RK update fused in. */
+int es_dg_step(es_dg_t* h, double dt, int nsteps);
+int es_dg_sync(es_dg_t* h);
+
+/* Global integrals of the handle's state: mass, total energy, entropy
+ * (sum over elements of the quadrature of rho, E and -rho s/(gamma-1)).
+ * Synchronous. */
+int es_dg_integrals(es_dg_t* h, double out[3]);
+
+/* Device geometry for inspection: x[e][3][n], J[e][n], Ja[e][d][c][n] (double).
+ * Any pointer may be NULL.  Synchronous when on_device = 0. */
+int es_dg_geometry(es_dg_t* h, double* x, double* J, double* Ja, int on_device);
+
+/* Launch a single kernel of the right-hand side on the handle's state, for
+ * timing: which = 0 interface flux, 1 volume (writes the rhs buffer), 2 volume
+ * with the fused RK update at stage `stage` (0..4) and step dt. */
+int es_dg_launch(es_dg_t* h, int which, int stage, double dt);
+
+const char* es_dg_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

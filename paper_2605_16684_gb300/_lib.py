@@ -1,0 +1,243 @@
+"""ctypes binding of include/es_dg.h (argument marshalling only).
+
+Every computation happens in libesdg.so's CUDA kernels.  If the library has not
+been built, loading raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+ES_DG_OK = 0
+ES_DG_PENDING = 1
+ES_DG_FP64 = 0
+ES_DG_FP32_MIXED = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class es_dg_mesh(C.Structure):
+    _fields_ = [("kx", C.c_int), ("ky", C.c_int), ("kz", C.c_int),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("periodic", C.c_int * 3), ("warp", C.c_double)]
+
+
+class es_dg_physics(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("g", C.c_double), ("R", C.c_double),
+                ("p0", C.c_double), ("f0", C.c_double), ("beta", C.c_double),
+                ("y0", C.c_double), ("dissipation", C.c_int)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class es_dg_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class es_dg_info_t(C.Structure):
+    _fields_ = [("N", C.c_int), ("Nq", C.c_int), ("np", C.c_int), ("nelem", C.c_int),
+                ("ndof", C.c_longlong), ("nfaces", C.c_longlong),
+                ("device_bytes", C.c_size_t), ("precision", C.c_int)]
+
+
+_VP = C.c_void_p
+_DP = C.POINTER(C.c_double)
+
+SIGNATURES = {
+    "es_dg_create": (C.c_int, [C.POINTER(es_dg_mesh), C.c_int, C.c_int, C.POINTER(es_dg_physics),
+                               C.POINTER(es_dg_allocator), _VP, C.POINTER(_VP)]),
+    "es_dg_destroy": (None, [_VP]),
+    "es_dg_get_info": (C.c_int, [_VP, C.POINTER(es_dg_info_t)]),
+    "es_dg_set_state": (C.c_int, [_VP, _VP, C.c_int]),
+    "es_dg_get_state": (C.c_int, [_VP, _VP, C.c_int]),
+    "es_dg_init_bubble": (C.c_int, [_VP, C.c_double, C.c_double, _DP, C.c_double]),
+    "es_dg_init_channel": (C.c_int, [_VP]),
+    "es_dg_rhs": (C.c_int, [_VP, _VP, _VP, C.c_int]),
+    "es_dg_cfl_dt": (C.c_int, [_VP, C.c_double, _DP]),
+    "es_dg_step": (C.c_int, [_VP, C.c_double, C.c_int]),
+    "es_dg_sync": (C.c_int, [_VP]),
+    "es_dg_integrals": (C.c_int, [_VP, _DP]),
+    "es_dg_geometry": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int]),
+    "es_dg_launch": (C.c_int, [_VP, C.c_int, C.c_int, C.c_double]),
+    "es_dg_strerror": (C.c_char_p, [C.c_int]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libesdg.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+        return _lib
+
+
+class EsDgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = load().es_dg_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def check(code: int, where: str) -> int:
+    if code < 0:
+        raise EsDgError(code, where)
+    return code
+
+
+def _ptr(a) -> int:
+    """Data pointer of a C-contiguous float64 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.dtype.is_floating_point and a.is_contiguous()
+    return a.data_ptr()
+
+
+def _on_device(a) -> int:
+    return 0 if isinstance(a, np.ndarray) else int(a.is_cuda)
+
+
+class _TorchAllocator:
+    """Hands PyTorch's caching allocator to the library (es_dg_allocator)."""
+
+    def __init__(self, stream_ptr: int):
+        import torch
+        self._torch = torch
+        self._stream = stream_ptr
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+        self.struct = es_dg_allocator(self._alloc, self._free, None)
+
+    def _do_alloc(self, nbytes, ctx):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), stream=self._stream)
+        except Exception:
+            return None
+
+    def _do_free(self, ptr, ctx):
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+
+class Solver:
+    """One es_dg handle: a mesh, an order, a precision and the state on the GPU."""
+
+    def __init__(self, kx, ky, kz, N, lo=(0.0, 0.0, 0.0), hi=(1000.0, 1000.0, 1000.0),
+                 periodic=(1, 1, 0), warp=0.0, precision="fp64", stream=None,
+                 torch_allocator=True, **phys):
+        import torch
+        self.lib = load()
+        self.N, self.Nq, self.np = N, N + 1, (N + 1) ** 3
+        self.K = (kx, ky, kz)
+        self.E = kx * ky * kz
+        self.precision = precision
+        p = dict(gamma=1.4, g=9.81, R=287.0, p0=1.0e5, f0=0.0, beta=0.0, y0=0.0, dissipation=1)
+        p.update(phys)
+        self.phys = p
+        self._mesh = es_dg_mesh(kx, ky, kz, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi),
+                                (C.c_int * 3)(*periodic), float(warp))
+        self._phys = es_dg_physics(p["gamma"], p["g"], p["R"], p["p0"], p["f0"], p["beta"],
+                                   p["y0"], int(p["dissipation"]))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sp = stream.cuda_stream
+        self._alloc = _TorchAllocator(sp) if torch_allocator else None
+        h = C.c_void_p()
+        prec = {"fp64": ES_DG_FP64, "mixed": ES_DG_FP32_MIXED}[precision]
+        check(self.lib.es_dg_create(C.byref(self._mesh), N, prec, C.byref(self._phys),
+                                    C.byref(self._alloc.struct) if self._alloc else None,
+                                    C.c_void_p(sp), C.byref(h)), "es_dg_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.es_dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self):
+        return (self.E, 5, self.np)
+
+    def info(self) -> es_dg_info_t:
+        i = es_dg_info_t()
+        check(self.lib.es_dg_get_info(self.h, C.byref(i)), "es_dg_get_info")
+        return i
+
+    def set_state(self, q):
+        check(self.lib.es_dg_set_state(self.h, C.c_void_p(_ptr(q)), _on_device(q)), "es_dg_set_state")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape())
+        check(self.lib.es_dg_get_state(self.h, C.c_void_p(_ptr(out)), _on_device(out)), "es_dg_get_state")
+        return out
+
+    def init_bubble(self, theta0=300.0, amp=0.5, centre=(500.0, 500.0, 350.0), radius=250.0):
+        c = (C.c_double * 3)(*centre)
+        check(self.lib.es_dg_init_bubble(self.h, theta0, amp, c, radius), "es_dg_init_bubble")
+
+    def init_channel(self):
+        check(self.lib.es_dg_init_channel(self.h), "es_dg_init_channel")
+
+    def rhs(self, q, out=None):
+        if out is None:
+            out = np.empty(self.shape()) if isinstance(q, np.ndarray) else q.new_empty(self.shape())
+        check(self.lib.es_dg_rhs(self.h, C.c_void_p(_ptr(q)), C.c_void_p(_ptr(out)), _on_device(q)),
+              "es_dg_rhs")
+        return out
+
+    def cfl_dt(self, C_=0.5) -> float:
+        dt = C.c_double()
+        check(self.lib.es_dg_cfl_dt(self.h, float(C_), C.byref(dt)), "es_dg_cfl_dt")
+        return dt.value
+
+    def step(self, dt, nsteps=1):
+        check(self.lib.es_dg_step(self.h, float(dt), int(nsteps)), "es_dg_step")
+
+    def sync(self):
+        check(self.lib.es_dg_sync(self.h), "es_dg_sync")
+
+    def integrals(self):
+        out = (C.c_double * 3)()
+        check(self.lib.es_dg_integrals(self.h, out), "es_dg_integrals")
+        return np.array(out[:])
+
+    def geometry(self):
+        x = np.empty((self.E, 3, self.np))
+        J = np.empty((self.E, self.np))
+        Ja = np.empty((self.E, 3, 3, self.np))
+        check(self.lib.es_dg_geometry(self.h, C.c_void_p(x.ctypes.data), C.c_void_p(J.ctypes.data),
+                                      C.c_void_p(Ja.ctypes.data), 0), "es_dg_geometry")
+        return x, J, Ja
+
+    def launch(self, which: int, stage: int = 0, dt: float = 0.0):
+        check(self.lib.es_dg_launch(self.h, int(which), int(stage), float(dt)), "es_dg_launch")

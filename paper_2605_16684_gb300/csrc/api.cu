@@ -1,0 +1,389 @@
+// api.cu -- the C ABI of include/es_dg.h: handle management, buffers and launch
+// sequences.  All arithmetic happens in the kernels; this file only validates
+// arguments, owns device memory and orders launches on the handle's stream.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/es_dg.h"
+#include "esdg_internal.cuh"
+
+namespace {
+
+// Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage coefficients
+const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+
+}  // namespace
+
+struct es_dg {
+  EsdgGrid g;
+  EsdgLGL L;
+  EsdgPhys P;
+  int mixed;
+  cudaStream_t stream;
+  es_dg_allocator alloc;
+  int has_alloc;
+  std::vector<void*> blocks;
+  size_t bytes;
+  double* q;
+  void* dq;
+  double *x, *J, *Ja, *vgeo, *fgeo;
+  float* vgeo32;
+  void* fflux;
+  double* rhs;      // lazily allocated
+  double* qtmp;     // lazily allocated
+  double* scratch;  // reductions
+  double* result;   // small device result slots (4 doubles)
+};
+
+namespace {
+
+int dev_alloc(es_dg_t* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (h->has_alloc) {
+    *p = h->alloc.alloc(bytes, h->alloc.ctx);
+    if (!*p) return ES_DG_ENOMEM;
+  } else {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return ES_DG_ENOMEM;
+    }
+  }
+  h->blocks.push_back(*p);
+  h->bytes += bytes;
+  return ES_DG_OK;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return ES_DG_OK;
+  if (e == cudaErrorMemoryAllocation) return ES_DG_ENOMEM;
+  return ES_DG_ECUDA;
+}
+
+int build_grid(const es_dg_mesh* m, int N, EsdgGrid* g) {
+  if (!m || N < 1 || N > 7) return ES_DG_EINVAL;
+  const int K[3] = {m->kx, m->ky, m->kz};
+  long long E = 1;
+  for (int d = 0; d < 3; d++) {
+    if (K[d] < 1 || !(m->hi[d] > m->lo[d])) return ES_DG_EINVAL;
+    E *= K[d];
+  }
+  if (E > (1LL << 30) || !(m->warp >= 0.0 && m->warp < 0.15)) return ES_DG_EINVAL;
+  std::memset(g, 0, sizeof(*g));
+  for (int d = 0; d < 3; d++) {
+    g->K[d] = K[d];
+    g->periodic[d] = m->periodic[d] ? 1 : 0;
+    g->lo[d] = m->lo[d];
+    g->hi[d] = m->hi[d];
+    g->nplanes[d] = g->periodic[d] ? K[d] : K[d] + 1;
+  }
+  g->warp = m->warp;
+  g->N = N;
+  g->Nq = N + 1;
+  g->np = g->Nq * g->Nq * g->Nq;
+  g->E = (int)E;
+  long long off = 0;
+  for (int d = 0; d < 3; d++) {
+    int o1, o2;
+    esdg_others(d, o1, o2);
+    g->face_off[d] = off;
+    off += (long long)g->nplanes[d] * K[o1] * K[o2];
+  }
+  g->nfaces = off;
+  return ES_DG_OK;
+}
+
+int ensure_rhs_buffers(es_dg_t* h) {
+  const size_t n = (size_t)h->g.E * 5 * h->g.np;
+  int st = ES_DG_OK;
+  if (!h->rhs) st = dev_alloc(h, (void**)&h->rhs, n * sizeof(double));
+  if (st == ES_DG_OK && !h->qtmp) st = dev_alloc(h, (void**)&h->qtmp, n * sizeof(double));
+  return st;
+}
+
+EsdgVolArgs vol_args(es_dg_t* h, const double* q_in, double* rhs_out) {
+  EsdgVolArgs a;
+  a.q_in = q_in;
+  a.q_io = h->q;
+  a.dq = h->dq;
+  a.rhs = rhs_out;
+  a.vgeo = h->mixed ? (const void*)h->vgeo32 : (const void*)h->vgeo;
+  a.vgeo64 = h->vgeo;
+  a.fflux = h->fflux;
+  a.x = h->x;
+  a.rkA = 0.0;
+  a.rkB = 0.0;
+  a.dt = 0.0;
+  return a;
+}
+
+// face fluxes then volume (+ lift, source, optional RK update) for state q_in
+int launch_stage(es_dg_t* h, const double* q_in, int mode, double* rhs_out, double A, double B,
+                 double dt) {
+  cudaError_t e = esdg_launch_face(h->g, h->P, h->mixed, q_in, h->fgeo, h->fflux, h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  EsdgVolArgs a = vol_args(h, q_in, rhs_out);
+  a.rkA = A;
+  a.rkB = B;
+  a.dt = dt;
+  e = esdg_launch_volume(h->g, h->L, h->P, h->mixed, mode, a, h->stream);
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,
+                 const es_dg_physics* physics, const es_dg_allocator* allocator,
+                 void* cuda_stream, es_dg_t** out) {
+  if (!out) return ES_DG_EINVAL;
+  *out = nullptr;
+  if (precision != ES_DG_FP64 && precision != ES_DG_FP32_MIXED) return ES_DG_EINVAL;
+  if (allocator && (!allocator->alloc || !allocator->free)) return ES_DG_EINVAL;
+  EsdgGrid g;
+  int st = build_grid(mesh, N, &g);
+  if (st) return st;
+  es_dg_t* h = new (std::nothrow) es_dg();
+  if (!h) return ES_DG_ENOMEM;
+  h->g = g;
+  if (esdg_lgl_build(N, &h->L)) {
+    delete h;
+    return ES_DG_EINVAL;
+  }
+  for (int i = 0; i < ESDG_MAXNQ; i++)
+    for (int l = 0; l < ESDG_MAXNQ; l++) h->L.Dtf[i][l] = (float)h->L.Dt[i][l];
+  if (physics) {
+    h->P.gamma = physics->gamma;
+    h->P.g = physics->g;
+    h->P.R = physics->R;
+    h->P.p0 = physics->p0;
+    h->P.f0 = physics->f0;
+    h->P.beta = physics->beta;
+    h->P.y0 = physics->y0;
+    h->P.dissipation = physics->dissipation ? 1 : 0;
+    if (!(h->P.gamma > 1.0) || !(h->P.R > 0.0) || !(h->P.p0 > 0.0)) {
+      delete h;
+      return ES_DG_EINVAL;
+    }
+  } else {
+    h->P = EsdgPhys{1.4, 9.81, 287.0, 1.0e5, 0.0, 0.0, 0.0, 1};
+  }
+  {
+    // gravity acts along z: a z-periodic box would make phi = g z jump across
+    // the periodic faces, which the balance law does not allow
+    if (g.periodic[2] && h->P.g != 0.0) {
+      delete h;
+      return ES_DG_EINVAL;
+    }
+  }
+  h->mixed = (precision == ES_DG_FP32_MIXED);
+  h->stream = (cudaStream_t)cuda_stream;
+  if (allocator) {
+    h->alloc = *allocator;
+    h->has_alloc = 1;
+  }
+  const size_t E = g.E, np = g.np, nf2 = (size_t)g.Nq * g.Nq;
+  const size_t nq = E * 5 * np;
+  st = dev_alloc(h, (void**)&h->q, nq * sizeof(double));
+  if (!st) st = dev_alloc(h, &h->dq, nq * (h->mixed ? sizeof(float) : sizeof(double)));
+  if (!st) st = dev_alloc(h, (void**)&h->x, E * 3 * np * sizeof(double));
+  if (!st) st = dev_alloc(h, (void**)&h->J, E * np * sizeof(double));
+  if (!st) st = dev_alloc(h, (void**)&h->Ja, E * 9 * np * sizeof(double));
+  if (!st) st = dev_alloc(h, (void**)&h->vgeo, E * ESDG_NVGEO * np * sizeof(double));
+  if (!st) st = dev_alloc(h, (void**)&h->vgeo32, E * ESDG_NVGEO * np * sizeof(float));
+  if (!st) st = dev_alloc(h, (void**)&h->fgeo, (size_t)g.nfaces * 5 * nf2 * sizeof(double));
+  if (!st)
+    st = dev_alloc(h, &h->fflux,
+                   (size_t)g.nfaces * 5 * nf2 * (h->mixed ? sizeof(float) : sizeof(double)));
+  if (!st) st = dev_alloc(h, (void**)&h->scratch, esdg_reduce_scratch(g) * sizeof(double));
+  if (!st) st = dev_alloc(h, (void**)&h->result, 4 * sizeof(double));
+  if (st) {
+    es_dg_destroy(h);
+    return st;
+  }
+  cudaError_t e = cudaMemsetAsync(h->dq, 0, nq * (h->mixed ? sizeof(float) : sizeof(double)), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->q, 0, nq * sizeof(double), h->stream);
+  if (e == cudaSuccess)
+    e = esdg_launch_geometry(h->g, h->L, h->x, h->J, h->Ja, h->vgeo, h->vgeo32, h->fgeo, h->P,
+                             h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    es_dg_destroy(h);
+    return cuda_status(e);
+  }
+  *out = h;
+  return ES_DG_OK;
+}
+
+void es_dg_destroy(es_dg_t* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (void* p : h->blocks) {
+    if (h->has_alloc) h->alloc.free(p, h->alloc.ctx);
+    else cudaFree(p);
+  }
+  delete h;
+}
+
+int es_dg_get_info(const es_dg_t* h, es_dg_info_t* info) {
+  if (!h || !info) return ES_DG_EINVAL;
+  info->N = h->g.N;
+  info->Nq = h->g.Nq;
+  info->np = h->g.np;
+  info->nelem = h->g.E;
+  info->ndof = (long long)h->g.E * h->g.np;
+  info->nfaces = h->g.nfaces;
+  info->device_bytes = h->bytes;
+  info->precision = h->mixed ? ES_DG_FP32_MIXED : ES_DG_FP64;
+  return ES_DG_OK;
+}
+
+int es_dg_set_state(es_dg_t* h, const double* q, int on_device) {
+  if (!h || !q) return ES_DG_EINVAL;
+  const size_t bytes = (size_t)h->g.E * 5 * h->g.np * sizeof(double);
+  cudaError_t e = cudaMemcpyAsync(h->q, q, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                            : cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+  return cuda_status(e);
+}
+
+int es_dg_get_state(es_dg_t* h, double* q, int on_device) {
+  if (!h || !q) return ES_DG_EINVAL;
+  const size_t bytes = (size_t)h->g.E * 5 * h->g.np * sizeof(double);
+  cudaError_t e = cudaMemcpyAsync(q, h->q, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                            : cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+  return cuda_status(e);
+}
+
+int es_dg_init_bubble(es_dg_t* h, double theta0, double amp, const double centre[3],
+                      double radius) {
+  if (!h || !centre || !(theta0 > 0.0) || !(radius > 0.0)) return ES_DG_EINVAL;
+  return cuda_status(
+      esdg_launch_bubble(h->g, h->P, h->x, theta0, amp, centre, radius, h->q, h->stream));
+}
+
+int es_dg_init_channel(es_dg_t* h) {
+  if (!h) return ES_DG_EINVAL;
+  if (h->P.f0 == 0.0 && h->P.beta == 0.0) return ES_DG_EINVAL;  // geostrophic balance needs f
+  return cuda_status(esdg_launch_channel(h->g, h->P, h->x, h->q, h->stream));
+}
+
+int es_dg_rhs(es_dg_t* h, const double* q, double* rhs, int on_device) {
+  if (!h || !q || !rhs) return ES_DG_EINVAL;
+  const size_t bytes = (size_t)h->g.E * 5 * h->g.np * sizeof(double);
+  const double* qin = q;
+  double* rout = rhs;
+  if (!on_device) {
+    int st = ensure_rhs_buffers(h);
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(h->qtmp, q, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    qin = h->qtmp;
+    rout = h->rhs;
+  }
+  int st = launch_stage(h, qin, 0, rout, 0.0, 0.0, 0.0);
+  if (st) return st;
+  if (!on_device) {
+    cudaError_t e = cudaMemcpyAsync(rhs, h->rhs, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+  }
+  return ES_DG_OK;
+}
+
+int es_dg_cfl_dt(es_dg_t* h, double C, double* dt) {
+  if (!h || !dt || !(C > 0.0)) return ES_DG_EINVAL;
+  cudaError_t e = esdg_launch_cfl(h->g, h->L, h->P, h->q, h->x, h->J, h->Ja, h->scratch, h->result,
+                                  h->stream);
+  double r = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&r, h->result, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!(r > 0.0) || r != r) return ES_DG_ENAN;
+  *dt = C * (h->L.xi[1] - h->L.xi[0]) * r;
+  return ES_DG_OK;
+}
+
+int es_dg_step(es_dg_t* h, double dt, int nsteps) {
+  if (!h || nsteps < 0 || !(dt > 0.0)) return ES_DG_EINVAL;
+  for (int n = 0; n < nsteps; n++)
+    for (int s = 0; s < 5; s++) {
+      int st = launch_stage(h, h->q, 1, nullptr, kRkA[s], kRkB[s], dt);
+      if (st) return st;
+    }
+  return ES_DG_OK;
+}
+
+int es_dg_sync(es_dg_t* h) {
+  if (!h) return ES_DG_EINVAL;
+  return cuda_status(cudaStreamSynchronize(h->stream));
+}
+
+int es_dg_integrals(es_dg_t* h, double out[3]) {
+  if (!h || !out) return ES_DG_EINVAL;
+  cudaError_t e = esdg_launch_integrals(h->g, h->L, h->P, h->q, h->J, h->x, h->scratch, h->result,
+                                        h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return cuda_status(e);
+}
+
+int es_dg_geometry(es_dg_t* h, double* x, double* J, double* Ja, int on_device) {
+  if (!h) return ES_DG_EINVAL;
+  const size_t E = h->g.E, np = h->g.np;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  if (x) e = cudaMemcpyAsync(x, h->x, E * 3 * np * sizeof(double), k, h->stream);
+  if (e == cudaSuccess && J) e = cudaMemcpyAsync(J, h->J, E * np * sizeof(double), k, h->stream);
+  if (e == cudaSuccess && Ja) e = cudaMemcpyAsync(Ja, h->Ja, E * 9 * np * sizeof(double), k, h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+  return cuda_status(e);
+}
+
+int es_dg_launch(es_dg_t* h, int which, int stage, double dt) {
+  if (!h || stage < 0 || stage > 4) return ES_DG_EINVAL;
+  if (which == 0)
+    return cuda_status(esdg_launch_face(h->g, h->P, h->mixed, h->q, h->fgeo, h->fflux, h->stream));
+  if (which == 1) {
+    int st = ensure_rhs_buffers(h);
+    if (st) return st;
+    EsdgVolArgs a = vol_args(h, h->q, h->rhs);
+    return cuda_status(esdg_launch_volume(h->g, h->L, h->P, h->mixed, 0, a, h->stream));
+  }
+  if (which == 2) {
+    EsdgVolArgs a = vol_args(h, h->q, nullptr);
+    a.rkA = kRkA[stage];
+    a.rkB = kRkB[stage];
+    a.dt = dt;
+    return cuda_status(esdg_launch_volume(h->g, h->L, h->P, h->mixed, 1, a, h->stream));
+  }
+  return ES_DG_EINVAL;
+}
+
+const char* es_dg_strerror(int status) {
+  switch (status) {
+    case ES_DG_OK: return "ok";
+    case ES_DG_PENDING: return "pending";
+    case ES_DG_EINVAL: return "invalid argument";
+    case ES_DG_ENOMEM: return "out of device memory or over budget";
+    case ES_DG_ECUDA: return "CUDA error";
+    case ES_DG_ENAN: return "non-finite or non-physical state";
+    case ES_DG_ETIMEOUT: return "bounded device wait timed out";
+    case ES_DG_EBUSY: return "queue full";
+    case ES_DG_ECANCELED: return "cancelled";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

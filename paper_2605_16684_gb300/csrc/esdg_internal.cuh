@@ -1,0 +1,169 @@
+// esdg_internal.cuh -- device-side definitions shared by the library's kernels.
+//
+// Data layout in HBM (one handle, E elements, np = Nq^3 nodes each):
+//   q, dq, rhs      double [E][5][np]            element-major, variable, node
+//   vgeo            double [E][11][np]           1/2 Ja^d_c (9), 1/J, phi
+//   vgeo32          float  [E][11][np]           same, FP32 copy (mixed mode)
+//   x               double [E][3][np]            node coordinates
+//   fgeo            double [F][5][Nq^2]          nhat (3), s / w_end, phi per face node
+//   fflux           double/float [F][5][Nq^2]    (s / w_end) F* per face node
+// Faces are numbered direction by direction: face (d, P, a, b) with plane P along
+// d and element indices (a, b) along the two other directions in increasing
+// order; its node (s, t) has node index s along the first, t along the second.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#define ESDG_NV 5
+#define ESDG_MAXNQ 8
+#define ESDG_NVGEO 11
+
+struct EsdgLGL {  // LGL operators, passed by value (lives in the constant bank)
+  int N;
+  double xi[ESDG_MAXNQ];
+  double w[ESDG_MAXNQ];
+  double D[ESDG_MAXNQ][ESDG_MAXNQ];   // nodal differentiation matrix
+  double Dt[ESDG_MAXNQ][ESDG_MAXNQ];  // 2D - W^-1 B, zero diagonal
+  float Dtf[ESDG_MAXNQ][ESDG_MAXNQ];  // FP32 copy for the mixed-precision pair loop
+  double xi_lo[ESDG_MAXNQ];           // low parts (xi = xi + xi_lo, D = D + D_lo) for the
+  double D_lo[ESDG_MAXNQ][ESDG_MAXNQ];  // double-double geometry construction
+};
+
+struct EsdgPhys {
+  double gamma, g, R, p0, f0, beta, y0;
+  int dissipation;
+};
+
+struct EsdgGrid {  // structured box and derived face numbering
+  int K[3];
+  int periodic[3];
+  double lo[3], hi[3];
+  double warp;
+  int N, Nq, np, E;
+  int nplanes[3];
+  long long face_off[3];
+  long long nfaces;
+};
+
+// the two directions other than d, in increasing order
+__host__ __device__ inline void esdg_others(int d, int& o1, int& o2) {
+  o1 = (d == 0) ? 1 : 0;
+  o2 = (d == 2) ? 1 : 2;
+}
+
+__host__ __device__ inline int esdg_node(int Nq, int i, int j, int k) { return i + Nq * (j + Nq * k); }
+
+// face id of plane P in direction d at transverse element indices (a, b)
+__host__ __device__ inline long long esdg_face_id(const EsdgGrid& g, int d, int P, int a, int b) {
+  int o1, o2;
+  esdg_others(d, o1, o2);
+  return g.face_off[d] + ((long long)P * g.K[o2] + b) * g.K[o1] + a;
+}
+
+#ifdef __CUDACC__
+// Reciprocal in FP64 by Newton-Raphson refinement of an FP32 seed.  With
+// e = 1 - x r0 the update r0 (1 + e + e^2) is the cubically convergent
+// (Householder order-2) step for f(r) = 1/r - x; from the ~2^-23 seed of
+// rcp.approx.f32 the truncation error e^3 is below 2^-66, so the result is
+// within one rounding of 1/x.  Valid for |x| in the normal FP32 range.
+__device__ __forceinline__ double esdg_rcp(double x) {
+  float xf = __double2float_rn(x);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+  double r = (double)rf;
+  double e = fma(-x, r, 1.0);
+  double t = fma(e, e, e);
+  return fma(r, t, r);
+}
+
+// Same with a single Newton step (relative error ~2^-46); used only where the
+// result feeds a small correction term.
+__device__ __forceinline__ double esdg_rcp_lo(double x) {
+  float xf = __double2float_rn(x);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+  double r = (double)rf;
+  double e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+__device__ __forceinline__ float esdg_rcpf(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Log-mean series.  With f = (a - b)/(a + b), u = f^2:
+//   ln(a/b) = 2 f A(u),  A(u) = sum_k u^k / (2k + 1),
+//   <a>_log = (a - b)/ln(a/b) = {{a}} Q(u),  Q = 1/A = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
+// (coefficients of f/artanh f).  For u < 1e-4 four terms leave a truncation
+// error below 2e-17.
+#define ESDG_LOG_EPS 1.0e-4
+__device__ __forceinline__ double esdg_A(double u) {
+  return fma(u, fma(u, fma(u, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), 1.0);
+}
+__device__ __forceinline__ double esdg_Q(double u) {
+  return fma(u, fma(u, fma(u, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
+}
+__device__ __forceinline__ double esdg_Q2(double u) {  // 2 Q(u)
+  return fma(u, fma(u, fma(u, -88.0 / 945.0, -8.0 / 45.0), -2.0 / 3.0), 2.0);
+}
+// FP32 variants: for u < 2e-2 the four-term truncation error is below 2e-8.
+#define ESDG_LOG_EPS32 2.0e-2f
+__device__ __forceinline__ float esdg_Af(float u) {
+  return fmaf(u, fmaf(u, fmaf(u, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
+}
+__device__ __forceinline__ float esdg_Qf(float u) {
+  return fmaf(u, fmaf(u, fmaf(u, -44.0f / 945.0f, -4.0f / 45.0f), -1.0f / 3.0f), 1.0f);
+}
+__device__ __forceinline__ float esdg_Q2f(float u) {
+  return fmaf(u, fmaf(u, fmaf(u, -88.0f / 945.0f, -8.0f / 45.0f), -2.0f / 3.0f), 2.0f);
+}
+
+#endif  // __CUDACC__
+
+// ---- launch wrappers implemented in the kernel translation units ----------
+cudaError_t esdg_launch_geometry(const EsdgGrid& g, const EsdgLGL& L, double* x, double* J,
+                                 double* Ja, double* vgeo, float* vgeo32, double* fgeo,
+                                 const EsdgPhys& P, cudaStream_t s);
+cudaError_t esdg_launch_bubble(const EsdgGrid& g, const EsdgPhys& P, const double* x, double theta0,
+                               double amp, const double* centre, double radius, double* q,
+                               cudaStream_t s);
+cudaError_t esdg_launch_channel(const EsdgGrid& g, const EsdgPhys& P, const double* x, double* q,
+                                cudaStream_t s);
+cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
+                             const double* fgeo, void* fflux, cudaStream_t s);
+// mode 0: write rhs; mode 1: fused LSRK stage (dq, q updated in place)
+struct EsdgVolArgs {
+  const double* q_in;    // state read by the prologue and the source term
+  double* q_io;          // mode 1: state updated in place (may equal q_in)
+  void* dq;              // mode 1: RK register (double in FP64 mode, float in mixed mode)
+  double* rhs;           // mode 0: right-hand side output
+  const void* vgeo;      // [E][11][np] double (FP64) or float (mixed)
+  const double* vgeo64;  // [E][11][np] double (geopotential for the pressure recovery)
+  const void* fflux;     // face fluxes, double or float
+  const double* x;       // coordinates (Coriolis parameter)
+  double rkA, rkB, dt;
+};
+cudaError_t esdg_launch_volume_f64(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P, int mode,
+                                   const EsdgVolArgs& a, cudaStream_t s);
+cudaError_t esdg_launch_volume_mixed(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P,
+                                     int mode, const EsdgVolArgs& a, cudaStream_t s);
+#ifdef __CUDACC__
+inline cudaError_t esdg_launch_volume(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P,
+                                      int mixed, int mode, const EsdgVolArgs& a, cudaStream_t s) {
+  return mixed ? esdg_launch_volume_mixed(g, L, P, mode, a, s)
+               : esdg_launch_volume_f64(g, L, P, mode, a, s);
+}
+#endif
+// Reductions with a scratch buffer of at least esdg_reduce_scratch(g) doubles;
+// the result lands in out[0] (CFL: 1 / the largest reference-space signal
+// speed) or out[0..2] (integrals: mass, energy, entropy), device memory.
+size_t esdg_reduce_scratch(const EsdgGrid& g);
+cudaError_t esdg_launch_cfl(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P, const double* q,
+                            const double* x, const double* J, const double* Ja, double* scratch,
+                            double* out, cudaStream_t s);
+cudaError_t esdg_launch_integrals(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P,
+                                  const double* q, const double* J, const double* x,
+                                  double* scratch, double* out, cudaStream_t s);
+int esdg_lgl_build(int N, EsdgLGL* out);

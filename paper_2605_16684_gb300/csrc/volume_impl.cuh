@@ -1,0 +1,455 @@
+// volume_impl.cuh -- flux-differencing volume kernel (Section 3, the volume term
+// of Eq. (nm:semi), with the optimisations of Section 4.1).
+//
+//   rhs_i = -(1/J_i) [ sum_d sum_l Dt^{(d)}_{il} H^d(q_i, q_l) + face lifts ] + h_i
+//
+// H^d is the two-point entropy-conservative flux with the metric average
+// n = {{Ja^d}}_{il} plus the non-symmetric gravity term 1/2 rho_hat [[phi]] n.
+//
+// Layout on the GPU (one CTA = EPB elements):
+//   prologue   one thread per node: primitives once per node (u = rho u/rho, p,
+//              b = rho/(2p), 1/b), staged in shared memory with 1/2 Ja;
+//   pair pass  one thread per pencil (element, direction d, transverse node):
+//              every unordered pair (i < l) of the pencil is evaluated once and
+//              added to both nodes in registers -- node i gets Dt_il H(i,l),
+//              node l gets Dt_li H(l,i), where H(l,i) shares the symmetric flux
+//              and takes the gravity part -G(i,l) b_i/b_l (Section 4.1).  The
+//              pencil's two end nodes also receive the interface fluxes of the
+//              two faces the pencil pierces;
+//   epilogue   one thread per node: sum the three directions, scale by -1/J,
+//              add the Coriolis source, then write rhs or apply the LSRK stage.
+//
+// The pencil-per-thread pair pass evaluates exactly N_q (N_q - 1)/2 pairs per
+// pencil for every N (no antipodal double counting at odd N, no load
+// imbalance, no shuffles or atomics); the pencil's accumulators live in
+// registers and are exchanged once through shared memory.
+//
+// FP64: log means use the artanh series when u = f^2 < 1e-4 and per-node
+// logarithms otherwise (computed only for CTAs that need them).  Mixed: the
+// prologue recovers the pressure in FP64 and stages FP32 node data; pairs,
+// sums and face lifts run in FP32; the log branch uses log1pf of the ratio;
+// the geopotential is carried relative to each element's first node.
+#pragma once
+#include <type_traits>
+
+#include "esdg_internal.cuh"
+
+namespace esdg_vol {
+
+template <int N, bool MIXED>
+struct Cfg;
+// elements per CTA, chosen so that 3 Nq^2 EPB pencils fill whole warps
+template <> struct Cfg<1, false> { static constexpr int EPB = 8; };
+template <> struct Cfg<2, false> { static constexpr int EPB = 16; };
+template <> struct Cfg<3, false> { static constexpr int EPB = 8; };
+template <> struct Cfg<4, false> { static constexpr int EPB = 5; };
+template <> struct Cfg<5, false> { static constexpr int EPB = 2; };
+template <> struct Cfg<6, false> { static constexpr int EPB = 1; };
+template <> struct Cfg<7, false> { static constexpr int EPB = 1; };
+template <> struct Cfg<1, true> { static constexpr int EPB = 16; };
+template <> struct Cfg<2, true> { static constexpr int EPB = 16; };
+template <> struct Cfg<3, true> { static constexpr int EPB = 8; };
+template <> struct Cfg<4, true> { static constexpr int EPB = 5; };
+template <> struct Cfg<5, true> { static constexpr int EPB = 3; };
+template <> struct Cfg<6, true> { static constexpr int EPB = 2; };
+template <> struct Cfg<7, true> { static constexpr int EPB = 2; };
+
+template <int N, bool MIXED>
+struct Shape {
+  static constexpr int Nq = N + 1, NP = Nq * Nq * Nq, NPEN = Nq * Nq;
+  static constexpr int EPB = Cfg<N, MIXED>::EPB;
+  static constexpr int PENCILS = 3 * NPEN * EPB;
+  static constexpr int THREADS = ((PENCILS + 31) / 32) * 32;
+  // node fields: rq=rho/4, bh=b/2, ib=1/b, uh=u/2 (3), ph=phi/2, [lr, lb], nh=Ja/2 (9)
+  static constexpr int F_LR = 7, F_LB = 8;
+  static constexpr int F_NH = MIXED ? 7 : 9;
+  static constexpr int NF = F_NH + 9;
+  using R = typename std::conditional<MIXED, float, double>::type;
+  static constexpr size_t SMEM = sizeof(R) * (size_t)NF * NP * EPB;
+};
+
+template <typename R>
+struct Node {
+  R rq, bh, ib, u0, u1, u2, ph, n0, n1, n2, lr, lb;
+};
+
+template <typename R, bool LOGS, int F_NH, int NP>
+__device__ __forceinline__ Node<R> load_node(const R* __restrict__ S, int n, int d) {
+  Node<R> a;
+  a.rq = S[0 * NP + n];
+  a.bh = S[1 * NP + n];
+  a.ib = S[2 * NP + n];
+  a.u0 = S[3 * NP + n];
+  a.u1 = S[4 * NP + n];
+  a.u2 = S[5 * NP + n];
+  a.ph = S[6 * NP + n];
+  const R* nh = S + (F_NH + 3 * d) * NP;
+  a.n0 = nh[0 * NP + n];
+  a.n1 = nh[1 * NP + n];
+  a.n2 = nh[2 * NP + n];
+  if (LOGS) {
+    a.lr = S[7 * NP + n];
+    a.lb = S[8 * NP + n];
+  } else {
+    a.lr = a.lb = (R)0;
+  }
+  return a;
+}
+
+// One unordered pair (i = A, l = B) in FP64: 68 FP64 instructions on the
+// series path.  ai += Dt_il H(i,l), al += Dt_li H(l,i).
+template <bool LOGS>
+__device__ __forceinline__ void pair64(const Node<double>& A, const Node<double>& B, double dil,
+                                       double dli, double ce, double* ai, double* al) {
+  const double sr = A.rq + B.rq;  // {{rho}}/2
+  const double sb = A.bh + B.bh;  // {{b}}
+  const double rsb = esdg_rcp(sb);
+  const double pt = sr * rsb;     // p* = {{rho}}/(2{{b}})
+  const double dr = A.rq - B.rq, db = A.bh - B.bh;
+  const double fr = dr * esdg_rcp_lo(sr), ur = fr * fr;
+  const double fb = db * rsb, ub = fb * fb;
+  double rlog, iblog;
+  if (!LOGS) {
+    rlog = sr * esdg_Q2(ur);     // <rho>_log
+    iblog = rsb * esdg_A(ub);    // 1/<b>_log
+  } else {
+    if ((float)ur < (float)ESDG_LOG_EPS) rlog = sr * esdg_Q2(ur);
+    else rlog = (4.0 * dr) * esdg_rcp(A.lr - B.lr);
+    if ((float)ub < (float)ESDG_LOG_EPS) iblog = rsb * esdg_A(ub);
+    else iblog = (A.lb - B.lb) * esdg_rcp(2.0 * db);
+  }
+  const double n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;  // {{Ja^d}}
+  const double u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;  // {{u}}
+  const double un = fma(u2, n2, fma(u1, n1, u0 * n0));
+  const double Fr = rlog * un;
+  const double m0 = fma(Fr, u0, pt * n0);
+  const double m1 = fma(Fr, u1, pt * n1);
+  const double m2 = fma(Fr, u2, pt * n2);
+  const double uu = fma(A.u2, B.u2, fma(A.u1, B.u1, A.u0 * B.u0));  // u_i . u_l / 4
+  const double t = fma(2.0, uu, A.ph + B.ph);                        // u_i.u_l/2 + {{phi}}
+  const double FE = fma(Fr, fma(iblog, ce, t), pt * un);
+  // gravity: 1/2 rho_hat [[phi]] with rho_hat = {{b}} <rho>_log / b_(own node)
+  const double gq = sb * rlog * (B.ph - A.ph);
+  const double gi = gq * A.ib, gl = -gq * B.ib;
+  ai[0] = fma(dil, Fr, ai[0]);
+  ai[1] = fma(dil, fma(gi, n0, m0), ai[1]);
+  ai[2] = fma(dil, fma(gi, n1, m1), ai[2]);
+  ai[3] = fma(dil, fma(gi, n2, m2), ai[3]);
+  ai[4] = fma(dil, FE, ai[4]);
+  al[0] = fma(dli, Fr, al[0]);
+  al[1] = fma(dli, fma(gl, n0, m0), al[1]);
+  al[2] = fma(dli, fma(gl, n1, m1), al[2]);
+  al[3] = fma(dli, fma(gl, n2, m2), al[3]);
+  al[4] = fma(dli, FE, al[4]);
+}
+
+// The same pair in FP32 (mixed mode; geopotential relative to the element).
+template <bool LOGS>
+__device__ __forceinline__ void pair32(const Node<float>& A, const Node<float>& B, float dil,
+                                       float dli, float ce, float* ai, float* al) {
+  const float sr = A.rq + B.rq;
+  const float sb = A.bh + B.bh;
+  const float rsb = esdg_rcpf(sb);
+  const float pt = sr * rsb;
+  const float dr = A.rq - B.rq, db = A.bh - B.bh;
+  const float fr = dr * esdg_rcpf(sr), ur = fr * fr;
+  const float fb = db * rsb, ub = fb * fb;
+  float rlog, iblog;
+  if (!LOGS || (ur < ESDG_LOG_EPS32 && ub < ESDG_LOG_EPS32)) {
+    rlog = sr * esdg_Q2f(ur);
+    iblog = rsb * esdg_Af(ub);
+  } else {
+    rlog = (ur < ESDG_LOG_EPS32) ? sr * esdg_Q2f(ur)
+                                 : (4.0f * dr) / log1pf(dr * esdg_rcpf(B.rq));
+    iblog = (ub < ESDG_LOG_EPS32) ? rsb * esdg_Af(ub)
+                                  : log1pf(db * esdg_rcpf(B.bh)) / (2.0f * db);
+  }
+  const float n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;
+  const float u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;
+  const float un = fmaf(u2, n2, fmaf(u1, n1, u0 * n0));
+  const float Fr = rlog * un;
+  const float m0 = fmaf(Fr, u0, pt * n0);
+  const float m1 = fmaf(Fr, u1, pt * n1);
+  const float m2 = fmaf(Fr, u2, pt * n2);
+  const float uu = fmaf(A.u2, B.u2, fmaf(A.u1, B.u1, A.u0 * B.u0));
+  const float t = fmaf(2.0f, uu, A.ph + B.ph);
+  const float FE = fmaf(Fr, fmaf(iblog, ce, t), pt * un);
+  const float gq = sb * rlog * (B.ph - A.ph);
+  const float gi = gq * A.ib, gl = -gq * B.ib;
+  ai[0] = fmaf(dil, Fr, ai[0]);
+  ai[1] = fmaf(dil, fmaf(gi, n0, m0), ai[1]);
+  ai[2] = fmaf(dil, fmaf(gi, n1, m1), ai[2]);
+  ai[3] = fmaf(dil, fmaf(gi, n2, m2), ai[3]);
+  ai[4] = fmaf(dil, FE, ai[4]);
+  al[0] = fmaf(dli, Fr, al[0]);
+  al[1] = fmaf(dli, fmaf(gl, n0, m0), al[1]);
+  al[2] = fmaf(dli, fmaf(gl, n1, m1), al[2]);
+  al[3] = fmaf(dli, fmaf(gl, n2, m2), al[3]);
+  al[4] = fmaf(dli, FE, al[4]);
+}
+
+template <int N, bool MIXED, bool LOGS>
+__device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED>::R* __restrict__ S,
+                                            int d, int base, int stride, const EsdgLGL& L,
+                                            typename Shape<N, MIXED>::R ce,
+                                            typename Shape<N, MIXED>::R (&acc)[N + 1][5]) {
+  using SH = Shape<N, MIXED>;
+  using R = typename SH::R;
+  constexpr int Nq = N + 1;
+#pragma unroll
+  for (int i = 0; i < Nq; i++) {
+    const Node<R> A = load_node<R, LOGS, SH::F_NH, SH::NP>(S, base + i * stride, d);
+#pragma unroll
+    for (int l = i + 1; l < Nq; l++) {
+      const Node<R> B = load_node<R, LOGS, SH::F_NH, SH::NP>(S, base + l * stride, d);
+      if constexpr (MIXED)
+        pair32<LOGS>(A, B, L.Dtf[i][l], L.Dtf[l][i], ce, acc[i], acc[l]);
+      else
+        pair64<LOGS>(A, B, L.Dt[i][l], L.Dt[l][i], ce, acc[i], acc[l]);
+    }
+  }
+}
+
+template <int N, bool MIXED, int MODE>
+__global__ void __launch_bounds__(Shape<N, MIXED>::THREADS)
+    k_volume(EsdgGrid g, EsdgPhys P, EsdgLGL L, EsdgVolArgs a) {
+  using SH = Shape<N, MIXED>;
+  using R = typename SH::R;
+  constexpr int Nq = SH::Nq, NP = SH::NP, NPEN = SH::NPEN, EPB = SH::EPB, NF = SH::NF;
+  constexpr int T = SH::THREADS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  const int e0 = blockIdx.x * EPB;
+  const int E = g.E;
+  const R* vg = reinterpret_cast<const R*>(a.vgeo);
+  const double gm1 = P.gamma - 1.0;
+
+  // ---- prologue: primitives once per node -------------------------------
+  int need_logs = 0;
+  for (int idx = threadIdx.x; idx < EPB * NP; idx += T) {
+    const int el = idx / NP, n = idx - el * NP, e = e0 + el;
+    R* S = sm + (size_t)el * NF * NP;
+    if (e < E) {
+      const double* qe = a.q_in + (size_t)e * 5 * NP;
+      const double q0 = qe[n], q1 = qe[NP + n], q2 = qe[2 * NP + n], q3 = qe[3 * NP + n],
+                   q4 = qe[4 * NP + n];
+      const double phi = a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP + n];
+      if constexpr (MIXED) {
+        // FP64 only where the hydrostatic background cancels: E - rho phi - KE
+        const float irf = esdg_rcpf((float)q0);
+        const float hf = 0.5f * irf;
+        const float u0 = (float)q1 * hf, u1 = (float)q2 * hf, u2 = (float)q3 * hf;
+        const float ke = fmaf((float)q3, u2, fmaf((float)q2, u1, (float)q1 * u0));
+        const double p = gm1 * (fma(-q0, phi, q4) - (double)ke);
+        const float pf = (float)p;
+        const float rq = 0.25f * (float)q0;
+        S[0 * NP + n] = rq;
+        S[1 * NP + n] = rq * esdg_rcpf(pf);
+        S[2 * NP + n] = 2.0f * pf * irf;
+        S[3 * NP + n] = u0;
+        S[4 * NP + n] = u1;
+        S[5 * NP + n] = u2;
+        const double phi0 = a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP];
+        S[6 * NP + n] = (float)(0.5 * (phi - phi0));
+      } else {
+        const double ir = esdg_rcp(q0);
+        const double hi = 0.5 * ir;
+        const double u0 = q1 * hi, u1 = q2 * hi, u2 = q3 * hi;
+        double ei = fma(-q0, phi, q4);
+        ei = fma(-q1, u0, ei);
+        ei = fma(-q2, u1, ei);
+        ei = fma(-q3, u2, ei);
+        const double p = gm1 * ei;
+        const double rq = 0.25 * q0;
+        S[0 * NP + n] = rq;
+        S[1 * NP + n] = rq * esdg_rcp(p);
+        S[2 * NP + n] = (p + p) * ir;
+        S[3 * NP + n] = u0;
+        S[4 * NP + n] = u1;
+        S[5 * NP + n] = u2;
+        S[6 * NP + n] = 0.5 * phi;
+      }
+#pragma unroll
+      for (int k = 0; k < 9; k++)
+        S[(SH::F_NH + k) * NP + n] = vg[((size_t)e * ESDG_NVGEO + k) * NP + n];
+    } else {  // padding element: any valid state, results are discarded
+      S[0 * NP + n] = (R)0.25;
+      S[1 * NP + n] = (R)0.5;
+      S[2 * NP + n] = (R)1;
+      for (int k = 3; k < NF; k++) S[k * NP + n] = (R)0;
+    }
+  }
+  __syncthreads();
+  if constexpr (!MIXED) {
+    // does any pair of this CTA leave the series range?  All |x_n/x_0 - 1| below
+    // 0.0095 bounds |f| < 0.0096 for every pair, i.e. u < 1e-4.
+    for (int idx = threadIdx.x; idx < EPB * NP; idx += T) {
+      const int el = idx / NP, n = idx - el * NP;
+      const R* S = sm + (size_t)el * NF * NP;
+      const float r0 = (float)S[0], rn = (float)S[n];
+      const float b0 = (float)S[NP], bn = (float)S[NP + n];
+      if (fabsf(rn - r0) > 0.0095f * r0 || fabsf(bn - b0) > 0.0095f * b0) need_logs = 1;
+    }
+    need_logs = __syncthreads_or(need_logs);
+    if (need_logs) {
+      for (int idx = threadIdx.x; idx < EPB * NP; idx += T) {
+        const int el = idx / NP, n = idx - el * NP;
+        R* S = sm + (size_t)el * NF * NP;
+        S[SH::F_LR * NP + n] = log(4.0 * S[n]);
+        S[SH::F_LB * NP + n] = log(2.0 * S[NP + n]);
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < EPB * NP; idx += T) {
+      const int el = idx / NP, n = idx - el * NP;
+      const R* S = sm + (size_t)el * NF * NP;
+      const float r0 = S[0], rn = S[n], b0 = S[NP], bn = S[NP + n];
+      // |f| < 0.14 keeps u < ESDG_LOG_EPS32 for every pair
+      if (fabsf(rn - r0) > 0.13f * r0 || fabsf(bn - b0) > 0.13f * b0) need_logs = 1;
+    }
+    need_logs = __syncthreads_or(need_logs);
+  }
+
+  // ---- pair pass: one pencil per thread ---------------------------------
+  const int tid = threadIdx.x;
+  const bool active = tid < SH::PENCILS;
+  const int el = active ? tid / (3 * NPEN) : 0;
+  const int rr = tid - el * 3 * NPEN;
+  const int d = active ? rr / NPEN : 0;
+  const int pen = rr - d * NPEN;
+  const int s = pen % Nq, t = pen / Nq;
+  const int stride = (d == 0) ? 1 : ((d == 1) ? Nq : Nq * Nq);
+  const int base = (d == 0) ? Nq * (s + Nq * t) : ((d == 1) ? (s + Nq * Nq * t) : (s + Nq * t));
+  const int e = e0 + el;
+  R acc[Nq][5];
+#pragma unroll
+  for (int i = 0; i < Nq; i++)
+#pragma unroll
+    for (int v = 0; v < 5; v++) acc[i][v] = (R)0;
+  if (active && e < E) {
+    const R* S = sm + (size_t)el * NF * NP;
+    const R ce = (R)(0.5 / gm1);
+    if (need_logs)
+      pencil_pass<N, MIXED, true>(S, d, base, stride, L, ce, acc);
+    else
+      pencil_pass<N, MIXED, false>(S, d, base, stride, L, ce, acc);
+    if constexpr (MIXED) {
+      // restore the element's reference geopotential in the energy flux
+      const R phi0 = (R)a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP];
+#pragma unroll
+      for (int i = 0; i < Nq; i++) acc[i][4] = fmaf(phi0, acc[i][0], acc[i][4]);
+    }
+    // face lifts: this element is the "+" side of plane e_d and the "-" side
+    // of plane e_d + 1
+    int idx3[3] = {e % g.K[0], (e / g.K[0]) % g.K[1], e / (g.K[0] * g.K[1])};
+    int o1, o2;
+    esdg_others(d, o1, o2);
+    const int Kd = g.K[d];
+    const int Pm = idx3[d];
+    int Pp = idx3[d] + 1;
+    if (Pp == Kd && g.periodic[d]) Pp = 0;
+    const long long fm = esdg_face_id(g, d, Pm, idx3[o1], idx3[o2]);
+    const long long fp = esdg_face_id(g, d, Pp, idx3[o1], idx3[o2]);
+    const R* ff = reinterpret_cast<const R*>(a.fflux);
+    const int fn = s + Nq * t;
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      acc[0][v] -= ff[((size_t)fm * 5 + v) * NPEN + fn];
+      acc[N][v] += ff[((size_t)fp * 5 + v) * NPEN + fn];
+    }
+  }
+  __syncthreads();
+  if (active && e < E) {
+    R* S = sm + (size_t)el * NF * NP;
+#pragma unroll
+    for (int i = 0; i < Nq; i++)
+#pragma unroll
+      for (int v = 0; v < 5; v++) S[(d * 5 + v) * NP + base + i * stride] = acc[i][v];
+  }
+  __syncthreads();
+
+  // ---- epilogue: one thread per node -------------------------------------
+  const bool rotating = (P.f0 != 0.0) || (P.beta != 0.0);
+  for (int idx = threadIdx.x; idx < EPB * NP; idx += T) {
+    const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
+    if (e2 >= E) continue;
+    const R* S = sm + (size_t)el2 * NF * NP;
+    const R iJ = vg[((size_t)e2 * ESDG_NVGEO + 9) * NP + n];
+    double r[5];
+#pragma unroll
+    for (int v = 0; v < 5; v++)
+      r[v] = (double)(-iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]));
+    const size_t qb = (size_t)e2 * 5 * NP + n;
+    if (rotating) {
+      const double y = a.x[((size_t)e2 * 3 + 1) * NP + n];
+      const double f = P.f0 + P.beta * (y - P.y0);
+      r[1] = fma(f, a.q_in[qb + 2 * NP], r[1]);
+      r[2] = fma(-f, a.q_in[qb + NP], r[2]);
+    }
+    if constexpr (MODE == 0) {
+#pragma unroll
+      for (int v = 0; v < 5; v++) a.rhs[qb + (size_t)v * NP] = r[v];
+    } else {
+      if constexpr (MIXED) {
+        float* dq = reinterpret_cast<float*>(a.dq);
+        const float A = (float)a.rkA, B = (float)a.rkB, dt = (float)a.dt;
+#pragma unroll
+        for (int v = 0; v < 5; v++) {
+          const float dv = fmaf(A, dq[qb + (size_t)v * NP], dt * (float)r[v]);
+          dq[qb + (size_t)v * NP] = dv;
+          a.q_io[qb + (size_t)v * NP] = a.q_in[qb + (size_t)v * NP] + (double)(B * dv);
+        }
+      } else {
+        double* dq = reinterpret_cast<double*>(a.dq);
+#pragma unroll
+        for (int v = 0; v < 5; v++) {
+          const double dv = fma(a.rkA, dq[qb + (size_t)v * NP], a.dt * r[v]);
+          dq[qb + (size_t)v * NP] = dv;
+          a.q_io[qb + (size_t)v * NP] = fma(a.rkB, dv, a.q_in[qb + (size_t)v * NP]);
+        }
+      }
+    }
+  }
+}
+
+template <int N, bool MIXED, int MODE>
+cudaError_t launch_one(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
+                       const EsdgVolArgs& a, cudaStream_t s) {
+  using SH = Shape<N, MIXED>;
+  static bool configured = false;  // one-time attribute set per instantiation
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(k_volume<N, MIXED, MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)SH::SMEM);
+    if (err != cudaSuccess) return err;
+    configured = true;
+  }
+  const unsigned blocks = (unsigned)((g.E + SH::EPB - 1) / SH::EPB);
+  if (blocks == 0) return cudaSuccess;
+  k_volume<N, MIXED, MODE><<<blocks, SH::THREADS, SH::SMEM, s>>>(g, P, L, a);
+  return cudaGetLastError();
+}
+
+template <bool MIXED>
+cudaError_t launch_volume_t(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P, int mode,
+                            const EsdgVolArgs& a, cudaStream_t s) {
+#define ESDG_CASE(NN)                                                          \
+  case NN:                                                                     \
+    return mode ? launch_one<NN, MIXED, 1>(g, P, L, a, s)                      \
+                : launch_one<NN, MIXED, 0>(g, P, L, a, s);
+  switch (g.N) {
+    ESDG_CASE(1)
+    ESDG_CASE(2)
+    ESDG_CASE(3)
+    ESDG_CASE(4)
+    ESDG_CASE(5)
+    ESDG_CASE(6)
+    ESDG_CASE(7)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef ESDG_CASE
+}
+
+}  // namespace esdg_vol

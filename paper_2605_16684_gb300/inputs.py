@@ -7,9 +7,11 @@ supply the coordinates.
 
 Recipes
 -------
-* ``perturbation_factors``: a few random Fourier modes (integer wavenumbers 1..3
-  per axis over the box) evaluated at the given nodes; each returned field is
-  scaled to unit maximum.
+* ``perturbation_factors``: a few random Fourier modes (integer wavenumbers
+  kmin..kmax per axis over the box, 1..3 by default) evaluated at the given
+  nodes; each returned field is scaled to unit maximum.  Fine meshes use
+  wavenumbers that scale with the element count so every element sees O(1)
+  variation and the right-hand side stays O(1) relative to its terms.
 * ``perturb_state``: multiplies density and total energy by (1 + eps f) with
   eps = 1e-2 and adds momentum rho * u0 * f with u0 = 5 m/s, so every conserved
   variable's right-hand side is O(1) ("generic state").
@@ -27,8 +29,9 @@ DEFAULT_SEED = 20260516
 
 
 def perturbation_factors(x: np.ndarray, lo, hi, nfields: int, seed: int = DEFAULT_SEED,
-                         modes: int = 6) -> np.ndarray:
-    """Smooth random fields at node coordinates x[E, 3, np] -> [nfields, E, np]."""
+                         modes: int = 6, kmin: int = 1, kmax: int = 3) -> np.ndarray:
+    """Smooth random fields at node coordinates x[E, 3, np] -> [nfields, E, np];
+    integer wavenumbers per axis are drawn from [kmin, kmax] over the box."""
     rng = np.random.default_rng(seed)
     lo = np.asarray(lo, dtype=np.float64).reshape(3, 1, 1)
     hi = np.asarray(hi, dtype=np.float64).reshape(3, 1, 1)
@@ -37,7 +40,7 @@ def perturbation_factors(x: np.ndarray, lo, hi, nfields: int, seed: int = DEFAUL
     for f in range(nfields):
         acc = np.zeros_like(out[f])
         for _ in range(modes):
-            k = rng.integers(1, 4, size=3)
+            k = rng.integers(kmin, kmax + 1, size=3)
             ph = rng.uniform(0, 2 * np.pi)
             a = rng.uniform(0.5, 1.0)
             acc += a * np.sin(2 * np.pi * (k[0] * xs[0] + k[1] * xs[1] + k[2] * xs[2]) + ph)
@@ -46,9 +49,9 @@ def perturbation_factors(x: np.ndarray, lo, hi, nfields: int, seed: int = DEFAUL
 
 
 def perturb_state(q: np.ndarray, x: np.ndarray, lo, hi, seed: int = DEFAULT_SEED,
-                  eps: float = 1e-2, u0: float = 5.0) -> np.ndarray:
+                  eps: float = 1e-2, u0: float = 5.0, kmin: int = 1, kmax: int = 3) -> np.ndarray:
     """Generic state: q[E, 5, np] with smooth random perturbations of every variable."""
-    f = perturbation_factors(x, lo, hi, 5, seed)
+    f = perturbation_factors(x, lo, hi, 5, seed, kmin=kmin, kmax=kmax)
     out = np.array(q, dtype=np.float64, copy=True)
     out[:, 0, :] = q[:, 0, :] * (1 + eps * f[0])
     for k in range(3):

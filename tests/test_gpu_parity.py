@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars
+* FP64 right-hand side on generic states: relative L2 error per variable
+  <= 1e-12 (the oracle's own double vs long-double floor is ~3e-13).
+* FP64 on near-hydrostatic bubble states, where the RHS is a cancellation of
+  terms ~1e6 times larger: the reference is the long-double oracle, and the
+  error per variable must be <= 1e-12 * ||rhs|| + 300 * 1e-16 * ||scale||
+  (scale = magnitude of the cancelling terms, or_rhs_scale) or no worse than
+  three times the double oracle's own distance from the long-double result.
+  (There the double oracle forms entropy-variable jumps as v+ - v- with
+  |v| ~ 25 and carries ~1e-15 absolute error per jump.)
+* State after LSRK steps: relative L2 error <= 1e-12 per variable, or, for
+  bubble states, no worse than three times the double oracle's distance from
+  the long-double trajectory.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_16684_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CUBE = dict(lo=(0.0, 0.0, 0.0), hi=(1000.0, 1000.0, 1000.0))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_16684_gb300 import _build, _lib
+    _build.build()
+    return _lib
+
+
+def rel_err(a, b):
+    return np.array([np.linalg.norm(a[:, v] - b[:, v]) / max(np.linalg.norm(b[:, v]), 1e-300)
+                     for v in range(5)])
+
+
+def check_floor(r_gpu, r_ref, scale, r_plain=None, rtol=1e-12, floor=300e-16):
+    """r_ref: reference (long double where given); r_plain: the double oracle."""
+    for v in range(5):
+        err = np.linalg.norm(r_gpu[:, v] - r_ref[:, v])
+        bound = rtol * np.linalg.norm(r_ref[:, v]) + floor * np.linalg.norm(scale[:, v])
+        if r_plain is not None:
+            bound = max(bound, 3.0 * np.linalg.norm(r_plain[:, v] - r_ref[:, v]))
+        assert err <= bound, (v, err, bound)
+
+
+def make_pair(lib, K, N, precision="fp64", **kw):
+    mesh = dict(CUBE)
+    mesh.update(kw.pop("mesh", {}))
+    s = lib.Solver(*K, N, precision=precision, **mesh, **kw)
+    o = O.Oracle(*K, N, **mesh, **kw)
+    return s, o, mesh
+
+
+def generic(o, mesh, seed=0, kmin=1, kmax=3):
+    x, _, _ = o.geometry()
+    return inputs.perturb_state(o.bubble(), x, mesh["lo"], mesh["hi"], seed=seed, kmin=kmin,
+                                kmax=kmax)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+def test_geometry_matches_oracle(lib, N):
+    s, o, _ = make_pair(lib, (2, 3, 2), N, mesh=dict(warp=0.05))
+    xg, Jg, Jag = s.geometry()
+    xo, Jo, Jao = o.geometry()
+    assert np.abs(xg - xo).max() <= 1e-12 * np.abs(xo).max()
+    assert np.abs(Jg - Jo).max() <= 1e-12 * np.abs(Jo).max()
+    assert np.abs(Jag - Jao).max() <= 1e-12 * np.abs(Jao).max()
+
+
+CASES = [
+    ((3, 3, 3), 3, dict(warp=0.05, periodic=(1, 1, 0))),
+    ((2, 3, 2), 4, dict(warp=0.05, periodic=(1, 1, 0))),
+    ((3, 2, 2), 2, dict(warp=0.05, periodic=(1, 0, 0))),
+    ((2, 2, 2), 5, dict(warp=0.05, periodic=(0, 0, 0))),
+    ((1, 2, 2), 6, dict(warp=0.05, periodic=(1, 1, 0))),
+    ((2, 1, 2), 7, dict(warp=0.05, periodic=(1, 1, 0))),
+    ((1, 1, 1), 1, dict(periodic=(1, 1, 0))),          # one element, its own x/y neighbour
+    ((7, 1, 1), 4, dict(periodic=(1, 1, 0))),          # ragged tail: 7 elements, 5 per CTA
+    ((4, 4, 4), 3, dict(periodic=(1, 1, 0))),          # the 4x4x4, N = 3 bubble box
+]
+
+
+@pytest.mark.parametrize("K,N,mesh", CASES)
+def test_rhs_parity_fp64_generic(lib, K, N, mesh):
+    s, o, m = make_pair(lib, K, N, mesh=mesh)
+    q = generic(o, m)
+    r_gpu = s.rhs(q)
+    r_ref = o.rhs(q)
+    err = rel_err(r_gpu, r_ref)
+    assert np.all(err <= 1e-12), err
+
+
+@pytest.mark.parametrize("dissipation", [0, 1])
+def test_rhs_parity_against_long_double(lib, dissipation):
+    s, o, m = make_pair(lib, (3, 3, 3), 4, mesh=dict(warp=0.05), dissipation=dissipation)
+    ol = O.Oracle(3, 3, 3, 4, precision="long", dissipation=dissipation, **m)
+    q = generic(o, m, seed=5)
+    err = rel_err(s.rhs(q), ol.rhs(q))
+    assert np.all(err <= 1e-12), err
+
+
+def test_rhs_parity_bubble_states(lib):
+    # 4 x 4 x 4 elements, N = 3, 1000 m cube, periodic x/y, walls z: t = 0 and
+    # after 10 oracle LSRK steps at CFL 0.5
+    s, o, m = make_pair(lib, (4, 4, 4), 3)
+    ol = O.Oracle(4, 4, 4, 3, precision="long", **m)
+    q0 = o.bubble()
+    dt = o.cfl_dt(q0, 0.5)
+    q10 = o.steps(q0, dt, 10)
+    for q in (q0, q10):
+        check_floor(s.rhs(q), ol.rhs(q), o.rhs_scale(q), r_plain=o.rhs(q))
+
+
+def test_step_parity_bubble_c0(lib):
+    s, o, m = make_pair(lib, (4, 4, 4), 3)
+    q0 = o.bubble()
+    s.init_bubble()
+    assert np.abs(s.get_state() - q0).max() <= 1e-12 * np.abs(q0).max()
+    dt = o.cfl_dt(q0, 0.5)
+    assert s.cfl_dt(0.5) == pytest.approx(dt, rel=1e-13)
+    s.set_state(q0)
+    s.step(dt, 10)
+    q_gpu = s.get_state()
+    q_ref = O.Oracle(4, 4, 4, 3, precision="long", **m).steps(q0, dt, 10)
+    q_plain = o.steps(q0, dt, 10)
+    e_gpu, e_plain = rel_err(q_gpu, q_ref), rel_err(q_plain, q_ref)
+    assert np.all((e_gpu <= 1e-12) | (e_gpu <= 3.0 * e_plain)), (e_gpu, e_plain)
+
+
+def test_step_parity_generic(lib):
+    s, o, m = make_pair(lib, (3, 2, 2), 4, mesh=dict(warp=0.05))
+    q0 = generic(o, m, seed=2)
+    dt = o.cfl_dt(q0, 0.5)
+    s.set_state(q0)
+    s.step(dt, 3)
+    q_ref = o.steps(q0, dt, 3)
+    q_gpu = s.get_state()
+    assert np.all(rel_err(q_gpu, q_ref) <= 1e-12)
+    assert np.all(rel_err(q_gpu - q0, q_ref - q0) <= 1e-10)
+
+
+def test_integrals_match_oracle(lib):
+    s, o, m = make_pair(lib, (3, 3, 3), 4, mesh=dict(warp=0.05))
+    q = generic(o, m, seed=3)
+    s.set_state(q)
+    assert np.allclose(s.integrals(), o.integrals(q), rtol=1e-12, atol=0)
+
+
+def test_channel_parity_with_coriolis(lib):
+    kw = dict(mesh=dict(lo=(0.0, 0.0, 0.0), hi=(40000e3, 6000e3, 30e3), periodic=(1, 0, 0)),
+              f0=1e-4)
+    s, o, m = make_pair(lib, (6, 3, 2), 4, **kw)
+    q = o.channel()
+    s.init_channel()
+    assert np.abs(s.get_state() - q).max() <= 1e-12 * np.abs(q).max()
+    ol = O.Oracle(6, 3, 2, 4, precision="long", **m, f0=1e-4)
+    check_floor(s.rhs(q), ol.rhs(q), o.rhs_scale(q), r_plain=o.rhs(q))
+    x, _, _ = o.geometry()
+    qg = inputs.perturb_state(q, x, m["lo"], m["hi"], seed=4)
+    assert np.all(rel_err(s.rhs(qg), o.rhs(qg)) <= 1e-12)
+
+
+def test_entropy_conservation_on_gpu(lib):
+    # EC interface flux: the GPU right-hand side conserves the discrete entropy
+    s, o, m = make_pair(lib, (3, 3, 3), 4, mesh=dict(warp=0.05), dissipation=0)
+    q = generic(o, m, seed=6)
+    r = s.rhs(q)
+    rate = o.entropy_rate(q, r)
+    v, sf, h = o.rhs_parts(q)
+    scale = abs(o.entropy_rate(q, np.abs(v))) + abs(o.entropy_rate(q, np.abs(sf)))
+    assert abs(rate) < 1e-13 * scale
+
+
+def test_device_pointers_and_torch_tensors(lib):
+    import torch
+    s, o, m = make_pair(lib, (2, 2, 2), 4, mesh=dict(warp=0.05))
+    q = generic(o, m)
+    qt = torch.from_numpy(q).cuda()
+    rt = s.rhs(qt)
+    torch.cuda.synchronize()
+    assert np.all(rel_err(rt.cpu().numpy(), o.rhs(q)) <= 1e-12)
+
+
+def test_rhs_parity_full_size_32cubed_N4(lib):
+    # the benchmark workload at full size: 32^3 elements, N = 4, warped cube
+    s, o, m = make_pair(lib, (32, 32, 32), 4, mesh=dict(warp=0.05))
+    # wavenumbers 8..16 per axis: O(1) variation per element, O(1) right-hand side
+    q = generic(o, m, seed=7, kmin=8, kmax=16)
+    err = rel_err(s.rhs(q), o.rhs(q))
+    assert np.all(err <= 1e-12), err
+    qb = o.bubble()
+    s.init_bubble()
+    assert np.abs(s.get_state() - qb).max() <= 1e-12 * np.abs(qb).max()
+    # at rest the plain double oracle is exact up to its term rounding
+    check_floor(s.rhs(qb), o.rhs(qb), o.rhs_scale(qb))
+    assert s.cfl_dt(0.5) == pytest.approx(o.cfl_dt(qb, 0.5), rel=1e-13)
