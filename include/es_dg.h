@@ -149,6 +149,32 @@ int es_dg_launch(es_dg_t* h, int which, int stage, double dt);
 
 const char* es_dg_strerror(int status);
 
+/* ---- allocation-free entry point -------------------------------------------
+ * The paper has no counterpart to this function; it exists for callers that
+ * cannot allocate device memory (a memory pool they do not own, a framework
+ * that forbids cudaMalloc on its hot path, an exhausted allocator).
+ *
+ * es_dg_integrals_noalloc computes the same three integrals as es_dg_integrals
+ * (mass, total energy, entropy) from caller-owned device arrays, without a
+ * handle and without allocating: q[e][v][n] (state), J[e][n] and x[e][3][n]
+ * (as returned by es_dg_geometry with on_device = 1), for the mesh, order and
+ * physics given (physics NULL = defaults).  out3 is caller-owned device memory
+ * for 3 doubles, written asynchronously on cuda_stream (a cudaStream_t, NULL =
+ * legacy default stream); synchronise the stream before reading it.
+ *
+ * Scratch: the per-element partial sums live in a static device array sized
+ * for ES_DG_NOALLOC_MAX_ELEMS elements (3 doubles each, 6 MiB), present on
+ * every GPU that loads the library until the process exits.  Meshes with more
+ * elements are rejected with -ES_DG_EINVAL.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array: calls whose work overlaps on the GPU (different streams
+ * without ordering) race and must be serialised by the caller. */
+#define ES_DG_NOALLOC_MAX_ELEMS 262144
+int es_dg_integrals_noalloc(const es_dg_mesh* mesh, int N, const es_dg_physics* physics,
+                            const double* q, const double* J, const double* x, double* out3,
+                            void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

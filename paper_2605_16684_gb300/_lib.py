@@ -68,6 +68,8 @@ SIGNATURES = {
     "es_dg_geometry": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int]),
     "es_dg_launch": (C.c_int, [_VP, C.c_int, C.c_int, C.c_double]),
     "es_dg_strerror": (C.c_char_p, [C.c_int]),
+    "es_dg_integrals_noalloc": (C.c_int, [C.POINTER(es_dg_mesh), C.c_int, C.POINTER(es_dg_physics),
+                                          _VP, _VP, _VP, _VP, _VP]),
 }
 
 

@@ -131,3 +131,87 @@ cudaError_t esdg_launch_integrals(const EsdgGrid& g, const EsdgLGL& L, const Esd
   k_fold<<<1, RT, 0, s>>>(scratch, g.E, 3, 3, 0, out);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the integrals reduction (es_dg_integrals_noalloc).
+//
+// Some callers cannot allocate device memory at all: code running under a
+// memory pool it does not own, inside a framework that forbids cudaMalloc on
+// its hot path, or in a process whose allocator is already exhausted.  For
+// them the per-element partial sums live in the file-scope array below instead
+// of a handle's scratch buffer.  The array is created with the module on every
+// device that loads this library and stays there until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#include "../../include/es_dg.h"
+
+namespace {
+
+static __device__ __align__(256) double g_noalloc_partials[3 * ES_DG_NOALLOC_MAX_ELEMS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_partials on the current device.  In host code the
+// symbol is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, once per device, with that device current.
+int noalloc_scratch(double** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return ES_DG_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return ES_DG_ECUDA;
+    }
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return ES_DG_OK;
+}
+
+}  // namespace
+
+extern "C" int es_dg_integrals_noalloc(const es_dg_mesh* mesh, int N, const es_dg_physics* physics,
+                                       const double* q, const double* J, const double* x,
+                                       double* out3, void* cuda_stream) {
+  if (!mesh || !q || !J || !x || !out3 || N < 1 || N > 7) return ES_DG_EINVAL;
+  if (mesh->kx < 1 || mesh->ky < 1 || mesh->kz < 1) return ES_DG_EINVAL;
+  const long long E = (long long)mesh->kx * mesh->ky * mesh->kz;
+  if (E > ES_DG_NOALLOC_MAX_ELEMS) return ES_DG_EINVAL;  // beyond the static scratch
+  EsdgGrid g{};
+  g.K[0] = mesh->kx;
+  g.K[1] = mesh->ky;
+  g.K[2] = mesh->kz;
+  g.N = N;
+  g.Nq = N + 1;
+  g.np = g.Nq * g.Nq * g.Nq;
+  g.E = (int)E;
+  EsdgLGL L;
+  if (esdg_lgl_build(N, &L)) return ES_DG_EINVAL;
+  EsdgPhys P{1.4, 9.81, 287.0, 1.0e5, 0.0, 0.0, 0.0, 1};
+  if (physics) {
+    P.gamma = physics->gamma;
+    P.g = physics->g;
+    P.R = physics->R;
+    P.p0 = physics->p0;
+    P.f0 = physics->f0;
+    P.beta = physics->beta;
+    P.y0 = physics->y0;
+    P.dissipation = physics->dissipation;
+  }
+  double* scratch = nullptr;
+  int st = noalloc_scratch(&scratch);
+  if (st) return st;
+  // every partial the fold reads (the first E triples) is written by this
+  // call, so nothing needs clearing between calls
+  cudaError_t e = esdg_launch_integrals(g, L, P, q, J, x, scratch, out3, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ES_DG_ENOMEM : ES_DG_ECUDA;
+  return ES_DG_OK;
+}
