@@ -133,7 +133,8 @@ def run_gpu_arm(args, rank, world, dist):
     stream = torch.cuda.current_stream()
     results = {}
     sampler = None
-    for prec in ("fp64", "mixed"):
+    precs = ("fp64", "mixed") if args.precision == "both" else (args.precision,)
+    for prec in precs:
         s = _lib.Solver(*w["K"], w["N"], lo=w["lo"], hi=w["hi"], periodic=w["periodic"],
                         warp=w["warp"], precision=prec, stream=stream)
         info = s.info()
@@ -150,7 +151,7 @@ def run_gpu_arm(args, rank, world, dist):
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)]
               for _ in range(5 * args.steps)]
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if prec == "fp64":
+        if prec == precs[0]:
             sampler = ClockSampler(local)
             time.sleep(0.3)
         t0.record(stream)
@@ -165,7 +166,7 @@ def run_gpu_arm(args, rank, world, dist):
                 k += 1
         t1.record(stream)
         torch.cuda.synchronize()
-        clocks = sampler.stop() if prec == "fp64" else None
+        clocks = sampler.stop() if prec == precs[0] else None
         ms = t0.elapsed_time(t1)
         t_face = sum(e[0].elapsed_time(e[1]) for e in ev) / len(ev)
         t_vol = sum(e[1].elapsed_time(e[2]) for e in ev) / len(ev)
@@ -249,7 +250,19 @@ def main_ours(args):
         import torch.distributed as dist_mod
         dist_mod.init_process_group("nccl")
         dist = dist_mod
+    if args.K:
+        WORKLOAD["K"] = (args.K, args.K, args.K)
     res = run_gpu_arm(args, rank, world, dist)
+    if args.precision != "both":
+        # single-precision small cases (profiling runs): short report only
+        if rank == 0:
+            r = res[args.precision]
+            print(json.dumps({"precision": args.precision, "K": WORKLOAD["K"],
+                              "ms_per_step": r["ms"] / args.steps, "ms_interface": r["t_face"],
+                              "ms_volume": r["t_vol"], "finite": r["finite"]}))
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -336,6 +349,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--K", type=int, default=0, help="elements per direction (small profiling cases)")
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -115,6 +115,20 @@ int es_dg_init_bubble(es_dg_t* h, double theta0, double amp, const double centre
  * plus a 1 m/s Gaussian wind perturbation; see the oracle for the formulas). */
 int es_dg_init_channel(es_dg_t* h);
 
+/* Hydrostatic background of the mixed-precision path (the perturbation-variable
+ * formulation the paper suggests for 32-bit runs, Section 5.2).  From q_bg the
+ * library keeps rho_bg and b_bg = rho/(2p) and evaluates, once and in FP64, the
+ * right-hand side of the same state at rest, (rho_bg, 0, p_bg/(gamma-1) + rho_bg phi).
+ * Every later mixed-precision evaluation computes rhs(q) = rhs(q_bg at rest) +
+ * [rhs(q) - rhs(q_bg at rest)], the bracket in FP32 with the pressure and gravity
+ * differences formed exactly in perturbation variables, so FP32 rounding is
+ * relative to the perturbation.  In exact arithmetic the result is unchanged.
+ * es_dg_init_bubble sets the unperturbed atmosphere and es_dg_init_channel the
+ * channel state at rest as background automatically.  No effect in FP64 mode.
+ * Synchronous when on_device = 0.  es_dg_clear_background returns to plain FP32. */
+int es_dg_set_background(es_dg_t* h, const double* q_bg, int on_device);
+int es_dg_clear_background(es_dg_t* h);
+
 /* One evaluation of the right-hand side dq/dt of Eq. (nm:semi) at state q
  * (not the handle's state), written to rhs.  Both pointers host or both device
  * per on_device.  Synchronous when on_device = 0. */

@@ -61,6 +61,8 @@ SIGNATURES = {
     "es_dg_init_bubble": (C.c_int, [_VP, C.c_double, C.c_double, _DP, C.c_double]),
     "es_dg_init_channel": (C.c_int, [_VP]),
     "es_dg_rhs": (C.c_int, [_VP, _VP, _VP, C.c_int]),
+    "es_dg_set_background": (C.c_int, [_VP, _VP, C.c_int]),
+    "es_dg_clear_background": (C.c_int, [_VP]),
     "es_dg_cfl_dt": (C.c_int, [_VP, C.c_double, _DP]),
     "es_dg_step": (C.c_int, [_VP, C.c_double, C.c_int]),
     "es_dg_sync": (C.c_int, [_VP]),
@@ -209,6 +211,13 @@ class Solver:
 
     def init_channel(self):
         check(self.lib.es_dg_init_channel(self.h), "es_dg_init_channel")
+
+    def set_background(self, q_bg):
+        check(self.lib.es_dg_set_background(self.h, C.c_void_p(_ptr(q_bg)), _on_device(q_bg)),
+              "es_dg_set_background")
+
+    def clear_background(self):
+        check(self.lib.es_dg_clear_background(self.h), "es_dg_clear_background")
 
     def rhs(self, q, out=None):
         if out is None:

@@ -40,6 +40,11 @@ struct es_dg {
   double* qtmp;     // lazily allocated
   double* scratch;  // reductions
   double* result;   // small device result slots (4 doubles)
+  // mixed precision relative to a hydrostatic background
+  int has_bg;
+  double* bg;       // [E][3][np] rho_bg, b_bg, p_bg
+  double* rhs_bg;   // [E][3][np] FP64 momentum right-hand side of the background at rest
+  double* fflux64;  // FP64 face fluxes for evaluating that right-hand side
 };
 
 namespace {
@@ -120,6 +125,8 @@ EsdgVolArgs vol_args(es_dg_t* h, const double* q_in, double* rhs_out) {
   a.vgeo64 = h->vgeo;
   a.fflux = h->fflux;
   a.x = h->x;
+  a.bg = (h->mixed && h->has_bg) ? h->bg : nullptr;
+  a.rhs_bg = h->rhs_bg;
   a.rkA = 0.0;
   a.rkB = 0.0;
   a.dt = 0.0;
@@ -129,7 +136,8 @@ EsdgVolArgs vol_args(es_dg_t* h, const double* q_in, double* rhs_out) {
 // face fluxes then volume (+ lift, source, optional RK update) for state q_in
 int launch_stage(es_dg_t* h, const double* q_in, int mode, double* rhs_out, double A, double B,
                  double dt) {
-  cudaError_t e = esdg_launch_face(h->g, h->P, h->mixed, q_in, h->fgeo, h->fflux, h->stream);
+  cudaError_t e = esdg_launch_face(h->g, h->P, h->mixed, q_in, h->fgeo, h->fflux, h->stream,
+                                   (h->mixed && h->has_bg) ? h->bg : nullptr);
   if (e != cudaSuccess) return cuda_status(e);
   EsdgVolArgs a = vol_args(h, q_in, rhs_out);
   a.rkA = A;
@@ -137,6 +145,37 @@ int launch_stage(es_dg_t* h, const double* q_in, int mode, double* rhs_out, doub
   a.dt = dt;
   e = esdg_launch_volume(h->g, h->L, h->P, h->mixed, mode, a, h->stream);
   return cuda_status(e);
+}
+
+// Set the mixed path's hydrostatic background from state q_dev (device): store
+// rho_bg and b_bg, and evaluate the right-hand side of the background at rest
+// once with the FP64 kernels.
+int set_background_dev(es_dg_t* h, const double* q_dev) {
+  const size_t E = h->g.E, np = h->g.np, nf2 = (size_t)h->g.Nq * h->g.Nq;
+  int st = ensure_rhs_buffers(h);
+  if (!st && !h->bg) st = dev_alloc(h, (void**)&h->bg, E * 3 * np * sizeof(double));
+  if (!st && !h->rhs_bg) st = dev_alloc(h, (void**)&h->rhs_bg, E * 3 * np * sizeof(double));
+  if (!st && !h->fflux64)
+    st = dev_alloc(h, (void**)&h->fflux64, (size_t)h->g.nfaces * 5 * nf2 * sizeof(double));
+  if (st) return st;
+  double* q0 = h->qtmp;
+  if (q_dev == q0) return ES_DG_EINVAL;
+  cudaError_t e = esdg_launch_background(h->g, h->P, h->vgeo, q_dev, h->bg, q0, h->stream);
+  if (e == cudaSuccess) e = esdg_launch_face(h->g, h->P, 0, q0, h->fgeo, h->fflux64, h->stream);
+  if (e == cudaSuccess) {
+    EsdgVolArgs a = vol_args(h, q0, h->rhs);
+    a.vgeo = h->vgeo;
+    a.fflux = h->fflux64;
+    a.bg = nullptr;
+    e = esdg_launch_volume(h->g, h->L, h->P, 0, 0, a, h->stream);
+  }
+  // momentum components: rhs[e][1..3][n] -> rhs_bg[e][0..2][n]
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(h->rhs_bg, 3 * np * sizeof(double), h->rhs + np, 5 * np * sizeof(double),
+                          3 * np * sizeof(double), E, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  h->has_bg = 1;
+  return ES_DG_OK;
 }
 
 }  // namespace
@@ -176,8 +215,9 @@ int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,
       return ES_DG_EINVAL;
     }
   } else {
-    h->P = EsdgPhys{1.4, 9.81, 287.0, 1.0e5, 0.0, 0.0, 0.0, 1};
+    h->P = EsdgPhys{1.4, 9.81, 287.0, 1.0e5, 0.0, 0.0, 0.0, 1, 0.0, 0.0};
   }
+  esdg_phys_derive(&h->P);
   {
     // gravity acts along z: a z-periodic box would make phi = g z jump across
     // the periodic faces, which the balance law does not allow
@@ -269,14 +309,51 @@ int es_dg_get_state(es_dg_t* h, double* q, int on_device) {
 int es_dg_init_bubble(es_dg_t* h, double theta0, double amp, const double centre[3],
                       double radius) {
   if (!h || !centre || !(theta0 > 0.0) || !(radius > 0.0)) return ES_DG_EINVAL;
-  return cuda_status(
-      esdg_launch_bubble(h->g, h->P, h->x, theta0, amp, centre, radius, h->q, h->stream));
+  cudaError_t e;
+  if (h->mixed) {
+    // the unperturbed isentropic atmosphere is the mixed path's background
+    int st = ensure_rhs_buffers(h);
+    if (st) return st;
+    e = esdg_launch_bubble(h->g, h->P, h->x, theta0, 0.0, centre, radius, h->q, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemcpyAsync(h->rhs, h->q, (size_t)h->g.E * 5 * h->g.np * sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    st = set_background_dev(h, h->rhs);
+    if (st) return st;
+  }
+  e = esdg_launch_bubble(h->g, h->P, h->x, theta0, amp, centre, radius, h->q, h->stream);
+  return cuda_status(e);
 }
 
 int es_dg_init_channel(es_dg_t* h) {
   if (!h) return ES_DG_EINVAL;
   if (h->P.f0 == 0.0 && h->P.beta == 0.0) return ES_DG_EINVAL;  // geostrophic balance needs f
-  return cuda_status(esdg_launch_channel(h->g, h->P, h->x, h->q, h->stream));
+  cudaError_t e = esdg_launch_channel(h->g, h->P, h->x, h->q, h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (h->mixed) return set_background_dev(h, h->q);  // the jump-free state at rest
+  return ES_DG_OK;
+}
+
+int es_dg_set_background(es_dg_t* h, const double* q_bg, int on_device) {
+  if (!h || !q_bg) return ES_DG_EINVAL;
+  if (!h->mixed) return ES_DG_OK;  // the FP64 path needs no background
+  const size_t bytes = (size_t)h->g.E * 5 * h->g.np * sizeof(double);
+  int st = ensure_rhs_buffers(h);
+  if (st) return st;
+  // stage the input in the rhs buffer (the background's own evaluation uses qtmp)
+  cudaError_t e = cudaMemcpyAsync(h->rhs, q_bg, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                                 : cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  st = set_background_dev(h, h->rhs);
+  if (!st && !on_device) st = cuda_status(cudaStreamSynchronize(h->stream));
+  return st;
+}
+
+int es_dg_clear_background(es_dg_t* h) {
+  if (!h) return ES_DG_EINVAL;
+  h->has_bg = 0;
+  return ES_DG_OK;
 }
 
 int es_dg_rhs(es_dg_t* h, const double* q, double* rhs, int on_device) {
@@ -354,7 +431,8 @@ int es_dg_geometry(es_dg_t* h, double* x, double* J, double* Ja, int on_device) 
 int es_dg_launch(es_dg_t* h, int which, int stage, double dt) {
   if (!h || stage < 0 || stage > 4) return ES_DG_EINVAL;
   if (which == 0)
-    return cuda_status(esdg_launch_face(h->g, h->P, h->mixed, h->q, h->fgeo, h->fflux, h->stream));
+    return cuda_status(esdg_launch_face(h->g, h->P, h->mixed, h->q, h->fgeo, h->fflux, h->stream,
+                                        (h->mixed && h->has_bg) ? h->bg : nullptr));
   if (which == 1) {
     int st = ensure_rhs_buffers(h);
     if (st) return st;

@@ -32,7 +32,12 @@ struct EsdgLGL {  // LGL operators, passed by value (lives in the constant bank)
 struct EsdgPhys {
   double gamma, g, R, p0, f0, beta, y0;
   int dissipation;
+  double igm1, igamma;  // 1/(gamma-1) and 1/gamma, set by esdg_phys_derive on the host
 };
+inline void esdg_phys_derive(EsdgPhys* P) {
+  P->igm1 = 1.0 / (P->gamma - 1.0);
+  P->igamma = 1.0 / P->gamma;
+}
 
 struct EsdgGrid {  // structured box and derived face numbering
   int K[3];
@@ -61,30 +66,53 @@ __host__ __device__ inline long long esdg_face_id(const EsdgGrid& g, int d, int 
 }
 
 #ifdef __CUDACC__
-// Reciprocal in FP64 by Newton-Raphson refinement of an FP32 seed.  With
-// e = 1 - x r0 the update r0 (1 + e + e^2) is the cubically convergent
-// (Householder order-2) step for f(r) = 1/r - x; from the ~2^-23 seed of
-// rcp.approx.f32 the truncation error e^3 is below 2^-66, so the result is
-// within one rounding of 1/x.  Valid for |x| in the normal FP32 range.
+// Reciprocal in FP64 from the hardware approximation rcp.approx.ftz.f64
+// (MUFU; relative error below 2^-19.9, measured on this GPU over 1M values)
+// refined by one cubically convergent step: with e = 1 - x r0 the update
+// r0 (1 + e + e^2) is the order-2 Householder step for f(r) = 1/r - x, leaving
+// a truncation error e^3 < 2^-59, i.e. the result is within about one rounding
+// of 1/x.  Three DFMA on the FP64 pipe; the seed runs on the MUFU pipe.
 __device__ __forceinline__ double esdg_rcp(double x) {
-  float xf = __double2float_rn(x);
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
-  double r = (double)rf;
-  double e = fma(-x, r, 1.0);
-  double t = fma(e, e, e);
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double e = fma(-x, r, 1.0);
+  const double t = fma(e, e, e);
   return fma(r, t, r);
 }
 
-// Same with a single Newton step (relative error ~2^-46); used only where the
-// result feeds a small correction term.
+// Same seed with a single Newton step (relative error ~2^-39); used only where
+// the result feeds a small correction term.
 __device__ __forceinline__ double esdg_rcp_lo(double x) {
-  float xf = __double2float_rn(x);
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
-  double r = (double)rf;
-  double e = fma(-x, r, 1.0);
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double e = fma(-x, r, 1.0);
   return fma(r, e, r);
+}
+
+// IEEE-754 double <-> float repacking with integer instructions (normal
+// numbers; round to nearest even; magnitudes below the float range flush to
+// zero).  cvt.f32.f64 and cvt.f64.f32 occupy the FP64 pipe on this GPU, which
+// is the bottleneck of the FP64 kernels; these run on the integer pipes and
+// agree bit for bit with cvt.rn on normal inputs (checked on 1M random values).
+__device__ __forceinline__ float esdg_d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  unsigned f = (hi & 0x80000000u) | ((unsigned)e << 23) | m;
+  f += (rest > 0x10000000u) | ((rest == 0x10000000u) & (f & 1u));
+  return (e <= 0) ? 0.0f : __uint_as_float(f);
+}
+__device__ __forceinline__ double esdg_f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
+  return (e == 0) ? 0.0 : __longlong_as_double((long long)(((unsigned long long)hi << 32) | (m << 29)));
+}
+// x < y for non-negative doubles, compared as integers (no FP64-pipe compare)
+__device__ __forceinline__ bool esdg_lt_pos(double x, double y) {
+  return __double_as_longlong(x) < __double_as_longlong(y);
 }
 
 __device__ __forceinline__ float esdg_rcpf(float x) {
@@ -131,8 +159,11 @@ cudaError_t esdg_launch_bubble(const EsdgGrid& g, const EsdgPhys& P, const doubl
                                cudaStream_t s);
 cudaError_t esdg_launch_channel(const EsdgGrid& g, const EsdgPhys& P, const double* x, double* q,
                                 cudaStream_t s);
+cudaError_t esdg_launch_background(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
+                                   const double* q, double* bg, double* q0, cudaStream_t s);
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
-                             const double* fgeo, void* fflux, cudaStream_t s);
+                             const double* fgeo, void* fflux, cudaStream_t s,
+                             const double* bg = nullptr);
 // mode 0: write rhs; mode 1: fused LSRK stage (dq, q updated in place)
 struct EsdgVolArgs {
   const double* q_in;    // state read by the prologue and the source term
@@ -143,6 +174,8 @@ struct EsdgVolArgs {
   const double* vgeo64;  // [E][11][np] double (geopotential for the pressure recovery)
   const void* fflux;     // face fluxes, double or float
   const double* x;       // coordinates (Coriolis parameter)
+  const double* bg;      // mixed mode with a background: [E][3][np] rho_bg, b_bg, p_bg (else null)
+  const double* rhs_bg;  // mixed mode with a background: [E][3][np] FP64 momentum rhs of it
   double rkA, rkB, dt;
 };
 cudaError_t esdg_launch_volume_f64(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P, int mode,

@@ -218,7 +218,41 @@ __global__ void k_channel(EsdgGrid g, EsdgPhys P, const double* __restrict__ x,
   qe[4 * np + n] = p / (P.gamma - 1.0) + 0.5 * rho * u * u + rho * P.g * Z;
 }
 
+// Background of the mixed-precision path: rho_bg, b_bg = rho/(2p) and p_bg of a
+// given state, and the same state at rest, (rho, 0, 0, 0, p/(gamma-1) + rho phi).
+__global__ void k_background(EsdgGrid g, EsdgPhys P, const double* __restrict__ vgeo,
+                             const double* __restrict__ q, double* __restrict__ bg,
+                             double* __restrict__ q0) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int np = g.np;
+  if (tid >= (long long)g.E * np) return;
+  const long long e = tid / np;
+  const int n = (int)(tid - e * np);
+  const double* qe = q + e * 5 * np;
+  const double phi = vgeo[(e * ESDG_NVGEO + 10) * np + n];
+  const double rho = qe[n];
+  const double ke = 0.5 * (qe[np + n] * qe[np + n] + qe[2 * np + n] * qe[2 * np + n] +
+                           qe[3 * np + n] * qe[3 * np + n]) / rho;
+  const double p = (P.gamma - 1.0) * (qe[4 * np + n] - ke - rho * phi);
+  bg[(e * 3 + 0) * np + n] = rho;
+  bg[(e * 3 + 1) * np + n] = rho / (2.0 * p);
+  bg[(e * 3 + 2) * np + n] = p;
+  double* o = q0 + e * 5 * np;
+  o[n] = rho;
+  o[np + n] = 0.0;
+  o[2 * np + n] = 0.0;
+  o[3 * np + n] = 0.0;
+  o[4 * np + n] = p / (P.gamma - 1.0) + rho * phi;
+}
+
 }  // namespace
+
+cudaError_t esdg_launch_background(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
+                                   const double* q, double* bg, double* q0, cudaStream_t s) {
+  const long long nt = (long long)g.E * g.np;
+  k_background<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, P, vgeo, q, bg, q0);
+  return cudaGetLastError();
+}
 
 cudaError_t esdg_launch_geometry(const EsdgGrid& g, const EsdgLGL& L, double* x, double* J,
                                  double* Ja, double* vgeo, float* vgeo32, double* fgeo,

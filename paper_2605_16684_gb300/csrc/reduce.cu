@@ -195,7 +195,7 @@ extern "C" int es_dg_integrals_noalloc(const es_dg_mesh* mesh, int N, const es_d
   g.E = (int)E;
   EsdgLGL L;
   if (esdg_lgl_build(N, &L)) return ES_DG_EINVAL;
-  EsdgPhys P{1.4, 9.81, 287.0, 1.0e5, 0.0, 0.0, 0.0, 1};
+  EsdgPhys P{1.4, 9.81, 287.0, 1.0e5, 0.0, 0.0, 0.0, 1, 0.0, 0.0};
   if (physics) {
     P.gamma = physics->gamma;
     P.g = physics->g;
@@ -206,6 +206,7 @@ extern "C" int es_dg_integrals_noalloc(const es_dg_mesh* mesh, int N, const es_d
     P.y0 = physics->y0;
     P.dissipation = physics->dissipation;
   }
+  esdg_phys_derive(&P);
   double* scratch = nullptr;
   int st = noalloc_scratch(&scratch);
   if (st) return st;

@@ -25,7 +25,7 @@ struct FaceMath<double> {
   static __device__ __forceinline__ double rcp(double x) { return esdg_rcp(x); }
   static __device__ __forceinline__ double A(double u) { return esdg_A(u); }
   static __device__ __forceinline__ double Q(double u) { return esdg_Q(u); }
-  static __device__ __forceinline__ bool small(double u) { return (float)u < (float)ESDG_LOG_EPS; }
+  static __device__ __forceinline__ bool small(double u) { return esdg_lt_pos(u, ESDG_LOG_EPS); }
   // ln(p/m) by per-side logarithms (the log branch of the log mean)
   static __device__ __forceinline__ double ljump(double p, double m, double diff) {
     return log(p) - log(m);
@@ -46,6 +46,13 @@ struct FaceMath<float> {
   static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
 };
 
+// double -> R without the FP64-pipe conversion instruction
+template <typename R>
+__device__ __forceinline__ R to_r(double x) {
+  if constexpr (sizeof(R) == sizeof(float)) return esdg_d2f(x);
+  else return x;
+}
+
 template <typename R>
 struct Side {
   R rho, u0, u1, u2, b;
@@ -64,17 +71,25 @@ __device__ __forceinline__ Side<R> side_from(const double* q, double phi, double
   e = fma(-0.5 * q[3], u2, e);
   const double p = gm1 * e;
   Side<R> s;
-  s.rho = (R)rho;
-  s.u0 = (R)u0;
-  s.u1 = (R)u1;
-  s.u2 = (R)u2;
-  s.b = (R)(0.5 * rho * esdg_rcp(p));
+  if constexpr (sizeof(R) == sizeof(float)) {
+    s.rho = esdg_d2f(rho);
+    s.u0 = esdg_d2f(u0);
+    s.u1 = esdg_d2f(u1);
+    s.u2 = esdg_d2f(u2);
+    s.b = esdg_d2f(0.5 * rho * esdg_rcp(p));
+  } else {
+    s.rho = rho;
+    s.u0 = u0;
+    s.u1 = u1;
+    s.u2 = u2;
+    s.b = 0.5 * rho * esdg_rcp(p);
+  }
   return s;
 }
 
 template <typename R>
 __device__ __forceinline__ void face_flux(const Side<R>& M, const Side<R>& Pp, R phi, R n0, R n1,
-                                          R n2, R gamma, int dissipation, R* F) {
+                                          R n2, R gamma, R igm1, R igamma, int dissipation, R* F) {
   using Mth = FaceMath<R>;
   const R gm1 = gamma - (R)1;
   const R half = (R)0.5;
@@ -110,12 +125,12 @@ __device__ __forceinline__ void face_flux(const Side<R>& M, const Side<R>& Pp, R
   F[1] = Fr * u0 + pt * n0;
   F[2] = Fr * u1 + pt * n1;
   F[3] = Fr * u2 + pt * n2;
-  F[4] = Fr * (iblog / ((R)2 * gm1) + half * uu + phi) + pt * un;
+  F[4] = Fr * (iblog * half * igm1 + half * uu + phi) + pt * un;
   if (!dissipation) return;
   // entropy-variable jumps
   const R bu2m = M.b * (M.u0 * M.u0 + M.u1 * M.u1 + M.u2 * M.u2);
   const R bu2p = Pp.b * (Pp.u0 * Pp.u0 + Pp.u1 * Pp.u1 + Pp.u2 * Pp.u2);
-  const R jv1 = lnr_jump + lnb_jump / gm1 - (bu2p - bu2m) + (R)2 * phi * db;
+  const R jv1 = lnr_jump + lnb_jump * igm1 - (bu2p - bu2m) + (R)2 * phi * db;
   const R jm0 = (R)2 * (Pp.b * Pp.u0 - M.b * M.u0);
   const R jm1 = (R)2 * (Pp.b * Pp.u1 - M.b * M.u1);
   const R jm2 = (R)2 * (Pp.b * Pp.u2 - M.b * M.u2);
@@ -126,13 +141,14 @@ __device__ __forceinline__ void face_flux(const Side<R>& M, const Side<R>& Pp, R
   const R a2 = gamma * pt * irh;
   const R a = Mth::sq(a2);
   const R k2 = half * (u0 * u0 + u1 * u1 + u2 * u2) + phi;
-  const R H = a2 / gm1 + k2;
+  const R a2g = a2 * igm1;
+  const R H = a2g + k2;
   const R njm = n0 * jm0 + n1 * jm1 + n2 * jm2;
   const R w2 = jv1 + u0 * jm0 + u1 * jm1 + u2 * jm2 + k2 * jv5;
-  const R ac = a2 / gm1 * jv5;
+  const R ac = a2g * jv5;
   const R w1 = w2 - a * njm + ac - a * un * jv5;
   const R w5 = w2 + a * njm + ac + a * un * jv5;
-  const R ig = (R)1 / gamma;
+  const R ig = igamma;
   const R c1 = fabs(un - a) * rho_log * half * ig * w1;
   const R c2 = fabs(un) * rho_log * gm1 * ig * w2;
   const R c5 = fabs(un + a) * rho_log * half * ig * w5;
@@ -154,10 +170,105 @@ __device__ __forceinline__ void face_flux(const Side<R>& M, const Side<R>& Pp, R
   F[4] -= half * dE;
 }
 
-template <typename R, int N>
+// Mixed precision relative to a hydrostatic background (u_bg = 0, continuous
+// across faces): the face flux's background part is the Euler flux
+// (0, p_bg nhat, 0), so the kernel stores F* - (0, p_bg nhat, 0).  Its momentum
+// pressure p* - p_bg and the jumps feeding the dissipation ([[rho]], [[b]],
+// [[b u]], [[b |u|^2]]) come in from FP64 differences, so FP32 rounding is
+// relative to the perturbations and jumps, not to the state.
+struct BgFace {
+  float dr, db, dbu0, dbu1, dbu2, dbuu, ptp;
+};
+
+__device__ __forceinline__ void face_flux_bg(const Side<float>& M, const Side<float>& Pp, float phi,
+                                             float n0, float n1, float n2, float gamma, float igm1,
+                                             float igamma, int dissipation, const BgFace& J,
+                                             float* F) {
+  using Mth = FaceMath<float>;
+  const float gm1 = gamma - 1.0f;
+  const float half = 0.5f;
+  const float sr = Pp.rho + M.rho, dr = J.dr;
+  const float sb = Pp.b + M.b, db = J.db;
+  const float rsr = Mth::rcp(sr), rsb = Mth::rcp(sb);
+  const float fr = dr * rsr, ur = fr * fr;
+  const float fb = db * rsb, ub = fb * fb;
+  float rho_log, lnr_jump, iblog, lnb_jump;
+  if (Mth::small(ur)) {
+    rho_log = half * sr * Mth::Q(ur);
+    lnr_jump = 2.0f * fr * Mth::A(ur);
+  } else {
+    lnr_jump = Mth::ljump(Pp.rho, M.rho, dr);
+    rho_log = dr / lnr_jump;
+  }
+  if (Mth::small(ub)) {
+    const float Ab = Mth::A(ub);
+    iblog = 2.0f * rsb * Ab;
+    lnb_jump = 2.0f * fb * Ab;
+  } else {
+    lnb_jump = Mth::ljump(Pp.b, M.b, db);
+    iblog = lnb_jump / db;
+  }
+  const float u0 = half * (M.u0 + Pp.u0), u1 = half * (M.u1 + Pp.u1), u2 = half * (M.u2 + Pp.u2);
+  const float un = u0 * n0 + u1 * n1 + u2 * n2;
+  const float pt = sr * rsb * half;
+  const float ptp = J.ptp;
+  const float uu = M.u0 * Pp.u0 + M.u1 * Pp.u1 + M.u2 * Pp.u2;
+  const float Fr = rho_log * un;
+  F[0] = Fr;
+  F[1] = Fr * u0 + ptp * n0;
+  F[2] = Fr * u1 + ptp * n1;
+  F[3] = Fr * u2 + ptp * n2;
+  F[4] = Fr * (iblog * half * igm1 + half * uu + phi) + pt * un;
+  if (!dissipation) return;
+  const float jv1 = lnr_jump + lnb_jump * igm1 - J.dbuu + 2.0f * phi * db;
+  const float jm0 = 2.0f * J.dbu0, jm1 = 2.0f * J.dbu1, jm2 = 2.0f * J.dbu2;
+  const float jv5 = -2.0f * db;
+  const float irh = Mth::small(ur) ? 2.0f * rsr * Mth::A(ur) : lnr_jump / dr;
+  const float a2 = gamma * pt * irh;
+  const float a = sqrtf(a2);
+  const float k2 = half * (u0 * u0 + u1 * u1 + u2 * u2) + phi;
+  const float a2g = a2 * igm1;
+  const float H = a2g + k2;
+  const float njm = n0 * jm0 + n1 * jm1 + n2 * jm2;
+  const float w2 = jv1 + u0 * jm0 + u1 * jm1 + u2 * jm2 + k2 * jv5;
+  const float ac = a2g * jv5;
+  const float w1 = w2 - a * njm + ac - a * un * jv5;
+  const float w5 = w2 + a * njm + ac + a * un * jv5;
+  const float c1 = fabsf(un - a) * rho_log * half * igamma * w1;
+  const float c2 = fabsf(un) * rho_log * gm1 * igamma * w2;
+  const float c5 = fabsf(un + a) * rho_log * half * igamma * w5;
+  const float ls = fabsf(un) * pt;
+  const float y0 = jm0 + u0 * jv5, y1 = jm1 + u1 * jv5, y2 = jm2 + u2 * jv5;
+  const float yn = y0 * n0 + y1 * n1 + y2 * n2;
+  const float t0 = y0 - yn * n0, t1 = y1 - yn * n1, t2 = y2 - yn * n2;
+  const float csum = c1 + c2 + c5, cdif = c5 - c1;
+  F[0] -= half * csum;
+  F[1] -= half * (csum * u0 + a * cdif * n0 + ls * t0);
+  F[2] -= half * (csum * u1 + a * cdif * n1 + ls * t1);
+  F[3] -= half * (csum * u2 + a * cdif * n2 + ls * t2);
+  F[4] -= half * ((c1 + c5) * H + a * un * cdif + c2 * k2 + ls * (u0 * t0 + u1 * t1 + u2 * t2));
+}
+
+// FP64 primitives of one side
+struct Side64 {
+  double rho, u0, u1, u2, b;
+};
+__device__ __forceinline__ Side64 side64(const double* q, double phi, double gm1) {
+  const double rho = q[0];
+  const double ir = esdg_rcp(rho);
+  const double u0 = q[1] * ir, u1 = q[2] * ir, u2 = q[3] * ir;
+  double e = fma(-rho, phi, q[4]);
+  e = fma(-0.5 * q[1], u0, e);
+  e = fma(-0.5 * q[2], u1, e);
+  e = fma(-0.5 * q[3], u2, e);
+  return Side64{rho, u0, u1, u2, 0.5 * rho * esdg_rcp(gm1 * e)};
+}
+
+template <typename R, int N, bool BG>
 __global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const double* __restrict__ q,
                                               const double* __restrict__ fgeo,
-                                              R* __restrict__ fflux) {
+                                              R* __restrict__ fflux,
+                                              const double* __restrict__ bg) {
   constexpr int Nq = N + 1, NF2 = Nq * Nq, NP = Nq * Nq * Nq;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= g.nfaces * NF2) return;
@@ -214,29 +325,49 @@ __global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const doub
     dst[4] = src[4];
   }
   const double gm1 = P.gamma - 1.0;
-  const Side<R> M = side_from<R>(qm, phi, gm1), Pp = side_from<R>(qp, phi, gm1);
   R F[5];
-  face_flux<R>(M, Pp, (R)phi, (R)n0, (R)n1, (R)n2, (R)P.gamma, P.dissipation, F);
+  if constexpr (BG) {
+    const Side64 m = side64(qm, phi, gm1), p = side64(qp, phi, gm1);
+    const int eb = (em >= 0) ? em : ep, nb = (em >= 0) ? nm : npn;
+    const double pbg = bg[((size_t)eb * 3 + 2) * NP + nb];
+    BgFace J;
+    J.dr = esdg_d2f(p.rho - m.rho);
+    J.db = esdg_d2f(p.b - m.b);
+    J.dbu0 = esdg_d2f(p.b * p.u0 - m.b * m.u0);
+    J.dbu1 = esdg_d2f(p.b * p.u1 - m.b * m.u1);
+    J.dbu2 = esdg_d2f(p.b * p.u2 - m.b * m.u2);
+    J.dbuu = esdg_d2f(p.b * (p.u0 * p.u0 + p.u1 * p.u1 + p.u2 * p.u2) -
+                      m.b * (m.u0 * m.u0 + m.u1 * m.u1 + m.u2 * m.u2));
+    J.ptp = esdg_d2f(0.5 * (p.rho + m.rho) * esdg_rcp(p.b + m.b) - pbg);  // p* - p_bg
+    const Side<float> M{esdg_d2f(m.rho), esdg_d2f(m.u0), esdg_d2f(m.u1), esdg_d2f(m.u2), esdg_d2f(m.b)};
+    const Side<float> Pp{esdg_d2f(p.rho), esdg_d2f(p.u0), esdg_d2f(p.u1), esdg_d2f(p.u2), esdg_d2f(p.b)};
+    face_flux_bg(M, Pp, esdg_d2f(phi), esdg_d2f(n0), esdg_d2f(n1), esdg_d2f(n2), esdg_d2f(P.gamma),
+                 esdg_d2f(P.igm1), esdg_d2f(P.igamma), P.dissipation, J, F);
+  } else {
+    const Side<R> M = side_from<R>(qm, phi, gm1), Pp = side_from<R>(qp, phi, gm1);
+    face_flux<R>(M, Pp, to_r<R>(phi), to_r<R>(n0), to_r<R>(n1), to_r<R>(n2), to_r<R>(P.gamma),
+                 to_r<R>(P.igm1), to_r<R>(P.igamma), P.dissipation, F);
+  }
   R* out = fflux + (size_t)f * 5 * NF2;
-  const R sc = (R)scale;
+  const R sc = to_r<R>(scale);
 #pragma unroll
   for (int v = 0; v < 5; v++) out[v * NF2 + fn] = sc * F[v];
 }
 
-template <typename R>
+template <typename R, bool BG>
 cudaError_t launch_face_t(const EsdgGrid& g, const EsdgPhys& P, const double* q, const double* fgeo,
-                          R* fflux, cudaStream_t s) {
+                          R* fflux, const double* bg, cudaStream_t s) {
   const long long nt = g.nfaces * g.Nq * g.Nq;
   if (nt == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((nt + 255) / 256);
   switch (g.N) {
-    case 1: k_face<R, 1><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux); break;
-    case 2: k_face<R, 2><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux); break;
-    case 3: k_face<R, 3><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux); break;
-    case 4: k_face<R, 4><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux); break;
-    case 5: k_face<R, 5><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux); break;
-    case 6: k_face<R, 6><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux); break;
-    case 7: k_face<R, 7><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux); break;
+    case 1: k_face<R, 1, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
+    case 2: k_face<R, 2, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
+    case 3: k_face<R, 3, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
+    case 4: k_face<R, 4, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
+    case 5: k_face<R, 5, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
+    case 6: k_face<R, 6, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
+    case 7: k_face<R, 7, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -245,7 +376,8 @@ cudaError_t launch_face_t(const EsdgGrid& g, const EsdgPhys& P, const double* q,
 }  // namespace
 
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
-                             const double* fgeo, void* fflux, cudaStream_t s) {
-  if (mixed) return launch_face_t<float>(g, P, q, fgeo, (float*)fflux, s);
-  return launch_face_t<double>(g, P, q, fgeo, (double*)fflux, s);
+                             const double* fgeo, void* fflux, cudaStream_t s, const double* bg) {
+  if (mixed && bg) return launch_face_t<float, true>(g, P, q, fgeo, (float*)fflux, bg, s);
+  if (mixed) return launch_face_t<float, false>(g, P, q, fgeo, (float*)fflux, nullptr, s);
+  return launch_face_t<double, false>(g, P, q, fgeo, (double*)fflux, nullptr, s);
 }

@@ -54,16 +54,18 @@ template <> struct Cfg<5, true> { static constexpr int EPB = 3; };
 template <> struct Cfg<6, true> { static constexpr int EPB = 2; };
 template <> struct Cfg<7, true> { static constexpr int EPB = 2; };
 
-template <int N, bool MIXED>
+template <int N, bool MIXED, bool BG = false>
 struct Shape {
   static constexpr int Nq = N + 1, NP = Nq * Nq * Nq, NPEN = Nq * Nq;
   static constexpr int EPB = Cfg<N, MIXED>::EPB;
   static constexpr int PENCILS = 3 * NPEN * EPB;
   static constexpr int THREADS = ((PENCILS + 31) / 32) * 32;
-  // node fields: rq=rho/4, bh=b/2, ib=1/b, uh=u/2 (3), ph=phi/2, [lr, lb], nh=Ja/2 (9)
+  // node fields: rq=rho/4, bh=b/2, ib=1/b, uh=u/2 (3), ph=phi/2, [lr, lb], nh=Ja/2 (9),
+  // [background: rq'=rho'/4, bh'=b'/2, rq_bg, bh_bg, 1/b_bg, p_bg, p'=p-p_bg]
   static constexpr int F_LR = 7, F_LB = 8;
   static constexpr int F_NH = MIXED ? 7 : 9;
-  static constexpr int NF = F_NH + 9;
+  static constexpr int F_BG = F_NH + 9;
+  static constexpr int NF = F_NH + 9 + (BG ? 7 : 0);
   using R = typename std::conditional<MIXED, float, double>::type;
   static constexpr size_t SMEM = sizeof(R) * (size_t)NF * NP * EPB;
 };
@@ -71,9 +73,10 @@ struct Shape {
 template <typename R>
 struct Node {
   R rq, bh, ib, u0, u1, u2, ph, n0, n1, n2, lr, lb;
+  R rqp, bhp, rqb, bhb, ibb, pb, pp;  // perturbation and background (mixed mode with a background)
 };
 
-template <typename R, bool LOGS, int F_NH, int NP>
+template <typename R, bool LOGS, int F_NH, int NP, bool BG = false>
 __device__ __forceinline__ Node<R> load_node(const R* __restrict__ S, int n, int d) {
   Node<R> a;
   a.rq = S[0 * NP + n];
@@ -87,11 +90,21 @@ __device__ __forceinline__ Node<R> load_node(const R* __restrict__ S, int n, int
   a.n0 = nh[0 * NP + n];
   a.n1 = nh[1 * NP + n];
   a.n2 = nh[2 * NP + n];
-  if (LOGS) {
+  if (LOGS && F_NH == 9) {
     a.lr = S[7 * NP + n];
     a.lb = S[8 * NP + n];
   } else {
     a.lr = a.lb = (R)0;
+  }
+  if (BG) {
+    const R* b = S + (F_NH + 9) * NP;
+    a.rqp = b[0 * NP + n];
+    a.bhp = b[1 * NP + n];
+    a.rqb = b[2 * NP + n];
+    a.bhb = b[3 * NP + n];
+    a.ibb = b[4 * NP + n];
+    a.pb = b[5 * NP + n];
+    a.pp = b[6 * NP + n];
   }
   return a;
 }
@@ -113,9 +126,9 @@ __device__ __forceinline__ void pair64(const Node<double>& A, const Node<double>
     rlog = sr * esdg_Q2(ur);     // <rho>_log
     iblog = rsb * esdg_A(ub);    // 1/<b>_log
   } else {
-    if ((float)ur < (float)ESDG_LOG_EPS) rlog = sr * esdg_Q2(ur);
+    if (esdg_lt_pos(ur, ESDG_LOG_EPS)) rlog = sr * esdg_Q2(ur);
     else rlog = (4.0 * dr) * esdg_rcp(A.lr - B.lr);
-    if ((float)ub < (float)ESDG_LOG_EPS) iblog = rsb * esdg_A(ub);
+    if (esdg_lt_pos(ub, ESDG_LOG_EPS)) iblog = rsb * esdg_A(ub);
     else iblog = (A.lb - B.lb) * esdg_rcp(2.0 * db);
   }
   const double n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;  // {{Ja^d}}
@@ -188,21 +201,118 @@ __device__ __forceinline__ void pair32(const Node<float>& A, const Node<float>& 
   al[4] = fmaf(dli, FE, al[4]);
 }
 
-template <int N, bool MIXED, bool LOGS>
-__device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED>::R* __restrict__ S,
+// The FP32 pair relative to a hydrostatic background (u_bg = 0): the
+// momentum flux's pressure and gravity parts are formed as exact differences
+// H - H_bg in perturbation variables rho' = rho - rho_bg, b' = b - b_bg, so
+// their FP32 rounding is relative to the perturbation, not to the hydrostatic
+// pressure (the background's own FP64 right-hand side is added in the
+// epilogue).  The pressure mean is rewritten exactly as
+//   p* = {{rho}}/(2{{b}}) = {{p}} + T,  T = (p_i - p_l)(rho_i p_l - rho_l p_i) / (2 D),
+//   D = rho_i p_l + rho_l p_i,
+// so p* - p*_bg = {{p'}} + T - T_bg with p' = p - p_bg exact from the FP64
+// prologue and T - T_bg expanded into terms that each carry a perturbation
+// factor.  With sums over the pair (sr = rq_i + rq_l etc.):
+//   <rho>_log - <rho_bg>_log = sr' Q2(u) + sr_bg (u - u_bg) S2(u, u_bg),
+//     u - u_bg = (f - f_bg)(f + f_bg), f - f_bg = 2 (rq'_i rq_bg,l - rq'_l rq_bg,i)/(sr sr_bg),
+//     S2 the divided difference of the Q2 polynomial,
+//   {{b}}/b_i - {{b_bg}}/b_bg,i = 2 (bh'_l bh_bg,i - bh_bg,l bh'_i) / (b_i b_bg,i),
+// and the gravity difference follows by the product rule.  Density and energy
+// fluxes carry no background part (u_bg = 0) and are unchanged.
+template <bool LOGS>
+__device__ __forceinline__ void pair32bg(const Node<float>& A, const Node<float>& B, float dil,
+                                         float dli, float ce, float* ai, float* al) {
+  const float sr = A.rq + B.rq;
+  const float sb = A.bh + B.bh;
+  const float rsb = esdg_rcpf(sb);
+  const float pt = sr * rsb;
+  const float dr = A.rq - B.rq, db = A.bh - B.bh;
+  const float rsr = esdg_rcpf(sr);
+  const float fr = dr * rsr, ur = fr * fr;
+  const float fb = db * rsb, ub = fb * fb;
+  // background sums and perturbation sums
+  const float srb = A.rqb + B.rqb, sbb = A.bhb + B.bhb;
+  const float srp = A.rqp + B.rqp;
+  float ptp;
+  {
+    const float ri = 4.0f * A.rqb, rl = 4.0f * B.rqb, rpi = 4.0f * A.rqp, rpl = 4.0f * B.rqp;
+    const float dpb = A.pb - B.pb, dpp = A.pp - B.pp;
+    const float Cb = ri * B.pb - rl * A.pb;
+    const float Db = fmaf(ri, B.pb, rl * A.pb);
+    const float x1 = fmaf(ri, B.pp, fmaf(rpi, B.pb, rpi * B.pp));
+    const float x2 = fmaf(rl, A.pp, fmaf(rpl, A.pb, rpl * A.pp));
+    const float Cp = x1 - x2, Dp = x1 + x2;
+    const float C = Cb + Cp, D = Db + Dp;
+    const float num = fmaf(dpp * C, Db, dpb * fmaf(Cp, Db, -Cb * Dp));
+    ptp = fmaf(0.5f, A.pp + B.pp, num * esdg_rcpf(2.0f * D * Db));
+  }
+  const float drb = A.rqb - B.rqb;
+  const float rsrb = esdg_rcpf(srb);
+  const float frb = drb * rsrb, urb = frb * frb;
+  float rlog, iblog, rlogp;
+  if (!LOGS || (ur < ESDG_LOG_EPS32 && ub < ESDG_LOG_EPS32 && urb < ESDG_LOG_EPS32)) {
+    const float q2 = esdg_Q2f(ur);
+    rlog = sr * q2;
+    iblog = rsb * esdg_Af(ub);
+    const float fdiff = 2.0f * (A.rqp * B.rqb - B.rqp * A.rqb) * rsr * rsrb;
+    const float udiff = fdiff * (fr + frb);
+    // divided difference of Q2(u) = 2 - 2u/3 - 8u^2/45 - 88u^3/945
+    const float s2 = fmaf(-88.0f / 945.0f, fmaf(ur, ur, fmaf(ur, urb, urb * urb)),
+                          fmaf(-8.0f / 45.0f, ur + urb, -2.0f / 3.0f));
+    rlogp = fmaf(srp, q2, srb * udiff * s2);
+  } else {
+    rlog = (ur < ESDG_LOG_EPS32) ? sr * esdg_Q2f(ur)
+                                 : (4.0f * dr) / log1pf(dr * esdg_rcpf(B.rq));
+    iblog = (ub < ESDG_LOG_EPS32) ? rsb * esdg_Af(ub)
+                                  : log1pf(db * esdg_rcpf(B.bh)) / (2.0f * db);
+    const float rlogb = (urb < ESDG_LOG_EPS32) ? srb * esdg_Q2f(urb)
+                                               : (4.0f * drb) / log1pf(drb * esdg_rcpf(B.rqb));
+    rlogp = rlog - rlogb;
+  }
+  const float n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;
+  const float u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;
+  const float un = fmaf(u2, n2, fmaf(u1, n1, u0 * n0));
+  const float Fr = rlog * un;
+  const float m0 = fmaf(Fr, u0, ptp * n0);
+  const float m1 = fmaf(Fr, u1, ptp * n1);
+  const float m2 = fmaf(Fr, u2, ptp * n2);
+  const float uu = fmaf(A.u2, B.u2, fmaf(A.u1, B.u1, A.u0 * B.u0));
+  const float t = fmaf(2.0f, uu, A.ph + B.ph);
+  const float FE = fmaf(Fr, fmaf(iblog, ce, t), pt * un);
+  // gravity perturbation
+  const float dph = B.ph - A.ph;
+  const float dYi = 2.0f * (B.bhp * A.bhb - B.bhb * A.bhp) * A.ib * A.ibb;
+  const float dYl = 2.0f * (A.bhp * B.bhb - A.bhb * B.bhp) * B.ib * B.ibb;
+  const float gi = dph * fmaf(dYi, rlog, sbb * A.ibb * rlogp);
+  const float gl = -dph * fmaf(dYl, rlog, sbb * B.ibb * rlogp);
+  ai[0] = fmaf(dil, Fr, ai[0]);
+  ai[1] = fmaf(dil, fmaf(gi, n0, m0), ai[1]);
+  ai[2] = fmaf(dil, fmaf(gi, n1, m1), ai[2]);
+  ai[3] = fmaf(dil, fmaf(gi, n2, m2), ai[3]);
+  ai[4] = fmaf(dil, FE, ai[4]);
+  al[0] = fmaf(dli, Fr, al[0]);
+  al[1] = fmaf(dli, fmaf(gl, n0, m0), al[1]);
+  al[2] = fmaf(dli, fmaf(gl, n1, m1), al[2]);
+  al[3] = fmaf(dli, fmaf(gl, n2, m2), al[3]);
+  al[4] = fmaf(dli, FE, al[4]);
+}
+
+template <int N, bool MIXED, bool LOGS, bool BG>
+__device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED, BG>::R* __restrict__ S,
                                             int d, int base, int stride, const EsdgLGL& L,
-                                            typename Shape<N, MIXED>::R ce,
-                                            typename Shape<N, MIXED>::R (&acc)[N + 1][5]) {
-  using SH = Shape<N, MIXED>;
+                                            typename Shape<N, MIXED, BG>::R ce,
+                                            typename Shape<N, MIXED, BG>::R (&acc)[N + 1][5]) {
+  using SH = Shape<N, MIXED, BG>;
   using R = typename SH::R;
   constexpr int Nq = N + 1;
 #pragma unroll
   for (int i = 0; i < Nq; i++) {
-    const Node<R> A = load_node<R, LOGS, SH::F_NH, SH::NP>(S, base + i * stride, d);
+    const Node<R> A = load_node<R, LOGS, SH::F_NH, SH::NP, BG>(S, base + i * stride, d);
 #pragma unroll
     for (int l = i + 1; l < Nq; l++) {
-      const Node<R> B = load_node<R, LOGS, SH::F_NH, SH::NP>(S, base + l * stride, d);
-      if constexpr (MIXED)
+      const Node<R> B = load_node<R, LOGS, SH::F_NH, SH::NP, BG>(S, base + l * stride, d);
+      if constexpr (MIXED && BG)
+        pair32bg<LOGS>(A, B, L.Dtf[i][l], L.Dtf[l][i], ce, acc[i], acc[l]);
+      else if constexpr (MIXED)
         pair32<LOGS>(A, B, L.Dtf[i][l], L.Dtf[l][i], ce, acc[i], acc[l]);
       else
         pair64<LOGS>(A, B, L.Dt[i][l], L.Dt[l][i], ce, acc[i], acc[l]);
@@ -210,10 +320,10 @@ __device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED>::R* _
   }
 }
 
-template <int N, bool MIXED, int MODE>
-__global__ void __launch_bounds__(Shape<N, MIXED>::THREADS)
+template <int N, bool MIXED, int MODE, bool BG>
+__global__ void __launch_bounds__(Shape<N, MIXED, BG>::THREADS)
     k_volume(EsdgGrid g, EsdgPhys P, EsdgLGL L, EsdgVolArgs a) {
-  using SH = Shape<N, MIXED>;
+  using SH = Shape<N, MIXED, BG>;
   using R = typename SH::R;
   constexpr int Nq = SH::Nq, NP = SH::NP, NPEN = SH::NPEN, EPB = SH::EPB, NF = SH::NF;
   constexpr int T = SH::THREADS;
@@ -235,14 +345,16 @@ __global__ void __launch_bounds__(Shape<N, MIXED>::THREADS)
                    q4 = qe[4 * NP + n];
       const double phi = a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP + n];
       if constexpr (MIXED) {
-        // FP64 only where the hydrostatic background cancels: E - rho phi - KE
-        const float irf = esdg_rcpf((float)q0);
+        // FP64 only where the hydrostatic background cancels: E - rho phi - KE;
+        // conversions by integer repacking keep the FP64 pipe free
+        const float q0f = esdg_d2f(q0), q1f = esdg_d2f(q1), q2f = esdg_d2f(q2), q3f = esdg_d2f(q3);
+        const float irf = esdg_rcpf(q0f);
         const float hf = 0.5f * irf;
-        const float u0 = (float)q1 * hf, u1 = (float)q2 * hf, u2 = (float)q3 * hf;
-        const float ke = fmaf((float)q3, u2, fmaf((float)q2, u1, (float)q1 * u0));
-        const double p = gm1 * (fma(-q0, phi, q4) - (double)ke);
-        const float pf = (float)p;
-        const float rq = 0.25f * (float)q0;
+        const float u0 = q1f * hf, u1 = q2f * hf, u2 = q3f * hf;
+        const float ke = fmaf(q3f, u2, fmaf(q2f, u1, q1f * u0));
+        const double p = gm1 * (fma(-q0, phi, q4) - esdg_f2d(ke));
+        const float pf = esdg_d2f(p);
+        const float rq = 0.25f * q0f;
         S[0 * NP + n] = rq;
         S[1 * NP + n] = rq * esdg_rcpf(pf);
         S[2 * NP + n] = 2.0f * pf * irf;
@@ -250,7 +362,22 @@ __global__ void __launch_bounds__(Shape<N, MIXED>::THREADS)
         S[4 * NP + n] = u1;
         S[5 * NP + n] = u2;
         const double phi0 = a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP];
-        S[6 * NP + n] = (float)(0.5 * (phi - phi0));
+        S[6 * NP + n] = esdg_d2f(0.5 * (phi - phi0));
+        if constexpr (BG) {
+          // perturbations in FP64: rho' = rho - rho_bg, b' = rho/(2p) - b_bg
+          const double rb = a.bg[((size_t)e * 3 + 0) * NP + n];
+          const double bb = a.bg[((size_t)e * 3 + 1) * NP + n];
+          const double b = 0.5 * q0 * esdg_rcp(p);
+          const double pbg = a.bg[((size_t)e * 3 + 2) * NP + n];
+          R* Bf = S + SH::F_BG * NP;
+          Bf[0 * NP + n] = esdg_d2f(0.25 * (q0 - rb));
+          Bf[1 * NP + n] = esdg_d2f(0.5 * (b - bb));
+          Bf[2 * NP + n] = esdg_d2f(0.25 * rb);
+          Bf[3 * NP + n] = esdg_d2f(0.5 * bb);
+          Bf[4 * NP + n] = esdg_rcpf(esdg_d2f(bb));
+          Bf[5 * NP + n] = esdg_d2f(pbg);
+          Bf[6 * NP + n] = esdg_d2f(p - pbg);
+        }
       } else {
         const double ir = esdg_rcp(q0);
         const double hi = 0.5 * ir;
@@ -286,8 +413,8 @@ __global__ void __launch_bounds__(Shape<N, MIXED>::THREADS)
     for (int idx = threadIdx.x; idx < EPB * NP; idx += T) {
       const int el = idx / NP, n = idx - el * NP;
       const R* S = sm + (size_t)el * NF * NP;
-      const float r0 = (float)S[0], rn = (float)S[n];
-      const float b0 = (float)S[NP], bn = (float)S[NP + n];
+      const float r0 = esdg_d2f(S[0]), rn = esdg_d2f(S[n]);
+      const float b0 = esdg_d2f(S[NP]), bn = esdg_d2f(S[NP + n]);
       if (fabsf(rn - r0) > 0.0095f * r0 || fabsf(bn - b0) > 0.0095f * b0) need_logs = 1;
     }
     need_logs = __syncthreads_or(need_logs);
@@ -329,14 +456,16 @@ __global__ void __launch_bounds__(Shape<N, MIXED>::THREADS)
     for (int v = 0; v < 5; v++) acc[i][v] = (R)0;
   if (active && e < E) {
     const R* S = sm + (size_t)el * NF * NP;
-    const R ce = (R)(0.5 / gm1);
+    R ce;
+    if constexpr (MIXED) ce = esdg_d2f(0.5 * P.igm1);
+    else ce = 0.5 * P.igm1;
     if (need_logs)
-      pencil_pass<N, MIXED, true>(S, d, base, stride, L, ce, acc);
+      pencil_pass<N, MIXED, true, BG>(S, d, base, stride, L, ce, acc);
     else
-      pencil_pass<N, MIXED, false>(S, d, base, stride, L, ce, acc);
+      pencil_pass<N, MIXED, false, BG>(S, d, base, stride, L, ce, acc);
     if constexpr (MIXED) {
       // restore the element's reference geopotential in the energy flux
-      const R phi0 = (R)a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP];
+      const R phi0 = esdg_d2f(a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP]);
 #pragma unroll
       for (int i = 0; i < Nq; i++) acc[i][4] = fmaf(phi0, acc[i][0], acc[i][4]);
     }
@@ -378,9 +507,17 @@ __global__ void __launch_bounds__(Shape<N, MIXED>::THREADS)
     const R iJ = vg[((size_t)e2 * ESDG_NVGEO + 9) * NP + n];
     double r[5];
 #pragma unroll
-    for (int v = 0; v < 5; v++)
-      r[v] = (double)(-iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]));
+    for (int v = 0; v < 5; v++) {
+      const R rv = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
+      if constexpr (MIXED) r[v] = esdg_f2d(rv);
+      else r[v] = rv;
+    }
     const size_t qb = (size_t)e2 * 5 * NP + n;
+    if constexpr (BG) {  // the background's own FP64 momentum right-hand side
+      r[1] += a.rhs_bg[((size_t)e2 * 3 + 0) * NP + n];
+      r[2] += a.rhs_bg[((size_t)e2 * 3 + 1) * NP + n];
+      r[3] += a.rhs_bg[((size_t)e2 * 3 + 2) * NP + n];
+    }
     if (rotating) {
       const double y = a.x[((size_t)e2 * 3 + 1) * NP + n];
       const double f = P.f0 + P.beta * (y - P.y0);
@@ -393,12 +530,12 @@ __global__ void __launch_bounds__(Shape<N, MIXED>::THREADS)
     } else {
       if constexpr (MIXED) {
         float* dq = reinterpret_cast<float*>(a.dq);
-        const float A = (float)a.rkA, B = (float)a.rkB, dt = (float)a.dt;
+        const float A = esdg_d2f(a.rkA), B = esdg_d2f(a.rkB), dt = esdg_d2f(a.dt);
 #pragma unroll
         for (int v = 0; v < 5; v++) {
-          const float dv = fmaf(A, dq[qb + (size_t)v * NP], dt * (float)r[v]);
+          const float dv = fmaf(A, dq[qb + (size_t)v * NP], dt * esdg_d2f(r[v]));
           dq[qb + (size_t)v * NP] = dv;
-          a.q_io[qb + (size_t)v * NP] = a.q_in[qb + (size_t)v * NP] + (double)(B * dv);
+          a.q_io[qb + (size_t)v * NP] = a.q_in[qb + (size_t)v * NP] + esdg_f2d(B * dv);
         }
       } else {
         double* dq = reinterpret_cast<double*>(a.dq);
@@ -413,13 +550,13 @@ __global__ void __launch_bounds__(Shape<N, MIXED>::THREADS)
   }
 }
 
-template <int N, bool MIXED, int MODE>
+template <int N, bool MIXED, int MODE, bool BG>
 cudaError_t launch_one(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
                        const EsdgVolArgs& a, cudaStream_t s) {
-  using SH = Shape<N, MIXED>;
+  using SH = Shape<N, MIXED, BG>;
   static bool configured = false;  // one-time attribute set per instantiation
   if (!configured) {
-    cudaError_t err = cudaFuncSetAttribute(k_volume<N, MIXED, MODE>,
+    cudaError_t err = cudaFuncSetAttribute(k_volume<N, MIXED, MODE, BG>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)SH::SMEM);
     if (err != cudaSuccess) return err;
@@ -427,7 +564,7 @@ cudaError_t launch_one(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
   }
   const unsigned blocks = (unsigned)((g.E + SH::EPB - 1) / SH::EPB);
   if (blocks == 0) return cudaSuccess;
-  k_volume<N, MIXED, MODE><<<blocks, SH::THREADS, SH::SMEM, s>>>(g, P, L, a);
+  k_volume<N, MIXED, MODE, BG><<<blocks, SH::THREADS, SH::SMEM, s>>>(g, P, L, a);
   return cudaGetLastError();
 }
 
@@ -436,8 +573,11 @@ cudaError_t launch_volume_t(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys&
                             const EsdgVolArgs& a, cudaStream_t s) {
 #define ESDG_CASE(NN)                                                          \
   case NN:                                                                     \
-    return mode ? launch_one<NN, MIXED, 1>(g, P, L, a, s)                      \
-                : launch_one<NN, MIXED, 0>(g, P, L, a, s);
+    if (MIXED && a.bg)                                                         \
+      return mode ? launch_one<NN, MIXED, 1, MIXED>(g, P, L, a, s)             \
+                  : launch_one<NN, MIXED, 0, MIXED>(g, P, L, a, s);            \
+    return mode ? launch_one<NN, MIXED, 1, false>(g, P, L, a, s)               \
+                : launch_one<NN, MIXED, 0, false>(g, P, L, a, s);
   switch (g.N) {
     ESDG_CASE(1)
     ESDG_CASE(2)

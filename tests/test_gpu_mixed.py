@@ -1,0 +1,117 @@
+"""GPU mixed precision (FP32 pairs and sums, FP64 state, pressure recovery and RK
+accumulation, hydrostatic background carried exactly) against the FP64 oracle.
+
+Bars
+* right-hand side: relative L2 error <= 1e-5 per variable.  For the three
+  momentum components the reference norm is that of the whole momentum
+  right-hand side: on a rising-bubble state the horizontal components vanish
+  by symmetry at t = 0 (their exact value is round-off), so a per-component
+  ratio would be 0/0.
+* state after 100 LSRK steps: relative L2 error <= 1e-4 per variable.
+* the balanced channel jet: its density and energy right-hand sides are a
+  cancellation of convective fluxes ~700 times larger (the uniform zonal flow),
+  which no hydrostatic background removes; there the bar is the FP32 floor of
+  those terms, error <= 1e-5 ||rhs|| + 3 * 2^-24 * ||terms|| (terms = or_rhs_scale).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_16684_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CUBE = dict(lo=(0.0, 0.0, 0.0), hi=(1000.0, 1000.0, 1000.0))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_16684_gb300 import _build, _lib
+    _build.build()
+    return _lib
+
+
+def mixed_errors(r_gpu, r_ref):
+    mom = np.sqrt(sum(np.linalg.norm(r_ref[:, v]) ** 2 for v in (1, 2, 3)))
+    out = []
+    for v in range(5):
+        ref = mom if v in (1, 2, 3) else np.linalg.norm(r_ref[:, v])
+        out.append(np.linalg.norm(r_gpu[:, v] - r_ref[:, v]) / max(ref, 1e-300))
+    return np.array(out)
+
+
+def rel_err(a, b):
+    return np.array([np.linalg.norm(a[:, v] - b[:, v]) / np.linalg.norm(b[:, v]) for v in range(5)])
+
+
+@pytest.mark.parametrize("K,N,warp", [((4, 4, 4), 3, 0.0), ((6, 5, 4), 4, 0.05),
+                                      ((3, 3, 3), 7, 0.05), ((4, 3, 3), 2, 0.05)])
+def test_mixed_rhs_generic_and_bubble_states(lib, K, N, warp):
+    s = lib.Solver(*K, N, precision="mixed", warp=warp, **CUBE)
+    s.init_bubble()  # sets the unperturbed atmosphere as background
+    o = O.Oracle(*K, N, warp=warp, **CUBE)
+    x, _, _ = o.geometry()
+    qb = o.bubble()
+    qg = inputs.perturb_state(qb, x, CUBE["lo"], CUBE["hi"], seed=11)
+    q10 = o.steps(qb, o.cfl_dt(qb, 0.5), 10)
+    for q in (qg, qb, q10):
+        e = mixed_errors(s.rhs(q), o.rhs(q))
+        assert np.all(e <= 1e-5), e
+
+
+def test_mixed_state_after_100_steps(lib):
+    # the 4 x 4 x 4, N = 3 rising bubble
+    s = lib.Solver(4, 4, 4, 3, precision="mixed", **CUBE)
+    s.init_bubble()
+    o = O.Oracle(4, 4, 4, 3, **CUBE)
+    q0 = o.bubble()
+    dt = o.cfl_dt(q0, 0.5)
+    s.step(dt, 100)
+    q_gpu = s.get_state()
+    q_ref = o.steps(q0, dt, 100)
+    assert np.all(rel_err(q_gpu, q_ref) <= 1e-4)
+    # the flow itself (state minus initial state), momentum as one vector
+    assert np.all(mixed_errors(q_gpu - q0, q_ref - q0) <= 1e-4)
+
+
+def test_mixed_full_size_32cubed_N4(lib):
+    s = lib.Solver(32, 32, 32, 4, precision="mixed", warp=0.05, **CUBE)
+    s.init_bubble()
+    o = O.Oracle(32, 32, 32, 4, warp=0.05, **CUBE)
+    x, _, _ = o.geometry()
+    qg = inputs.perturb_state(o.bubble(), x, CUBE["lo"], CUBE["hi"], seed=7, kmin=8, kmax=16)
+    assert np.all(mixed_errors(s.rhs(qg), o.rhs(qg)) <= 1e-5)
+
+
+def test_mixed_channel_with_background(lib):
+    m = dict(lo=(0.0, 0.0, 0.0), hi=(40000e3, 6000e3, 30e3), periodic=(1, 0, 0))
+    s = lib.Solver(6, 3, 2, 4, precision="mixed", f0=1e-4, **m)
+    s.init_channel()  # the channel state at rest is the background
+    o = O.Oracle(6, 3, 2, 4, f0=1e-4, **m)
+    q = o.channel()
+    x, _, _ = o.geometry()
+    qg = inputs.perturb_state(q, x, m["lo"], m["hi"], seed=12)
+    r, ref, scale = s.rhs(q), o.rhs(q), o.rhs_scale(q)
+    e = mixed_errors(r, ref)
+    assert np.all(e[1:4] <= 1e-5), e
+    for v in (0, 4):
+        err = np.linalg.norm(r[:, v] - ref[:, v])
+        assert err <= 1e-5 * np.linalg.norm(ref[:, v]) + 3 * 2.0 ** -24 * np.linalg.norm(scale[:, v])
+    e = mixed_errors(s.rhs(qg), o.rhs(qg))
+    assert np.all(e <= 1e-5), e
+
+
+def test_mixed_without_background_still_runs(lib):
+    # plain FP32 pairs (no background): finite, and within FP32 rounding of the
+    # cancelling terms on a generic state
+    s = lib.Solver(3, 3, 3, 4, precision="mixed", warp=0.05, **CUBE)
+    s.init_bubble()
+    s.clear_background()
+    o = O.Oracle(3, 3, 3, 4, warp=0.05, **CUBE)
+    x, _, _ = o.geometry()
+    q = inputs.perturb_state(o.bubble(), x, CUBE["lo"], CUBE["hi"], seed=13)
+    r = s.rhs(q)
+    ref, scale = o.rhs(q), o.rhs_scale(q)
+    assert np.isfinite(r).all()
+    for v in range(5):
+        assert np.linalg.norm(r[:, v] - ref[:, v]) <= 1e-6 * np.linalg.norm(scale[:, v])
