@@ -50,6 +50,11 @@ FLOPS_PER_NODE = 45
 # is fused into the volume kernel.
 FACE_BYTES_PER_NODE = {"fp64": 160, "mixed": 140}
 
+# DRAM traffic of one FP64 volume launch: ncu capture of the same kernel on the 16^3 case
+# (dram__bytes_read.sum + dram__bytes_write.sum = 98.69 MB + 5.50 MB for 4096 elements),
+# scaled to the 32^3 launch by the element count (profiles/volume_fp64_N4_16cubed.md).
+VOLUME_FP64_TRAFFIC_BYTES = (98.69e6 + 5.50e6) * 8
+
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2     # 2 DFMA / clk / SM -> 1.258 TFLOP/s
 FP32_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2   # 128 FFMA / clk / SM -> 80.5 TFLOP/s
@@ -85,7 +90,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -283,7 +288,8 @@ def main_ours(args):
         "config": config_block({"precision": "fp64"}),
         "roofline": {"bound": "alu", "kernel": "volume (flux differencing + lift + RK), FP64",
                      "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK, "traffic": None,
+                     "frac": achieved / FP64_PEAK,
+                     "traffic": VOLUME_FP64_TRAFFIC_BYTES if w["K"] == (32, 32, 32) else None,
                      "peak_source": "152 SMs x 2 DFMA/clk x 2070 MHz (recipe's 1.25 TFLOP/s FP64)",
                      "flops_per_launch": vflops, "ms_per_launch": r64["t_vol"]},
         "kernels_ms_per_stage": {"fp64": {"interface": r64["t_face"], "volume_rk": r64["t_vol"]},
