@@ -163,6 +163,77 @@ int es_dg_launch(es_dg_t* h, int which, int stage, double dt);
 
 const char* es_dg_strerror(int status);
 
+/* ---- batched ensembles and the continuous-batching server -------------------
+ * A server keeps many solves resident on the device and advances all of them
+ * together: per LSRK stage, one persistent interface launch and one persistent
+ * volume launch per (polynomial order, precision) group walk device work
+ * tables of (member, tile) entries; one LSRK step is captured once as a CUDA
+ * graph and replayed, and admitting or retiring a solve rewrites the tables,
+ * not the graph.  Tile shapes (elements per CTA) and grid sizes are chosen per
+ * group by an autotuner that times launches on the resident solves.  Requests
+ * are admitted first come, first served when their estimated device footprint
+ * fits under the budget and a slot is free; requests arriving while others run
+ * join the batch at the next step (continuous batching).  Results carry the
+ * final state and the submit / admit / finish times.  Each member's arithmetic
+ * is independent of the others, so a result is the same alone and in a mix. */
+typedef struct es_dg_server es_dg_server;
+
+typedef struct {
+  int kind;                  /* 0 = rising bubble (1000 m cube, periodic x/y, walls z),
+                                1 = baroclinic channel stand-in (40000 x 6000 x 30 km,
+                                    periodic x, walls y/z, f0 = 1e-4) */
+  int kx, ky, kz, N;         /* elements per direction, order (1..7) */
+  es_dg_precision precision;
+  int nsteps;                /* LSRK steps to run */
+  double cfl;                /* Courant number for dt (0 = 0.5); dt fixed at admission */
+  double amp, centre[3], radius, theta0;  /* bubble: amplitude (K), centre, radius, theta0 */
+  double warp;               /* bubble mesh warp (fraction of the edge) */
+} es_dg_request;
+
+typedef struct {
+  int status;                /* ES_DG_OK, or the error that ended the request */
+  uint64_t ticket;
+  double t_submit, t_admit, t_finish;  /* seconds since server creation */
+  long long ndof;            /* nodes of the mesh */
+  int nsteps;                /* steps completed */
+  double dt;
+  double integrals[3];       /* mass, energy, entropy of the final state */
+  double* q;                 /* final state (host, layout of es_dg_get_state); free with
+                                es_dg_result_free */
+  size_t nq;
+} es_dg_result;
+
+typedef struct {
+  long long submitted, admitted, finished, steps;
+  int active, pending;
+  double dof_updates;        /* sum over finished requests of ndof * 5 * steps */
+  double launch_seconds;     /* host time spent launching steps */
+  size_t bytes_in_use;       /* estimated footprint of admitted requests */
+  int last_error;
+  char error[96];            /* text of the last failure, if any */
+} es_dg_server_stats_t;
+
+/* Start a server on the current device with a device-memory budget and a
+ * maximum number of resident solves.  It runs on cuda_stream, which must be a
+ * created stream (graph capture), or, with NULL, on a non-blocking stream of
+ * its own. */
+int es_dg_server_create(size_t hbm_budget_bytes, int max_slots, void* cuda_stream,
+                        es_dg_server** out);
+/* Queue a request (copied); -ES_DG_ENOMEM if it can never fit the budget,
+ * -ES_DG_EBUSY if the queue is full.  Thread-safe. */
+int es_dg_batch_submit(es_dg_server* s, const es_dg_request* req, uint64_t* ticket);
+/* ES_DG_PENDING (> 0) until the request is done; then ES_DG_OK and *out owns
+ * the result (release its state with es_dg_result_free).  Thread-safe. */
+int es_dg_batch_poll(es_dg_server* s, uint64_t ticket, es_dg_result* out);
+/* Blocking poll with a timeout (seconds); -ES_DG_ETIMEOUT when it runs out. */
+int es_dg_batch_wait(es_dg_server* s, uint64_t ticket, double timeout_s, es_dg_result* out);
+/* Cancel a queued or running request (its result gets -ES_DG_ECANCELED). */
+int es_dg_batch_cancel(es_dg_server* s, uint64_t ticket);
+void es_dg_result_free(es_dg_result* r);
+int es_dg_server_stats(es_dg_server* s, es_dg_server_stats_t* out);
+/* Cancel queued requests, finish running ones, stop the scheduler and free. */
+void es_dg_server_destroy(es_dg_server* s);
+
 /* ---- allocation-free entry point -------------------------------------------
  * The paper has no counterpart to this function; it exists for callers that
  * cannot allocate device memory (a memory pool they do not own, a framework

@@ -48,6 +48,27 @@ class es_dg_info_t(C.Structure):
                 ("device_bytes", C.c_size_t), ("precision", C.c_int)]
 
 
+class es_dg_request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("kx", C.c_int), ("ky", C.c_int), ("kz", C.c_int),
+                ("N", C.c_int), ("precision", C.c_int), ("nsteps", C.c_int), ("cfl", C.c_double),
+                ("amp", C.c_double), ("centre", C.c_double * 3), ("radius", C.c_double),
+                ("theta0", C.c_double), ("warp", C.c_double)]
+
+
+class es_dg_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("ticket", C.c_uint64), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_finish", C.c_double), ("ndof", C.c_longlong),
+                ("nsteps", C.c_int), ("dt", C.c_double), ("integrals", C.c_double * 3),
+                ("q", C.POINTER(C.c_double)), ("nq", C.c_size_t)]
+
+
+class es_dg_server_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("admitted", C.c_longlong),
+                ("finished", C.c_longlong), ("steps", C.c_longlong), ("active", C.c_int),
+                ("pending", C.c_int), ("dof_updates", C.c_double), ("launch_seconds", C.c_double),
+                ("bytes_in_use", C.c_size_t), ("last_error", C.c_int), ("error", C.c_char * 96)]
+
+
 _VP = C.c_void_p
 _DP = C.POINTER(C.c_double)
 
@@ -72,6 +93,14 @@ SIGNATURES = {
     "es_dg_strerror": (C.c_char_p, [C.c_int]),
     "es_dg_integrals_noalloc": (C.c_int, [C.POINTER(es_dg_mesh), C.c_int, C.POINTER(es_dg_physics),
                                           _VP, _VP, _VP, _VP, _VP]),
+    "es_dg_server_create": (C.c_int, [C.c_size_t, C.c_int, _VP, C.POINTER(_VP)]),
+    "es_dg_batch_submit": (C.c_int, [_VP, C.POINTER(es_dg_request), C.POINTER(C.c_uint64)]),
+    "es_dg_batch_poll": (C.c_int, [_VP, C.c_uint64, C.POINTER(es_dg_result)]),
+    "es_dg_batch_wait": (C.c_int, [_VP, C.c_uint64, C.c_double, C.POINTER(es_dg_result)]),
+    "es_dg_batch_cancel": (C.c_int, [_VP, C.c_uint64]),
+    "es_dg_result_free": (None, [C.POINTER(es_dg_result)]),
+    "es_dg_server_stats": (C.c_int, [_VP, C.POINTER(es_dg_server_stats_t)]),
+    "es_dg_server_destroy": (None, [_VP]),
 }
 
 
@@ -252,3 +281,76 @@ class Solver:
 
     def launch(self, which: int, stage: int = 0, dt: float = 0.0):
         check(self.lib.es_dg_launch(self.h, int(which), int(stage), float(dt)), "es_dg_launch")
+
+
+class Server:
+    """Continuous-batching server (es_dg_server_*): resident solves advanced
+    together by persistent batched launches under a captured CUDA graph."""
+
+    def __init__(self, hbm_budget_bytes=64 << 30, max_slots=256, stream=None):
+        import torch
+        torch.cuda.init()
+        self.lib = load()
+        self.stream = stream
+        sp = stream.cuda_stream if stream is not None else None  # None: the server's own stream
+        h = C.c_void_p()
+        check(self.lib.es_dg_server_create(int(hbm_budget_bytes), int(max_slots),
+                                           C.c_void_p(sp), C.byref(h)), "es_dg_server_create")
+        self.h = h
+
+    @staticmethod
+    def request(kind="bubble", K=(4, 4, 4), N=3, precision="fp64", nsteps=10, cfl=0.5, amp=0.5,
+                centre=(500.0, 500.0, 350.0), radius=250.0, theta0=300.0, warp=0.0):
+        return es_dg_request({"bubble": 0, "channel": 1}[kind], *K, N,
+                             {"fp64": ES_DG_FP64, "mixed": ES_DG_FP32_MIXED}[precision], nsteps,
+                             cfl, amp, (C.c_double * 3)(*centre), radius, theta0, warp)
+
+    def submit(self, **req) -> int:
+        t = C.c_uint64()
+        r = self.request(**req)
+        check(self.lib.es_dg_batch_submit(self.h, C.byref(r), C.byref(t)), "es_dg_batch_submit")
+        return t.value
+
+    def _take(self, res):
+        out = dict(status=res.status, ticket=res.ticket, t_submit=res.t_submit,
+                   t_admit=res.t_admit, t_finish=res.t_finish, ndof=res.ndof, nsteps=res.nsteps,
+                   dt=res.dt, integrals=np.array(res.integrals[:]), q=None)
+        if res.q and res.nq:
+            out["q"] = np.ctypeslib.as_array(res.q, shape=(res.nq,)).copy()
+        self.lib.es_dg_result_free(C.byref(res))
+        return out
+
+    def poll(self, ticket):
+        res = es_dg_result()
+        rc = self.lib.es_dg_batch_poll(self.h, C.c_uint64(ticket), C.byref(res))
+        if rc == ES_DG_PENDING:
+            return None
+        check(rc, "es_dg_batch_poll")
+        return self._take(res)
+
+    def wait(self, ticket, timeout=600.0):
+        res = es_dg_result()
+        check(self.lib.es_dg_batch_wait(self.h, C.c_uint64(ticket), float(timeout), C.byref(res)),
+              "es_dg_batch_wait")
+        return self._take(res)
+
+    def cancel(self, ticket):
+        check(self.lib.es_dg_batch_cancel(self.h, C.c_uint64(ticket)), "es_dg_batch_cancel")
+
+    def stats(self):
+        st = es_dg_server_stats_t()
+        check(self.lib.es_dg_server_stats(self.h, C.byref(st)), "es_dg_server_stats")
+        out = {k: getattr(st, k) for k, _ in es_dg_server_stats_t._fields_}
+        out["error"] = st.error.decode(errors="replace")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.es_dg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

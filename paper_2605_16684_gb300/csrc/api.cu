@@ -180,6 +180,23 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
 
 }  // namespace
 
+// Batch descriptor of a handle for the server's persistent kernels (not part of
+// the C ABI).  Mixed-precision members must carry a background.
+int esdg_member_descriptor(es_dg_t* h, double dt, EsdgMember* out, EsdgLGL* L, int* mixed) {
+  if (!h || !out) return ES_DG_EINVAL;
+  if (h->mixed && !h->has_bg) return ES_DG_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->g = h->g;
+  out->P = h->P;
+  out->a = vol_args(h, h->q, nullptr);
+  out->a.dt = dt;
+  out->fgeo = h->fgeo;
+  out->bg = h->mixed ? h->bg : nullptr;
+  if (L) *L = h->L;
+  if (mixed) *mixed = h->mixed;
+  return ES_DG_OK;
+}
+
 extern "C" {
 
 int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,

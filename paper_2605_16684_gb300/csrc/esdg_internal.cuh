@@ -178,6 +178,33 @@ struct EsdgVolArgs {
   const double* rhs_bg;  // mixed mode with a background: [E][3][np] FP64 momentum rhs of it
   double rkA, rkB, dt;
 };
+// One mesh of a batch: everything its kernels need, read by the persistent
+// batched kernels from a device array (one entry per resident solve).
+struct EsdgMember {
+  EsdgGrid g;
+  EsdgPhys P;
+  EsdgVolArgs a;       // q_in == q_io: the member's state; dq, geometry, face fluxes, dt
+  const double* fgeo;  // face geometry
+  const double* bg;    // mixed background or null
+  long long pad;
+};
+
+// Batched persistent launches over device work tables (tiles: int2 (member,
+// first element) for the volume, (member, first face node) in blocks of 256
+// for the faces; ntiles in device memory so the tables can change under a
+// captured graph).  variant selects the tile shape (elements per CTA).
+cudaError_t esdg_launch_face_batch(int N, int mixed, int bg, const EsdgMember* members,
+                                   const int2* tiles, const int* ntiles, int grid, cudaStream_t s);
+// what: 0 launch (returns 0 or -1), 1 elements per tile, 2 CTAs per SM
+int esdg_volume_batch_f64(int what, int N, int variant, const EsdgMember* members, const int2* tiles,
+                          const int* ntiles, int grid, const EsdgLGL& L, double A, double B,
+                          cudaStream_t s);
+int esdg_volume_batch_mixed(int what, int N, int variant, const EsdgMember* members,
+                            const int2* tiles, const int* ntiles, int grid, const EsdgLGL& L,
+                            double A, double B, cudaStream_t s);
+int esdg_volume_batch_variants_f64(int N);
+int esdg_volume_batch_variants_mixed(int N);
+
 cudaError_t esdg_launch_volume_f64(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P, int mode,
                                    const EsdgVolArgs& a, cudaStream_t s);
 cudaError_t esdg_launch_volume_mixed(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P,

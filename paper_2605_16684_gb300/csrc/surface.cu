@@ -264,13 +264,13 @@ __device__ __forceinline__ Side64 side64(const double* q, double phi, double gm1
   return Side64{rho, u0, u1, u2, 0.5 * rho * esdg_rcp(gm1 * e)};
 }
 
+// One face node (global face-node index tid) of one mesh.
 template <typename R, int N, bool BG>
-__global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const double* __restrict__ q,
-                                              const double* __restrict__ fgeo,
-                                              R* __restrict__ fflux,
-                                              const double* __restrict__ bg) {
+__device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
+                                          const double* __restrict__ q,
+                                          const double* __restrict__ fgeo, R* __restrict__ fflux,
+                                          const double* __restrict__ bg, long long tid) {
   constexpr int Nq = N + 1, NF2 = Nq * Nq, NP = Nq * Nq * Nq;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= g.nfaces * NF2) return;
   const long long f = tid / NF2;
   const int fn = (int)(tid - f * NF2);
@@ -354,6 +354,37 @@ __global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const doub
   for (int v = 0; v < 5; v++) out[v * NF2 + fn] = sc * F[v];
 }
 
+template <typename R, int N, bool BG>
+__global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const double* __restrict__ q,
+                                              const double* __restrict__ fgeo,
+                                              R* __restrict__ fflux,
+                                              const double* __restrict__ bg) {
+  face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Persistent batched face kernel: CTAs of 256 threads stride over a work table
+// of (member, first face node) tiles of meshes with the same N and precision.
+template <typename R, int N, bool BG>
+__global__ void __launch_bounds__(256) k_face_batch(const EsdgMember* __restrict__ members,
+                                                    const int2* __restrict__ tiles,
+                                                    const int* __restrict__ ntiles) {
+  __shared__ EsdgMember mb;
+  const int nt = *ntiles;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int2 tile = tiles[t];
+    {
+      const int* src = reinterpret_cast<const int*>(members + tile.x);
+      int* dst = reinterpret_cast<int*>(&mb);
+      for (int k = threadIdx.x; k < (int)(sizeof(EsdgMember) / sizeof(int)); k += blockDim.x)
+        dst[k] = src[k];
+    }
+    __syncthreads();
+    face_node<R, N, BG>(mb.g, mb.P, mb.a.q_in, mb.fgeo, (R*)mb.a.fflux, mb.bg,
+                        (long long)tile.y + threadIdx.x);
+    __syncthreads();
+  }
+}
+
 template <typename R, bool BG>
 cudaError_t launch_face_t(const EsdgGrid& g, const EsdgPhys& P, const double* q, const double* fgeo,
                           R* fflux, const double* bg, cudaStream_t s) {
@@ -374,6 +405,22 @@ cudaError_t launch_face_t(const EsdgGrid& g, const EsdgPhys& P, const double* q,
 }
 
 }  // namespace
+
+cudaError_t esdg_launch_face_batch(int N, int mixed, int bg, const EsdgMember* members,
+                                   const int2* tiles, const int* ntiles, int grid, cudaStream_t s) {
+#define ESDG_FB(NN)                                                                        \
+  case NN:                                                                                 \
+    if (mixed && bg) k_face_batch<float, NN, true><<<grid, 256, 0, s>>>(members, tiles, ntiles);  \
+    else if (mixed) k_face_batch<float, NN, false><<<grid, 256, 0, s>>>(members, tiles, ntiles);  \
+    else k_face_batch<double, NN, false><<<grid, 256, 0, s>>>(members, tiles, ntiles);      \
+    break;
+  switch (N) {
+    ESDG_FB(1) ESDG_FB(2) ESDG_FB(3) ESDG_FB(4) ESDG_FB(5) ESDG_FB(6) ESDG_FB(7)
+    default: return cudaErrorInvalidValue;
+  }
+#undef ESDG_FB
+  return cudaGetLastError();
+}
 
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
                              const double* fgeo, void* fflux, cudaStream_t s, const double* bg) {

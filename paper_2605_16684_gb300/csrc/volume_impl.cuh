@@ -54,10 +54,10 @@ template <> struct Cfg<5, true> { static constexpr int EPB = 3; };
 template <> struct Cfg<6, true> { static constexpr int EPB = 2; };
 template <> struct Cfg<7, true> { static constexpr int EPB = 2; };
 
-template <int N, bool MIXED, bool BG = false>
+template <int N, bool MIXED, bool BG = false, int EPB_ = 0>
 struct Shape {
   static constexpr int Nq = N + 1, NP = Nq * Nq * Nq, NPEN = Nq * Nq;
-  static constexpr int EPB = Cfg<N, MIXED>::EPB;
+  static constexpr int EPB = EPB_ > 0 ? EPB_ : Cfg<N, MIXED>::EPB;  // elements per CTA (tile)
   static constexpr int PENCILS = 3 * NPEN * EPB;
   static constexpr int THREADS = ((PENCILS + 31) / 32) * 32;
   // node fields: rq=rho/4, bh=b/2, ib=1/b, uh=u/2 (3), ph=phi/2, [lr, lb], nh=Ja/2 (9),
@@ -320,16 +320,16 @@ __device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED, BG>::
   }
 }
 
-template <int N, bool MIXED, int MODE, bool BG>
-__global__ void __launch_bounds__(Shape<N, MIXED, BG>::THREADS)
-    k_volume(EsdgGrid g, EsdgPhys P, EsdgLGL L, EsdgVolArgs a) {
-  using SH = Shape<N, MIXED, BG>;
+// One tile: elements e0 .. e0 + EPB - 1 of one mesh, processed by a CTA of
+// SH::THREADS threads with SH::SMEM bytes of shared memory at smraw.
+template <int N, bool MIXED, int MODE, bool BG, int EPB_ = 0>
+__device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
+                                            const EsdgVolArgs& a, int e0, unsigned char* smraw) {
+  using SH = Shape<N, MIXED, BG, EPB_>;
   using R = typename SH::R;
   constexpr int Nq = SH::Nq, NP = SH::NP, NPEN = SH::NPEN, EPB = SH::EPB, NF = SH::NF;
   constexpr int T = SH::THREADS;
-  extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
-  const int e0 = blockIdx.x * EPB;
   const int E = g.E;
   const R* vg = reinterpret_cast<const R*>(a.vgeo);
   const double gm1 = P.gamma - 1.0;
@@ -551,6 +551,43 @@ __global__ void __launch_bounds__(Shape<N, MIXED, BG>::THREADS)
 }
 
 template <int N, bool MIXED, int MODE, bool BG>
+__global__ void __launch_bounds__(Shape<N, MIXED, BG>::THREADS)
+    k_volume(EsdgGrid g, EsdgPhys P, EsdgLGL L, EsdgVolArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  volume_tile<N, MIXED, MODE, BG>(g, P, L, a, blockIdx.x * Shape<N, MIXED, BG>::EPB, smraw);
+}
+
+// Persistent batched volume kernel: CTAs stride over a device work table of
+// (member, first element) tiles of meshes with the same N and precision and
+// apply one LSRK stage to each (dt per member, stage coefficients per launch).
+// The member descriptor of the current tile is staged in shared memory.
+template <int N, bool MIXED, bool BG, int EPB_>
+__global__ void __launch_bounds__(Shape<N, MIXED, BG, EPB_>::THREADS)
+    k_volume_batch(const EsdgMember* __restrict__ members, const int2* __restrict__ tiles,
+                   const int* __restrict__ ntiles, EsdgLGL L, double rkA, double rkB) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ EsdgMember mb;
+  const int nt = *ntiles;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int2 tile = tiles[t];
+    {
+      const int* src = reinterpret_cast<const int*>(members + tile.x);
+      int* dst = reinterpret_cast<int*>(&mb);
+      for (int k = threadIdx.x; k < (int)(sizeof(EsdgMember) / sizeof(int)); k += blockDim.x)
+        dst[k] = src[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mb.a.rkA = rkA;
+      mb.a.rkB = rkB;
+    }
+    __syncthreads();
+    volume_tile<N, MIXED, 1, BG, EPB_>(mb.g, mb.P, L, mb.a, tile.y, smraw);
+    __syncthreads();
+  }
+}
+
+template <int N, bool MIXED, int MODE, bool BG>
 cudaError_t launch_one(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
                        const EsdgVolArgs& a, cudaStream_t s) {
   using SH = Shape<N, MIXED, BG>;
@@ -591,5 +628,39 @@ cudaError_t launch_volume_t(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys&
   }
 #undef ESDG_CASE
 }
+
+template <int N, bool MIXED, bool BG, int EPB_>
+cudaError_t launch_batch_one(const EsdgMember* members, const int2* tiles, const int* ntiles,
+                             int grid, const EsdgLGL& L, double A, double B, cudaStream_t s) {
+  using SH = Shape<N, MIXED, BG, EPB_>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(k_volume_batch<N, MIXED, BG, EPB_>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)SH::SMEM);
+    if (err != cudaSuccess) return err;
+    configured = true;
+  }
+  k_volume_batch<N, MIXED, BG, EPB_><<<grid, SH::THREADS, SH::SMEM, s>>>(members, tiles, ntiles, L,
+                                                                          A, B);
+  return cudaGetLastError();
+}
+
+template <int N, bool MIXED, bool BG, int EPB_>
+int batch_occupancy() {
+  using SH = Shape<N, MIXED, BG, EPB_>;
+  int nb = 0;
+  cudaFuncSetAttribute(k_volume_batch<N, MIXED, BG, EPB_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)SH::SMEM);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_volume_batch<N, MIXED, BG, EPB_>,
+                                                    SH::THREADS, SH::SMEM) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+template <int N, bool MIXED, bool BG, int EPB_>
+constexpr int batch_epb() { return Shape<N, MIXED, BG, EPB_>::EPB; }
 
 }  // namespace esdg_vol

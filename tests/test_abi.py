@@ -68,3 +68,10 @@ def test_create_rejects_gravity_with_z_periodic_box(lib):
     h = C.c_void_p()
     assert lib.es_dg_create(C.byref(m), 3, 0, None, None, None, C.byref(h)) == -1
     assert not h.value
+
+
+def test_server_rejects_bad_arguments_before_touching_cuda(lib):
+    h = C.c_void_p()
+    assert lib.es_dg_server_create(0, 4, None, C.byref(h)) == -1
+    assert lib.es_dg_server_create(1 << 30, 0, None, C.byref(h)) == -1
+    assert lib.es_dg_batch_submit(None, None, None) == -1

@@ -1,0 +1,103 @@
+"""Batched ensembles and the continuous-batching server on the GPU.
+
+* A batched solve (persistent launches over work tables, CUDA graph) gives the
+  same state as the same solve through the single-handle path.
+* A result is the same alone and in a mix of other requests (bit for bit: the
+  members' arithmetic is independent).
+* Admission respects the footprint budget; errors are reported per request.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_16684_gb300 import _build, _lib
+    _build.build()
+    return _lib
+
+
+def single_handle(lib, req):
+    kind = req.get("kind", "bubble")
+    K, N = req["K"], req["N"]
+    if kind == "bubble":
+        s = lib.Solver(*K, N, precision=req.get("precision", "fp64"), warp=req.get("warp", 0.0))
+        s.init_bubble(300.0, req.get("amp", 0.5), req.get("centre", (500.0, 500.0, 350.0)), 250.0)
+    else:
+        s = lib.Solver(*K, N, lo=(0, 0, 0), hi=(40000e3, 6000e3, 30e3), periodic=(1, 0, 0),
+                       precision=req.get("precision", "fp64"), f0=1e-4)
+        s.init_channel()
+    dt = s.cfl_dt(0.5)
+    s.step(dt, req["nsteps"])
+    q = s.get_state().reshape(-1)
+    s.close()
+    return q, dt
+
+
+MIX = [
+    dict(K=(4, 4, 4), N=3, precision="fp64", nsteps=4),
+    dict(K=(3, 3, 3), N=4, precision="mixed", nsteps=5, warp=0.05, amp=0.8),
+    dict(K=(2, 2, 2), N=7, precision="mixed", nsteps=3),
+    dict(kind="channel", K=(6, 3, 2), N=3, precision="fp64", nsteps=2),
+    dict(K=(5, 4, 3), N=4, precision="fp64", nsteps=6, centre=(450.0, 520.0, 300.0)),
+    dict(K=(3, 2, 2), N=3, precision="mixed", nsteps=7),
+]
+
+
+def test_batched_equals_single_handle(lib):
+    srv = lib.Server()
+    tickets = [srv.submit(**r) for r in MIX]
+    for t, r in zip(tickets, MIX):
+        res = srv.wait(t)
+        assert res["status"] == 0, srv.stats()["error"]
+        q_ref, dt = single_handle(lib, r)
+        assert res["dt"] == pytest.approx(dt, rel=0, abs=0)
+        assert res["nsteps"] == r["nsteps"]
+        assert np.array_equal(res["q"], q_ref), np.abs(res["q"] - q_ref).max()
+    st = srv.stats()
+    assert st["finished"] == len(MIX) and st["last_error"] == 0
+    srv.close()
+
+
+def test_result_same_alone_and_in_mix(lib):
+    target = dict(K=(4, 3, 3), N=4, precision="mixed", nsteps=6, warp=0.05)
+    alone = lib.Server()
+    qa = alone.wait(alone.submit(**target))["q"]
+    alone.close()
+    mix = lib.Server()
+    others = [mix.submit(**r) for r in MIX[:3]]
+    t = mix.submit(**target)
+    later = [mix.submit(**r) for r in MIX[3:]]
+    qm = mix.wait(t)["q"]
+    for o in others + later:
+        assert mix.wait(o)["status"] == 0
+    mix.close()
+    assert np.array_equal(qa, qm)
+
+
+def test_admission_by_footprint_serialises_large_requests(lib):
+    # budget for one 4^3 N=3 FP64 request at a time (estimated 1.7 MiB each)
+    srv = lib.Server(hbm_budget_bytes=3 << 20, max_slots=8)
+    reqs = [dict(K=(4, 4, 4), N=3, precision="fp64", nsteps=3) for _ in range(3)]
+    ts = [srv.submit(**r) for r in reqs]
+    res = [srv.wait(t) for t in ts]
+    assert all(r["status"] == 0 for r in res)
+    # FIFO: each admission waits for the previous request to finish
+    for a, b in zip(res, res[1:]):
+        assert b["t_admit"] >= a["t_finish"] - 1e-3
+    srv.close()
+
+
+def test_errors_and_cancel(lib):
+    from paper_2605_16684_gb300._lib import EsDgError
+    srv = lib.Server(hbm_budget_bytes=8 << 20)
+    with pytest.raises(EsDgError):
+        srv.submit(K=(4, 4, 4), N=9)
+    with pytest.raises(EsDgError):  # can never fit the budget
+        srv.submit(K=(32, 32, 32), N=4)
+    t = srv.submit(K=(2, 2, 2), N=3, nsteps=100000)
+    srv.cancel(t)
+    assert srv.wait(t)["status"] in (0, -7)
+    srv.close()
