@@ -347,6 +347,138 @@ def main_reference(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------- ensemble and serving --
+
+def _sequential(req, precision):
+    """One request solved alone through the single-handle C ABI; returns
+    (stepping seconds, ndof, final state)."""
+    import torch
+    from paper_2605_16684_gb300 import _lib
+    if req["kind"] == "bubble":
+        s = _lib.Solver(*req["K"], req["N"], precision=precision, warp=req.get("warp", 0.0))
+        s.init_bubble(300.0, req.get("amp", 0.5), req.get("centre", (500.0, 500.0, 350.0)), 250.0)
+    else:
+        s = _lib.Solver(*req["K"], req["N"], lo=(0, 0, 0), hi=(40000e3, 6000e3, 30e3),
+                        periodic=(1, 0, 0), precision=precision, f0=1e-4)
+        s.init_channel()
+    dt = s.cfl_dt(0.5)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s.step(dt, req["nsteps"])
+    s.sync()
+    el = time.perf_counter() - t
+    q = s.get_state()
+    nd = s.E * s.np
+    s.close()
+    return el, nd, q
+
+
+def _pct(x, p):
+    import numpy as np
+    return float(np.percentile(np.asarray(x), p)) if len(x) else None
+
+
+def run_ensemble(args):
+    import numpy as np
+    import torch
+    from paper_2605_16684_gb300 import _build, _lib, inputs
+    _build.build()
+    torch.cuda.init()
+    members = inputs.ensemble_members(args.members)
+    reqs = [dict(kind="bubble", K=(m["K"],) * 3, N=m["N"], amp=m["amp"], centre=m["centre"],
+                 nsteps=args.steps) for m in members]
+    srv = _lib.Server(hbm_budget_bytes=200 << 30, max_slots=len(reqs))
+    t0 = time.perf_counter()
+    tickets = [srv.submit(precision="mixed", **r) for r in reqs]
+    res = [srv.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    assert all(r["status"] == 0 for r in res), stats["error"]
+    dof_updates = sum(r["ndof"] * 5 * r["nsteps"] for r in res)
+    run = max(r["t_finish"] for r in res) - max(r["t_admit"] for r in res)
+    lat = [r["t_finish"] - r["t_submit"] for r in res]
+    # sequential plain FP64 solves of the same members (stepping time only)
+    seq_t, seq_err = 0.0, []
+    for i, r in enumerate(reqs):
+        el, nd, q64 = _sequential(r, "fp64")
+        seq_t += el
+        if i < args.check:
+            qb = res[i]["q"].reshape(q64.shape)
+            seq_err.append([float(np.linalg.norm(qb[:, v] - q64[:, v]) / np.linalg.norm(q64[:, v]))
+                            for v in (0, 4)])
+    out = {"metric": "ensemble DOF-updates/s per RK stage", "value": dof_updates / run,
+           "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+           "config": {"workload": "batched_ensemble_64_bubbles", "members": len(reqs),
+                      "grids": "K^3, K ~ U{8..24}", "orders": "N ~ U{3,4,7}",
+                      "precision": "mixed (FP32 pairs, FP64 state)",
+                      "launches": "one persistent interface + volume launch per (N) group per "
+                                  "stage, one LSRK step per CUDA graph replay"},
+           "batched_run_seconds": run, "wall_seconds_incl_admission": wall,
+           "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+           "sequential_fp64_value": dof_updates / seq_t,
+           "speedup_vs_sequential_fp64": (dof_updates / run) / (dof_updates / seq_t),
+           "mixed_vs_fp64_state_rel_err_rho_E_first_members": seq_err,
+           "server_steps": stats["steps"]}
+    print(json.dumps(out))
+
+
+def run_serving(args):
+    import threading
+    import numpy as np
+    import torch
+    from paper_2605_16684_gb300 import _build, _lib, inputs
+    _build.build()
+    torch.cuda.init()
+    # sequential FP64 service rate from a sample of the stream
+    sample = inputs.request_stream(args.requests, 1.0, seed=inputs.DEFAULT_SEED + 1,
+                                   steps=args.steps)[: args.calib]
+    t_seq = [_sequential(dict(r, nsteps=r["steps"]), "fp64")[0] for r in sample]
+    seq_rate = 1.0 / float(np.mean(t_seq))
+    points = []
+    for mult in [float(x) for x in args.rates.split(",")]:
+        rate = mult * seq_rate
+        stream = inputs.request_stream(args.requests, rate, steps=args.steps)
+        srv = _lib.Server(hbm_budget_bytes=args.budget_gb << 30, max_slots=args.slots)
+        tickets = [None] * len(stream)
+
+        def submitter():
+            start = time.perf_counter()
+            for i, r in enumerate(stream):
+                d = r["arrival"] - (time.perf_counter() - start)
+                if d > 0:
+                    time.sleep(d)
+                kw = dict(kind=r["kind"], K=r["K"], N=r["N"], nsteps=r["steps"], precision="mixed")
+                if r["kind"] == "bubble":
+                    kw["amp"] = r["amp"]
+                tickets[i] = srv.submit(**kw)
+
+        th = threading.Thread(target=submitter)
+        t0 = time.perf_counter()
+        th.start()
+        th.join()
+        res = [srv.wait(t, timeout=3600.0) for t in tickets]
+        makespan = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        ok = [r for r in res if r["status"] == 0]
+        lat = [r["t_finish"] - r["t_submit"] for r in ok]
+        dof = sum(r["ndof"] * 5 * r["nsteps"] for r in ok)
+        points.append({"rate_x_seq_fp64": mult, "rate_hz": rate, "completed": len(ok),
+                       "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+                       "throughput": dof / makespan, "makespan_s": makespan,
+                       "error": st["error"]})
+    out = {"metric": "serving p50/p99 solve latency and DOF-updates/s per RK stage",
+           "unit": "s / DOF-updates/s", "higher_is_better": False, "n_gpus": 1,
+           "config": {"workload": "poisson_serving", "requests": args.requests,
+                      "steps_per_request": args.steps,
+                      "mix": "70% bubbles K^3 (K 8..32), 30% channels (40s,8s,4s), N in {3,4,7}",
+                      "precision": "mixed", "admission": "FIFO by HBM footprint"},
+           "sequential_fp64_service_rate_hz": seq_rate,
+           "sequential_fp64_mean_service_s": float(np.mean(t_seq)), "points": points}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,7 +489,21 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--K", type=int, default=0, help="elements per direction (small profiling cases)")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--workload", default="bubble32", choices=["bubble32", "ensemble", "serving"])
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--check", type=int, default=4, help="ensemble members compared with FP64")
+    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--rates", default="0.25,0.5,1,2,4")
+    ap.add_argument("--calib", type=int, default=6)
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--budget-gb", type=int, default=200)
     args = ap.parse_args()
+    if args.workload == "ensemble":
+        run_ensemble(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
