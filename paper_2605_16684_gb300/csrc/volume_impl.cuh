@@ -109,8 +109,10 @@ __device__ __forceinline__ Node<R> load_node(const R* __restrict__ S, int n, int
   return a;
 }
 
-// One unordered pair (i = A, l = B) in FP64: 68 FP64 instructions on the
-// series path.  ai += Dt_il H(i,l), al += Dt_li H(l,i).
+// One unordered pair (i = A, l = B) in FP64: 62 FP64 instructions on the
+// series path.  ai += Dt_il H(i,l), al += Dt_li H(l,i).  The momentum flux is
+// regrouped as Fr {{u}} + (p* + g_own) {{n}}, so the gravity coefficient of
+// each side folds into its pressure term with one FMA.
 template <bool LOGS>
 __device__ __forceinline__ void pair64(const Node<double>& A, const Node<double>& B, double dil,
                                        double dli, double ce, double* ai, double* al) {
@@ -123,36 +125,34 @@ __device__ __forceinline__ void pair64(const Node<double>& A, const Node<double>
   const double fb = db * rsb, ub = fb * fb;
   double rlog, iblog;
   if (!LOGS) {
-    rlog = sr * esdg_Q2(ur);     // <rho>_log
-    iblog = rsb * esdg_A(ub);    // 1/<b>_log
+    rlog = sr * esdg_Q2_t(ur);     // <rho>_log
+    iblog = rsb * esdg_A_t(ub);    // 1/<b>_log
   } else {
-    if (esdg_lt_pos(ur, ESDG_LOG_EPS)) rlog = sr * esdg_Q2(ur);
+    if (esdg_lt_pos(ur, ESDG_LOG_EPS)) rlog = sr * esdg_Q2_t(ur);
     else rlog = (4.0 * dr) * esdg_rcp(A.lr - B.lr);
-    if (esdg_lt_pos(ub, ESDG_LOG_EPS)) iblog = rsb * esdg_A(ub);
+    if (esdg_lt_pos(ub, ESDG_LOG_EPS)) iblog = rsb * esdg_A_t(ub);
     else iblog = (A.lb - B.lb) * esdg_rcp(2.0 * db);
   }
   const double n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;  // {{Ja^d}}
   const double u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;  // {{u}}
   const double un = fma(u2, n2, fma(u1, n1, u0 * n0));
   const double Fr = rlog * un;
-  const double m0 = fma(Fr, u0, pt * n0);
-  const double m1 = fma(Fr, u1, pt * n1);
-  const double m2 = fma(Fr, u2, pt * n2);
+  const double f0 = Fr * u0, f1 = Fr * u1, f2 = Fr * u2;
   const double uu = fma(A.u2, B.u2, fma(A.u1, B.u1, A.u0 * B.u0));  // u_i . u_l / 4
   const double t = fma(2.0, uu, A.ph + B.ph);                        // u_i.u_l/2 + {{phi}}
-  const double FE = fma(Fr, fma(iblog, ce, t), pt * un);
+  const double FE = un * fma(rlog, fma(iblog, ce, t), pt);
   // gravity: 1/2 rho_hat [[phi]] with rho_hat = {{b}} <rho>_log / b_(own node)
   const double gq = sb * rlog * (B.ph - A.ph);
-  const double gi = gq * A.ib, gl = -gq * B.ib;
+  const double pi = fma(gq, A.ib, pt), pl = fma(-gq, B.ib, pt);
   ai[0] = fma(dil, Fr, ai[0]);
-  ai[1] = fma(dil, fma(gi, n0, m0), ai[1]);
-  ai[2] = fma(dil, fma(gi, n1, m1), ai[2]);
-  ai[3] = fma(dil, fma(gi, n2, m2), ai[3]);
+  ai[1] = fma(dil, fma(pi, n0, f0), ai[1]);
+  ai[2] = fma(dil, fma(pi, n1, f1), ai[2]);
+  ai[3] = fma(dil, fma(pi, n2, f2), ai[3]);
   ai[4] = fma(dil, FE, ai[4]);
   al[0] = fma(dli, Fr, al[0]);
-  al[1] = fma(dli, fma(gl, n0, m0), al[1]);
-  al[2] = fma(dli, fma(gl, n1, m1), al[2]);
-  al[3] = fma(dli, fma(gl, n2, m2), al[3]);
+  al[1] = fma(dli, fma(pl, n0, f0), al[1]);
+  al[2] = fma(dli, fma(pl, n1, f1), al[2]);
+  al[3] = fma(dli, fma(pl, n2, f2), al[3]);
   al[4] = fma(dli, FE, al[4]);
 }
 
@@ -504,7 +504,10 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
     const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
     if (e2 >= E) continue;
     const R* S = sm + (size_t)el2 * NF * NP;
-    const R iJ = vg[((size_t)e2 * ESDG_NVGEO + 9) * NP + n];
+    // FP64 stage update: dt is folded into the -1/J scale (r then holds dt rhs)
+    constexpr bool DT_IN_R = !MIXED && MODE != 0;
+    R iJ = vg[((size_t)e2 * ESDG_NVGEO + 9) * NP + n];
+    if constexpr (DT_IN_R) iJ *= a.dt;
     double r[5];
 #pragma unroll
     for (int v = 0; v < 5; v++) {
@@ -520,7 +523,8 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
     }
     if (rotating) {
       const double y = a.x[((size_t)e2 * 3 + 1) * NP + n];
-      const double f = P.f0 + P.beta * (y - P.y0);
+      double f = P.f0 + P.beta * (y - P.y0);
+      if constexpr (DT_IN_R) f *= a.dt;
       r[1] = fma(f, a.q_in[qb + 2 * NP], r[1]);
       r[2] = fma(-f, a.q_in[qb + NP], r[2]);
     }
@@ -541,7 +545,7 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
         double* dq = reinterpret_cast<double*>(a.dq);
 #pragma unroll
         for (int v = 0; v < 5; v++) {
-          const double dv = fma(a.rkA, dq[qb + (size_t)v * NP], a.dt * r[v]);
+          const double dv = fma(a.rkA, dq[qb + (size_t)v * NP], r[v]);
           dq[qb + (size_t)v * NP] = dv;
           a.q_io[qb + (size_t)v * NP] = fma(a.rkB, dv, a.q_in[qb + (size_t)v * NP]);
         }
