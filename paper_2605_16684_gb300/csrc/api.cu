@@ -421,7 +421,11 @@ int es_dg_step(es_dg_t* h, double dt, int nsteps) {
 
 int es_dg_sync(es_dg_t* h) {
   if (!h) return ES_DG_EINVAL;
-  return cuda_status(cudaStreamSynchronize(h->stream));
+  const int st = cuda_status(cudaStreamSynchronize(h->stream));
+  if (st != ES_DG_OK) return st;
+  const int to = esdg_volume_take_timeout();
+  if (to < 0) return ES_DG_ECUDA;
+  return to ? ES_DG_ETIMEOUT : ES_DG_OK;
 }
 
 int es_dg_integrals(es_dg_t* h, double out[3]) {

@@ -110,6 +110,92 @@ __device__ __forceinline__ double esdg_f2d(float f) {
   const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
   return (e == 0) ? 0.0 : __longlong_as_double((long long)(((unsigned long long)hi << 32) | (m << 29)));
 }
+// x * 2^k, exact, for a normal x whose result stays normal: an integer add on
+// the exponent field instead of an FP64-pipe multiply.
+__device__ __forceinline__ double esdg_ldexp_n(double x, int k) {
+  return __hiloint2double(__double2hiint(x) + (k << 20), __double2loint(x));
+}
+// the same where x may also be +-0
+__device__ __forceinline__ double esdg_ldexp_z(double x, int k) {
+  return (__double_as_longlong(x) << 1) == 0 ? x : esdg_ldexp_n(x, k);
+}
+
+// ---- 1-D bulk copies (the TMA engine) completing on a shared-memory mbarrier
+__device__ __forceinline__ unsigned esdg_smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void esdg_mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(esdg_smem_addr(bar)), "r"(count)
+               : "memory");
+}
+// make barrier initialisation visible to the async proxy (the copy engine)
+__device__ __forceinline__ void esdg_fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this CTA's earlier generic shared-memory accesses before later async-proxy writes
+__device__ __forceinline__ void esdg_fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void esdg_mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(esdg_smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// global -> shared, 16-byte aligned addresses, bytes a multiple of 16
+__device__ __forceinline__ void esdg_bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          esdg_smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(esdg_smem_addr(bar))
+      : "memory");
+}
+// Wait for completion of the barrier phase with the given parity, at most
+// `limit` polls (each poll may suspend the thread briefly); false if the limit
+// ran out.
+__device__ __forceinline__ bool esdg_mbar_wait(unsigned long long* bar, unsigned parity,
+                                               unsigned limit) {
+  const unsigned a = esdg_smem_addr(bar);
+  for (unsigned it = 0; it < limit; it++) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// Copy n doubles from global src into shared memory at region + sh, where
+// sh = 1 when src is 8 (mod 16) bytes: the interior then is 16-byte aligned on
+// both sides and goes as one bulk copy on `bar`; a leading and a trailing odd
+// double are copied by the calling thread.  region must be 16-byte aligned and
+// hold n + 1 doubles.  esdg_block_bytes gives the bulk bytes of such a copy
+// (the barrier's expect_tx, registered before the copies are issued).
+__device__ __forceinline__ unsigned esdg_block_bytes(const double* src, int n) {
+  if (n <= 0) return 0;
+  const int sh = (int)((reinterpret_cast<unsigned long long>(src) >> 3) & 1);
+  const int head = sh < n ? sh : n;
+  return (unsigned)(((n - head) / 2) * 2) * 8u;
+}
+__device__ __forceinline__ void esdg_block_g2s(double* region, const double* src, int n,
+                                               unsigned long long* bar) {
+  if (n <= 0) return;
+  const int sh = (int)((reinterpret_cast<unsigned long long>(src) >> 3) & 1);
+  double* dst = region + sh;
+  const int head = sh < n ? sh : n;
+  const int body = ((n - head) / 2) * 2;
+  const int tail = n - head - body;  // 0 or 1
+  if (head) dst[0] = src[0];
+  if (tail) dst[n - 1] = src[n - 1];
+  if (body > 0) esdg_bulk_g2s(dst + head, src + head, (unsigned)body * 8u, bar);
+}
+__device__ __forceinline__ int esdg_block_shift(const double* src) {
+  return (int)((reinterpret_cast<unsigned long long>(src) >> 3) & 1);
+}
+
 // x < y for non-negative doubles, compared as integers (no FP64-pipe compare)
 __device__ __forceinline__ bool esdg_lt_pos(double x, double y) {
   return __double_as_longlong(x) < __double_as_longlong(y);
@@ -137,18 +223,29 @@ __device__ __forceinline__ double esdg_Q2(double u) {  // 2 Q(u)
   return fma(u, fma(u, fma(u, -88.0 / 945.0, -8.0 / 45.0), -2.0 / 3.0), 2.0);
 }
 // FP64 series with the tail in FP32: for u < 1e-4 the terms beyond u^1 are below
-// 2e-9 in size, so evaluating them in FP32 (relative error ~1e-7) perturbs the
-// result by < 2e-16 of its value; two DFMA instead of three.  Used on the
-// series path of the FP64 volume kernel, where every pair has u < 1e-4.
+// 2e-9 in size, so evaluating them in FP32 (relative error ~2^-22) perturbs the
+// result by < 1e-16 of its value; two DFMA instead of three.  Used on the
+// series path of the FP64 volume kernel, where every pair has u < 1e-4.  The
+// conversions are short integer sequences (they sit on the pair's dependency
+// chain): u -> float by truncating the mantissa, the positive tail back by
+// re-biasing the exponent.
+__device__ __forceinline__ float esdg_d2f_tail(double u) {  // 0 <= u < 2^128
+  const int hi = __double2hiint(u);
+  const unsigned lo = (unsigned)__double2loint(u);
+  const float f = __uint_as_float(__funnelshift_l(lo, (unsigned)(hi - 0x38000000), 3));
+  return hi < 0x38100000 ? 0.0f : f;  // below the float normal range: 0
+}
+__device__ __forceinline__ double esdg_f2d_pos(float f) {  // positive normal f
+  const unsigned b = __float_as_uint(f);
+  return __hiloint2double((int)((b >> 3) + 0x38000000u), (int)(b << 29));
+}
 __device__ __forceinline__ double esdg_A_t(double u) {
-  const float uf = esdg_d2f(u);
-  const float tail = fmaf(uf, 1.0f / 7.0f, 1.0f / 5.0f);
-  return fma(u, fma(u, esdg_f2d(tail), 1.0 / 3.0), 1.0);
+  const float tail = fmaf(esdg_d2f_tail(u), 1.0f / 7.0f, 1.0f / 5.0f);
+  return fma(u, fma(u, esdg_f2d_pos(tail), 1.0 / 3.0), 1.0);
 }
 __device__ __forceinline__ double esdg_Q2_t(double u) {
-  const float uf = esdg_d2f(u);
-  const float tail = fmaf(uf, -88.0f / 945.0f, -8.0f / 45.0f);
-  return fma(u, fma(u, esdg_f2d(tail), -2.0 / 3.0), 2.0);
+  const float tail = fmaf(esdg_d2f_tail(u), 88.0f / 945.0f, 8.0f / 45.0f);  // -(u^2 coefficient tail)
+  return fma(-u, fma(u, esdg_f2d_pos(tail), 2.0 / 3.0), 2.0);
 }
 // FP32 variants: for u < 2e-2 the four-term truncation error is below 2e-8.
 #define ESDG_LOG_EPS32 2.0e-2f
@@ -219,6 +316,9 @@ int esdg_volume_batch_mixed(int what, int N, int variant, const EsdgMember* memb
 int esdg_volume_batch_variants_f64(int N);
 int esdg_volume_batch_variants_mixed(int N);
 
+// 1 if a bounded wait of the pipelined FP64 volume kernel ran out since the
+// last call (the flag is cleared), 0 if not, -1 on a CUDA error
+int esdg_volume_take_timeout();
 cudaError_t esdg_launch_volume_f64(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P, int mode,
                                    const EsdgVolArgs& a, cudaStream_t s);
 cudaError_t esdg_launch_volume_mixed(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P,

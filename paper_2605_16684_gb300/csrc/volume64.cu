@@ -2,6 +2,16 @@
 // single-mesh launches and the persistent batched kernel (two tile shapes).
 #include "volume_impl.cuh"
 
+int esdg_volume_take_timeout() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, esdg_vol::g_esdg_vol_timeout, sizeof(int)) != cudaSuccess) return -1;
+  if (v) {
+    const int z = 0;
+    if (cudaMemcpyToSymbol(esdg_vol::g_esdg_vol_timeout, &z, sizeof(int)) != cudaSuccess) return -1;
+  }
+  return v ? 1 : 0;
+}
+
 cudaError_t esdg_launch_volume_f64(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P, int mode,
                                    const EsdgVolArgs& a, cudaStream_t s) {
   return esdg_vol::launch_volume_t<false>(g, L, P, mode, a, s);

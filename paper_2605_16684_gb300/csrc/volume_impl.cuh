@@ -320,6 +320,76 @@ __device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED, BG>::
   }
 }
 
+// Interface terms of one pencil: the element is the "+" side of plane e_d
+// (its first node receives -(s/w) F*) and the "-" side of plane e_d + 1 (its
+// last node receives +(s/w) F*); fn is the pencil's node index on those faces.
+// INIT: the terms are the accumulators' initial value (FP64: they are then
+// loaded long before their first use), else they are added at the end (mixed:
+// after the element's reference geopotential is restored in the pair sums).
+template <bool INIT, int N, typename R>
+__device__ __forceinline__ void face_lift(const EsdgGrid& g, const EsdgVolArgs& a, int e, int d,
+                                          int fn, R (&acc)[N + 1][5]) {
+  constexpr int NPEN = (N + 1) * (N + 1);
+  // element indices selected without dynamic array indexing (no local memory)
+  const int i0 = e % g.K[0], i1 = (e / g.K[0]) % g.K[1], i2 = e / (g.K[0] * g.K[1]);
+  const int Pm = (d == 0) ? i0 : ((d == 1) ? i1 : i2);
+  const int ia = (d == 0) ? i1 : i0;  // index along esdg_others(d).o1
+  const int ib = (d == 2) ? i1 : i2;  // index along esdg_others(d).o2
+  const int Kd = (d == 0) ? g.K[0] : ((d == 1) ? g.K[1] : g.K[2]);
+  const int per = (d == 0) ? g.periodic[0] : ((d == 1) ? g.periodic[1] : g.periodic[2]);
+  int Pp = Pm + 1;
+  if (Pp == Kd && per) Pp = 0;
+  const long long fm = esdg_face_id(g, d, Pm, ia, ib);
+  const long long fp = esdg_face_id(g, d, Pp, ia, ib);
+  const R* ff = reinterpret_cast<const R*>(a.fflux);
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const R m = ff[((size_t)fm * 5 + v) * NPEN + fn], p = ff[((size_t)fp * 5 + v) * NPEN + fn];
+    if (INIT) {
+      acc[0][v] = -m;
+      acc[N][v] = p;
+    } else {
+      acc[0][v] -= m;
+      acc[N][v] += p;
+    }
+  }
+}
+
+// FP64 node primitives from the conserved state: rho/4, b/2 = rho/(4p),
+// 1/b = 2p/rho, u/2 and phi/2, with p = (gamma - 1)(E - rho phi - |rho u|^2/(2 rho)).
+// Power-of-two factors are applied exactly on the exponent field and b/2 is
+// taken as 1/(2 (1/b)): 15 FP64-pipe instructions per node.
+template <int NP>
+__device__ __forceinline__ void prims64(double q0, double q1, double q2, double q3, double q4,
+                                        double phi, double gm1, double* S, int n) {
+  const double ir = esdg_rcp(q0);
+  const double hi = esdg_ldexp_n(ir, -1);  // 1/(2 rho)
+  const double u0 = q1 * hi, u1 = q2 * hi, u2 = q3 * hi;
+  double ei = fma(-q0, phi, q4);
+  ei = fma(-q1, u0, ei);
+  ei = fma(-q2, u1, ei);
+  ei = fma(-q3, u2, ei);
+  const double p = gm1 * ei;
+  const double ib = esdg_ldexp_n(p, 1) * ir;  // 1/b = 2p/rho
+  S[0 * NP + n] = esdg_ldexp_n(q0, -2);
+  S[1 * NP + n] = esdg_ldexp_n(esdg_rcp(ib), -1);
+  S[2 * NP + n] = ib;
+  S[3 * NP + n] = u0;
+  S[4 * NP + n] = u1;
+  S[5 * NP + n] = u2;
+  S[6 * NP + n] = esdg_ldexp_z(phi, -1);
+}
+
+// Does any pair of this element leave the FP64 series range?  All
+// |x_n/x_0 - 1| below 0.0095 (x = rho, b) bound |f| < 0.0096 for every pair,
+// i.e. u < 1e-4.  Integer-repacked FP32 comparisons keep the FP64 pipe free.
+template <int NP>
+__device__ __forceinline__ bool out_of_series64(const double* S, int n) {
+  const float r0 = esdg_d2f(S[0]), rn = esdg_d2f(S[n]);
+  const float b0 = esdg_d2f(S[NP]), bn = esdg_d2f(S[NP + n]);
+  return fabsf(rn - r0) > 0.0095f * r0 || fabsf(bn - b0) > 0.0095f * b0;
+}
+
 // One tile: elements e0 .. e0 + EPB - 1 of one mesh, processed by a CTA of
 // SH::THREADS threads with SH::SMEM bytes of shared memory at smraw.
 template <int N, bool MIXED, int MODE, bool BG, int EPB_ = 0>
@@ -379,22 +449,7 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
           Bf[6 * NP + n] = esdg_d2f(p - pbg);
         }
       } else {
-        const double ir = esdg_rcp(q0);
-        const double hi = 0.5 * ir;
-        const double u0 = q1 * hi, u1 = q2 * hi, u2 = q3 * hi;
-        double ei = fma(-q0, phi, q4);
-        ei = fma(-q1, u0, ei);
-        ei = fma(-q2, u1, ei);
-        ei = fma(-q3, u2, ei);
-        const double p = gm1 * ei;
-        const double rq = 0.25 * q0;
-        S[0 * NP + n] = rq;
-        S[1 * NP + n] = rq * esdg_rcp(p);
-        S[2 * NP + n] = (p + p) * ir;
-        S[3 * NP + n] = u0;
-        S[4 * NP + n] = u1;
-        S[5 * NP + n] = u2;
-        S[6 * NP + n] = 0.5 * phi;
+        prims64<NP>(q0, q1, q2, q3, q4, phi, gm1, S, n);
       }
 #pragma unroll
       for (int k = 0; k < 9; k++)
@@ -408,14 +463,9 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
   }
   __syncthreads();
   if constexpr (!MIXED) {
-    // does any pair of this CTA leave the series range?  All |x_n/x_0 - 1| below
-    // 0.0095 bounds |f| < 0.0096 for every pair, i.e. u < 1e-4.
     for (int idx = threadIdx.x; idx < EPB * NP; idx += T) {
       const int el = idx / NP, n = idx - el * NP;
-      const R* S = sm + (size_t)el * NF * NP;
-      const float r0 = esdg_d2f(S[0]), rn = esdg_d2f(S[n]);
-      const float b0 = esdg_d2f(S[NP]), bn = esdg_d2f(S[NP + n]);
-      if (fabsf(rn - r0) > 0.0095f * r0 || fabsf(bn - b0) > 0.0095f * b0) need_logs = 1;
+      if (out_of_series64<NP>(sm + (size_t)el * NF * NP, n)) need_logs = 1;
     }
     need_logs = __syncthreads_or(need_logs);
     if (need_logs) {
@@ -454,6 +504,8 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
   for (int i = 0; i < Nq; i++)
 #pragma unroll
     for (int v = 0; v < 5; v++) acc[i][v] = (R)0;
+  if constexpr (!MIXED)
+    if (active && e < E) face_lift<true, N, R>(g, a, e, d, s + Nq * t, acc);
   if (active && e < E) {
     const R* S = sm + (size_t)el * NF * NP;
     R ce;
@@ -468,24 +520,7 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       const R phi0 = esdg_d2f(a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP]);
 #pragma unroll
       for (int i = 0; i < Nq; i++) acc[i][4] = fmaf(phi0, acc[i][0], acc[i][4]);
-    }
-    // face lifts: this element is the "+" side of plane e_d and the "-" side
-    // of plane e_d + 1
-    int idx3[3] = {e % g.K[0], (e / g.K[0]) % g.K[1], e / (g.K[0] * g.K[1])};
-    int o1, o2;
-    esdg_others(d, o1, o2);
-    const int Kd = g.K[d];
-    const int Pm = idx3[d];
-    int Pp = idx3[d] + 1;
-    if (Pp == Kd && g.periodic[d]) Pp = 0;
-    const long long fm = esdg_face_id(g, d, Pm, idx3[o1], idx3[o2]);
-    const long long fp = esdg_face_id(g, d, Pp, idx3[o1], idx3[o2]);
-    const R* ff = reinterpret_cast<const R*>(a.fflux);
-    const int fn = s + Nq * t;
-#pragma unroll
-    for (int v = 0; v < 5; v++) {
-      acc[0][v] -= ff[((size_t)fm * 5 + v) * NPEN + fn];
-      acc[N][v] += ff[((size_t)fp * 5 + v) * NPEN + fn];
+      face_lift<false, N, R>(g, a, e, d, s + Nq * t, acc);
     }
   }
   __syncthreads();
@@ -591,6 +626,250 @@ __global__ void __launch_bounds__(Shape<N, MIXED, BG, EPB_>::THREADS)
   }
 }
 
+
+// ---- pipelined persistent FP64 kernel -------------------------------------
+// The FP64 kernel is bound by the FP64 pipe, and at 168 registers per thread
+// one CTA fills an SM, so global-load latency in the prologue and epilogue
+// would leave the pipe idle.  Here one CTA per SM walks the tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...; during tile t's pair pass the
+// copy engine brings tile t + gridDim.x's state and geometry (RAW) and tile
+// t's dq (DQ) into shared memory as 1-D bulk copies issued by one thread,
+// completing on two mbarriers.  The arithmetic is that of
+// volume_tile<N, false, MODE, false>, in the same order.
+#define ESDG_WAIT_LIMIT (1u << 20)
+// set when a bounded wait of the pipelined kernel ran out (read by es_dg_sync)
+static __device__ int g_esdg_vol_timeout;
+
+template <int N, int MODE>
+struct Pipe64 {
+  using SH = Shape<N, false, false>;
+  static constexpr int P = SH::NP * SH::EPB;  // nodes per tile
+  static constexpr int even(int x) { return (x + 1) & ~1; }
+  // offsets in doubles, all even (16-byte aligned); each copy target holds
+  // one extra double for the alignment shift of its source
+  static constexpr int RAW_Q = 0;                            // [el][5][NP]   next tile's q
+  static constexpr int RAW_G = even(RAW_Q + 5 * P + 1);      // [el][11][NP]  next tile's geometry
+  static constexpr int S0 = even(RAW_G + ESDG_NVGEO * P + 1);  // [el][18][NP] primitives, Ja/2; exchange
+  static constexpr int EPI = even(S0 + SH::NF * P);          // [el][6][NP]   q and 1/J of this tile
+  static constexpr int DQ = even(EPI + 6 * P);               // [el][5][NP]   dq of this tile
+  static constexpr int TOTAL = MODE ? DQ + 5 * P + 1 : DQ;
+  static constexpr size_t SMEM = sizeof(double) * (size_t)TOTAL;
+  static_assert(SH::NF == 18, "FP64 node fields");
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
+    k_volume_pipe64(EsdgGrid g, EsdgPhys P, EsdgLGL L, EsdgVolArgs a, int ntiles) {
+  using SH = Shape<N, false, false>;
+  using PP = Pipe64<N, MODE>;
+  constexpr int Nq = SH::Nq, NP = SH::NP, NPEN = SH::NPEN, EPB = SH::EPB, NF = SH::NF;
+  constexpr int T = SH::THREADS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ unsigned long long bars[2];  // [0] RAW of the next tile, [1] DQ of this tile
+  double* sm = reinterpret_cast<double*>(smraw);
+  const int E = g.E;
+  const double* vg = reinterpret_cast<const double*>(a.vgeo);
+  const double* dqg = reinterpret_cast<const double*>(a.dq);
+  const int tid = threadIdx.x;
+
+  // thread 0 issues the copies of a tile's state and geometry (RAW)
+  auto issue_raw = [&](int tile) {
+    const int e0 = tile * EPB, ne = min(EPB, E - e0);
+    const double* qs = a.q_in + (size_t)e0 * 5 * NP;
+    const double* gs = vg + (size_t)e0 * ESDG_NVGEO * NP;
+    esdg_mbar_arrive_tx(&bars[0], esdg_block_bytes(qs, ne * 5 * NP) +
+                                      esdg_block_bytes(gs, ne * ESDG_NVGEO * NP));
+    esdg_fence_proxy_async();
+    esdg_block_g2s(sm + PP::RAW_Q, qs, ne * 5 * NP, &bars[0]);
+    esdg_block_g2s(sm + PP::RAW_G, gs, ne * ESDG_NVGEO * NP, &bars[0]);
+  };
+
+  if (tid == 0) {
+    esdg_mbar_init(&bars[0], 1);
+    esdg_mbar_init(&bars[1], 1);
+    esdg_fence_mbar_init();
+  }
+  __syncthreads();
+  int tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue_raw(tile);
+  unsigned ph_raw = 0, ph_dq = 0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int e0 = tile * EPB;
+    const bool ok = esdg_mbar_wait(&bars[0], ph_raw, ESDG_WAIT_LIMIT);
+    ph_raw ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(&g_esdg_vol_timeout, 1);
+      return;
+    }
+    // ---- prologue: RAW -> primitives, Ja/2 (S) and q, 1/J (EPI) -----------
+    {
+      const double* qr0 = sm + PP::RAW_Q + esdg_block_shift(a.q_in + (size_t)e0 * 5 * NP);
+      const double* gr0 = sm + PP::RAW_G + esdg_block_shift(vg + (size_t)e0 * ESDG_NVGEO * NP);
+      for (int idx = tid; idx < EPB * NP; idx += T) {
+        const int el2 = idx / NP, n = idx - el2 * NP;
+        double* S = sm + PP::S0 + (size_t)el2 * NF * NP;
+        if (e0 + el2 < E) {
+          const double* qr = qr0 + (size_t)el2 * 5 * NP;
+          const double* gr = gr0 + (size_t)el2 * ESDG_NVGEO * NP;
+          double* X = sm + PP::EPI + (size_t)el2 * 6 * NP;
+          const double q0 = qr[n], q1 = qr[NP + n], q2 = qr[2 * NP + n], q3 = qr[3 * NP + n],
+                       q4 = qr[4 * NP + n];
+          prims64<NP>(q0, q1, q2, q3, q4, gr[10 * NP + n], P.gamma - 1.0, S, n);
+#pragma unroll
+          for (int k = 0; k < 9; k++) S[(SH::F_NH + k) * NP + n] = gr[k * NP + n];
+          X[n] = q0;
+          X[NP + n] = q1;
+          X[2 * NP + n] = q2;
+          X[3 * NP + n] = q3;
+          X[4 * NP + n] = q4;
+          X[5 * NP + n] = gr[9 * NP + n];
+        } else {  // padding element: any valid state, results are discarded
+          S[0 * NP + n] = 0.25;
+          S[1 * NP + n] = 0.5;
+          S[2 * NP + n] = 1.0;
+          for (int k = 3; k < NF; k++) S[k * NP + n] = 0.0;
+        }
+      }
+    }
+    __syncthreads();  // RAW consumed
+    if (tid == 0) {
+      if constexpr (MODE != 0) {
+        const int ne = min(EPB, E - e0);
+        const double* ds = dqg + (size_t)e0 * 5 * NP;
+        esdg_mbar_arrive_tx(&bars[1], esdg_block_bytes(ds, ne * 5 * NP));
+        esdg_fence_proxy_async();
+        esdg_block_g2s(sm + PP::DQ, ds, ne * 5 * NP, &bars[1]);
+      }
+      if (tile + (int)gridDim.x < ntiles) issue_raw(tile + gridDim.x);
+    }
+
+    int need_logs = 0;
+    for (int idx = tid; idx < EPB * NP; idx += T) {
+      const int el2 = idx / NP, n = idx - el2 * NP;
+      if (out_of_series64<NP>(sm + PP::S0 + (size_t)el2 * NF * NP, n)) need_logs = 1;
+    }
+    need_logs = __syncthreads_or(need_logs);
+    if (need_logs) {
+      for (int idx = tid; idx < EPB * NP; idx += T) {
+        const int el2 = idx / NP, n = idx - el2 * NP;
+        double* S = sm + PP::S0 + (size_t)el2 * NF * NP;
+        S[SH::F_LR * NP + n] = log(4.0 * S[n]);
+        S[SH::F_LB * NP + n] = log(2.0 * S[NP + n]);
+      }
+      __syncthreads();
+    }
+
+    // ---- pair pass: this thread's pencil (index arithmetic redone per tile
+    // rather than held in registers across the pair pass) -------------------
+    const bool active = tid < SH::PENCILS;
+    const int el = active ? tid / (3 * NPEN) : 0;
+    const int rr = tid - el * 3 * NPEN;
+    const int d = active ? rr / NPEN : 0;
+    const int pen = rr - d * NPEN;
+    const int ps = pen % Nq, pt = pen / Nq;
+    const int stride = (d == 0) ? 1 : ((d == 1) ? Nq : Nq * Nq);
+    const int base = (d == 0) ? Nq * (ps + Nq * pt) : ((d == 1) ? (ps + Nq * Nq * pt) : (ps + Nq * pt));
+    const int e = e0 + el;
+    double acc[Nq][5];
+#pragma unroll
+    for (int i = 0; i < Nq; i++)
+#pragma unroll
+      for (int v = 0; v < 5; v++) acc[i][v] = 0.0;
+    if (active && e < E) {
+      face_lift<true, N, double>(g, a, e, d, ps + Nq * pt, acc);
+      const double* S = sm + PP::S0 + (size_t)el * NF * NP;
+      if (need_logs)
+        pencil_pass<N, false, true, false>(S, d, base, stride, L, 0.5 * P.igm1, acc);
+      else
+        pencil_pass<N, false, false, false>(S, d, base, stride, L, 0.5 * P.igm1, acc);
+    }
+    __syncthreads();
+    if (active && e < E) {
+      double* S = sm + PP::S0 + (size_t)el * NF * NP;
+#pragma unroll
+      for (int i = 0; i < Nq; i++)
+#pragma unroll
+        for (int v = 0; v < 5; v++) S[(d * 5 + v) * NP + base + i * stride] = acc[i][v];
+    }
+    if constexpr (MODE != 0) {
+      const bool okd = esdg_mbar_wait(&bars[1], ph_dq, ESDG_WAIT_LIMIT);  // this tile's dq
+      ph_dq ^= 1u;
+      if (__syncthreads_or(!okd)) {
+        if (tid == 0) atomicExch(&g_esdg_vol_timeout, 1);
+        return;
+      }
+    } else {
+      __syncthreads();
+    }
+
+    // ---- epilogue: one thread per node --------------------------------------
+    const double* D0 = sm + PP::DQ + esdg_block_shift(dqg + (size_t)e0 * 5 * NP);
+    for (int idx = tid; idx < EPB * NP; idx += T) {
+      const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
+      if (e2 >= E) continue;
+      const double* S = sm + PP::S0 + (size_t)el2 * NF * NP;
+      const double* X = sm + PP::EPI + (size_t)el2 * 6 * NP;
+      double iJ = X[5 * NP + n];
+      if constexpr (MODE != 0) iJ *= a.dt;
+      double r[5];
+#pragma unroll
+      for (int v = 0; v < 5; v++) r[v] = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
+      if ((P.f0 != 0.0) || (P.beta != 0.0)) {
+        const double y = a.x[((size_t)e2 * 3 + 1) * NP + n];
+        double f = P.f0 + P.beta * (y - P.y0);
+        if constexpr (MODE != 0) f *= a.dt;
+        r[1] = fma(f, X[2 * NP + n], r[1]);
+        r[2] = fma(-f, X[NP + n], r[2]);
+      }
+      const size_t qb = (size_t)e2 * 5 * NP + n;
+      if constexpr (MODE == 0) {
+#pragma unroll
+        for (int v = 0; v < 5; v++) a.rhs[qb + (size_t)v * NP] = r[v];
+      } else {
+        const double* D = D0 + (size_t)el2 * 5 * NP;
+        double* dq = reinterpret_cast<double*>(a.dq);
+#pragma unroll
+        for (int v = 0; v < 5; v++) {
+          const double dv = fma(a.rkA, D[v * NP + n], r[v]);
+          dq[qb + (size_t)v * NP] = dv;
+          a.q_io[qb + (size_t)v * NP] = fma(a.rkB, dv, X[v * NP + n]);
+        }
+      }
+    }
+  }
+}
+
+template <int N, int MODE>
+cudaError_t launch_pipe64(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
+                          const EsdgVolArgs& a, cudaStream_t s) {
+  using SH = Shape<N, false, false>;
+  using PP = Pipe64<N, MODE>;
+  constexpr int MAXDEV = 64;
+  static int grid_cap[MAXDEV];  // resident CTAs per device, set on first use
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
+  if (grid_cap[dev] == 0) {
+    err = cudaFuncSetAttribute(k_volume_pipe64<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)PP::SMEM);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0, nsm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_volume_pipe64<N, MODE>,
+                                                        SH::THREADS, PP::SMEM);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    grid_cap[dev] = per_sm * nsm;
+  }
+  const int ntiles = (g.E + SH::EPB - 1) / SH::EPB;
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = ntiles < grid_cap[dev] ? ntiles : grid_cap[dev];
+  k_volume_pipe64<N, MODE><<<grid, SH::THREADS, PP::SMEM, s>>>(g, P, L, a, ntiles);
+  return cudaGetLastError();
+}
+
 template <int N, bool MIXED, int MODE, bool BG>
 cudaError_t launch_one(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
                        const EsdgVolArgs& a, cudaStream_t s) {
@@ -614,6 +893,10 @@ cudaError_t launch_volume_t(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys&
                             const EsdgVolArgs& a, cudaStream_t s) {
 #define ESDG_CASE(NN)                                                          \
   case NN:                                                                     \
+    if constexpr (!MIXED) {                                                    \
+      return mode ? launch_pipe64<NN, 1>(g, P, L, a, s)                        \
+                  : launch_pipe64<NN, 0>(g, P, L, a, s);                       \
+    }                                                                          \
     if (MIXED && a.bg)                                                         \
       return mode ? launch_one<NN, MIXED, 1, MIXED>(g, P, L, a, s)             \
                   : launch_one<NN, MIXED, 0, MIXED>(g, P, L, a, s);            \
