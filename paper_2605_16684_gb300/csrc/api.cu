@@ -423,9 +423,9 @@ int es_dg_sync(es_dg_t* h) {
   if (!h) return ES_DG_EINVAL;
   const int st = cuda_status(cudaStreamSynchronize(h->stream));
   if (st != ES_DG_OK) return st;
-  const int to = esdg_volume_take_timeout();
-  if (to < 0) return ES_DG_ECUDA;
-  return to ? ES_DG_ETIMEOUT : ES_DG_OK;
+  const int t64 = esdg_volume_f64_take_timeout(), t32 = esdg_volume_mixed_take_timeout();
+  if (t64 < 0 || t32 < 0) return ES_DG_ECUDA;
+  return (t64 || t32) ? ES_DG_ETIMEOUT : ES_DG_OK;
 }
 
 int es_dg_integrals(es_dg_t* h, double out[3]) {

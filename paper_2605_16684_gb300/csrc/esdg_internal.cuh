@@ -168,33 +168,67 @@ __device__ __forceinline__ bool esdg_mbar_wait(unsigned long long* bar, unsigned
   }
   return false;
 }
-// Copy n doubles from global src into shared memory at region + sh, where
-// sh = 1 when src is 8 (mod 16) bytes: the interior then is 16-byte aligned on
-// both sides and goes as one bulk copy on `bar`; a leading and a trailing odd
-// double are copied by the calling thread.  region must be 16-byte aligned and
-// hold n + 1 doubles.  esdg_block_bytes gives the bulk bytes of such a copy
-// (the barrier's expect_tx, registered before the copies are issued).
-__device__ __forceinline__ unsigned esdg_block_bytes(const double* src, int n) {
+// Copy n elements (double or float) from global src into shared memory at
+// region + sh, where sh = (src / sizeof(T)) mod (16 / sizeof(T)): the interior
+// then is 16-byte aligned on both sides and goes as one bulk copy on `bar`; the
+// few leading and trailing elements outside it are copied by the calling
+// thread.  region must be 16-byte aligned and hold n + 16/sizeof(T) - 1
+// elements.  esdg_block_bytes gives the bulk bytes of such a copy (the
+// barrier's expect_tx, registered before the copies are issued).
+template <typename T>
+__device__ __forceinline__ int esdg_block_shift(const T* src) {
+  constexpr unsigned long long K = 16 / sizeof(T);
+  return (int)((reinterpret_cast<unsigned long long>(src) / sizeof(T)) % K);
+}
+template <typename T>
+__device__ __forceinline__ void esdg_block_split(const T* src, int n, int& sh, int& head,
+                                                 int& body) {
+  constexpr int K = 16 / sizeof(T);
+  sh = esdg_block_shift(src);
+  head = (K - sh) % K;
+  if (head > n) head = n;
+  body = ((n - head) / K) * K;
+}
+template <typename T>
+__device__ __forceinline__ unsigned esdg_block_bytes(const T* src, int n) {
   if (n <= 0) return 0;
-  const int sh = (int)((reinterpret_cast<unsigned long long>(src) >> 3) & 1);
-  const int head = sh < n ? sh : n;
-  return (unsigned)(((n - head) / 2) * 2) * 8u;
+  int sh, head, body;
+  esdg_block_split(src, n, sh, head, body);
+  return (unsigned)body * (unsigned)sizeof(T);
 }
-__device__ __forceinline__ void esdg_block_g2s(double* region, const double* src, int n,
-                                               unsigned long long* bar) {
+template <typename T>
+__device__ __forceinline__ void esdg_cp_async(T* dst, const T* src) {  // sizeof(T) bytes
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(esdg_smem_addr(dst)), "l"(src),
+               "n"((int)sizeof(T))
+               : "memory");
+}
+__device__ __forceinline__ void esdg_cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+// the bulk interior of the block copy (one thread)
+template <typename T>
+__device__ __forceinline__ void esdg_block_bulk(T* region, const T* src, int n,
+                                                unsigned long long* bar) {
   if (n <= 0) return;
-  const int sh = (int)((reinterpret_cast<unsigned long long>(src) >> 3) & 1);
-  double* dst = region + sh;
-  const int head = sh < n ? sh : n;
-  const int body = ((n - head) / 2) * 2;
-  const int tail = n - head - body;  // 0 or 1
-  if (head) dst[0] = src[0];
-  if (tail) dst[n - 1] = src[n - 1];
-  if (body > 0) esdg_bulk_g2s(dst + head, src + head, (unsigned)body * 8u, bar);
+  int sh, head, body;
+  esdg_block_split(src, n, sh, head, body);
+  if (body > 0)
+    esdg_bulk_g2s(region + sh + head, src + head, (unsigned)body * (unsigned)sizeof(T), bar);
 }
-__device__ __forceinline__ int esdg_block_shift(const double* src) {
-  return (int)((reinterpret_cast<unsigned long long>(src) >> 3) & 1);
+// the k-th of the block's elements outside the bulk interior (k < 2 (16/sizeof(T) - 1)),
+// copied with cp.async by the calling thread; nothing for k past the last
+template <typename T>
+__device__ __forceinline__ void esdg_block_edge(T* region, const T* src, int n, int k) {
+  if (n <= 0) return;
+  int sh, head, body;
+  esdg_block_split(src, n, sh, head, body);
+  const int tail = n - head - body;
+  if (k < 0 || k >= head + tail) return;
+  const int i = k < head ? k : head + body + (k - head);
+  esdg_cp_async(region + sh + i, src + i);
 }
+// edge slots per block: 2 (16/4 - 1) = 6 for float, rounded up
+#define ESDG_EDGE_SLOTS 8
 
 // x < y for non-negative doubles, compared as integers (no FP64-pipe compare)
 __device__ __forceinline__ bool esdg_lt_pos(double x, double y) {
@@ -316,9 +350,10 @@ int esdg_volume_batch_mixed(int what, int N, int variant, const EsdgMember* memb
 int esdg_volume_batch_variants_f64(int N);
 int esdg_volume_batch_variants_mixed(int N);
 
-// 1 if a bounded wait of the pipelined FP64 volume kernel ran out since the
-// last call (the flag is cleared), 0 if not, -1 on a CUDA error
-int esdg_volume_take_timeout();
+// 1 if a bounded wait of the pipelined FP64 / mixed volume kernels ran out
+// since the last call (the flag is cleared), 0 if not, -1 on a CUDA error
+int esdg_volume_f64_take_timeout();
+int esdg_volume_mixed_take_timeout();
 cudaError_t esdg_launch_volume_f64(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P, int mode,
                                    const EsdgVolArgs& a, cudaStream_t s);
 cudaError_t esdg_launch_volume_mixed(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P,

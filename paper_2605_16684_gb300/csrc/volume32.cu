@@ -3,6 +3,16 @@
 // launches and the persistent batched kernel with a background (two tile shapes).
 #include "volume_impl.cuh"
 
+int esdg_volume_mixed_take_timeout() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, esdg_vol::g_esdg_vol_timeout, sizeof(int)) != cudaSuccess) return -1;
+  if (v) {
+    const int z = 0;
+    if (cudaMemcpyToSymbol(esdg_vol::g_esdg_vol_timeout, &z, sizeof(int)) != cudaSuccess) return -1;
+  }
+  return v ? 1 : 0;
+}
+
 cudaError_t esdg_launch_volume_mixed(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P,
                                      int mode, const EsdgVolArgs& a, cudaStream_t s) {
   return esdg_vol::launch_volume_t<true>(g, L, P, mode, a, s);

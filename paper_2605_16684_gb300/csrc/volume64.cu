@@ -2,7 +2,7 @@
 // single-mesh launches and the persistent batched kernel (two tile shapes).
 #include "volume_impl.cuh"
 
-int esdg_volume_take_timeout() {
+int esdg_volume_f64_take_timeout() {
   int v = 0;
   if (cudaMemcpyFromSymbol(&v, esdg_vol::g_esdg_vol_timeout, sizeof(int)) != cudaSuccess) return -1;
   if (v) {

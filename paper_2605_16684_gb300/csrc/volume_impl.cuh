@@ -390,6 +390,75 @@ __device__ __forceinline__ bool out_of_series64(const double* S, int n) {
   return fabsf(rn - r0) > 0.0095f * r0 || fabsf(bn - b0) > 0.0095f * b0;
 }
 
+// Mixed-precision node prologue: FP32 primitives, the pressure recovered in
+// FP64 (E - rho phi cancels there), the geopotential relative to the
+// element's first node and, with a background, the FP64 perturbations
+// rho' = rho - rho_bg, b' = b - b_bg, p' = p - p_bg rounded to FP32.
+// Power-of-two factors are applied after rounding to FP32 (exact), so the
+// FP64 pipe only carries the cancelling differences: 11 FP64 instructions per
+// node with a background.
+template <int NP, bool BG>
+__device__ __forceinline__ void prims32(double q0, double q1, double q2, double q3, double q4,
+                                        double phi, double phi0, double gm1, float* S, int n,
+                                        double rb = 0.0, double bb = 0.0, double pbg = 0.0,
+                                        float* Bf = nullptr) {
+  const float q0f = esdg_d2f(q0), q1f = esdg_d2f(q1), q2f = esdg_d2f(q2), q3f = esdg_d2f(q3);
+  const float irf = esdg_rcpf(q0f);
+  const float hf = 0.5f * irf;
+  const float u0 = q1f * hf, u1 = q2f * hf, u2 = q3f * hf;
+  const float ke = fmaf(q3f, u2, fmaf(q2f, u1, q1f * u0));
+  const double p = gm1 * (fma(-q0, phi, q4) - esdg_f2d(ke));
+  const float pf = esdg_d2f(p);
+  const float rq = 0.25f * q0f;
+  S[0 * NP + n] = rq;
+  S[1 * NP + n] = rq * esdg_rcpf(pf);
+  S[2 * NP + n] = 2.0f * pf * irf;
+  S[3 * NP + n] = u0;
+  S[4 * NP + n] = u1;
+  S[5 * NP + n] = u2;
+  S[6 * NP + n] = 0.5f * esdg_d2f(phi - phi0);
+  if constexpr (BG) {
+    const double b = esdg_ldexp_n(q0, -1) * esdg_rcp(p);  // rho/(2p)
+    Bf[0 * NP + n] = 0.25f * esdg_d2f(q0 - rb);
+    Bf[1 * NP + n] = 0.5f * esdg_d2f(b - bb);
+    const float rbf = esdg_d2f(rb), bbf = esdg_d2f(bb);
+    Bf[2 * NP + n] = 0.25f * rbf;
+    Bf[3 * NP + n] = 0.5f * bbf;
+    Bf[4 * NP + n] = esdg_rcpf(bbf);
+    Bf[5 * NP + n] = esdg_d2f(pbg);
+    Bf[6 * NP + n] = esdg_d2f(p - pbg);
+  }
+}
+
+// Mixed-precision stage update of one node: r = -(1/J) (volume + lifts) in
+// FP32, plus the background's right-hand side and the Coriolis source, all in
+// FP32 (they join an FP32 increment); FP64 only in q += B dq.  Arrays are per
+// node with stride NP between variables: rbg (3, background rhs), qin (5),
+// dqold (5) may be in shared or global memory; dq and qio are the node's
+// global locations.
+template <int NP, bool BG>
+__device__ __forceinline__ void stage32(float (&r)[5], const double* rbg, const EsdgPhys& P,
+                                        double y, const double* qin, const float* dqold, float* dq,
+                                        double* qio, double rkA, double rkB, double dt) {
+  if constexpr (BG) {
+    r[1] += esdg_d2f(rbg[0]);
+    r[2] += esdg_d2f(rbg[NP]);
+    r[3] += esdg_d2f(rbg[2 * NP]);
+  }
+  if ((P.f0 != 0.0) || (P.beta != 0.0)) {
+    const float f = esdg_d2f(P.f0 + P.beta * (y - P.y0));
+    r[1] = fmaf(f, esdg_d2f(qin[2 * NP]), r[1]);
+    r[2] = fmaf(-f, esdg_d2f(qin[NP]), r[2]);
+  }
+  const float A = esdg_d2f(rkA), B = esdg_d2f(rkB), dtf = esdg_d2f(dt);
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const float dv = fmaf(A, dqold[(size_t)v * NP], dtf * r[v]);
+    dq[(size_t)v * NP] = dv;
+    qio[(size_t)v * NP] = qin[(size_t)v * NP] + esdg_f2d(B * dv);
+  }
+}
+
 // One tile: elements e0 .. e0 + EPB - 1 of one mesh, processed by a CTA of
 // SH::THREADS threads with SH::SMEM bytes of shared memory at smraw.
 template <int N, bool MIXED, int MODE, bool BG, int EPB_ = 0>
@@ -415,38 +484,13 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
                    q4 = qe[4 * NP + n];
       const double phi = a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP + n];
       if constexpr (MIXED) {
-        // FP64 only where the hydrostatic background cancels: E - rho phi - KE;
-        // conversions by integer repacking keep the FP64 pipe free
-        const float q0f = esdg_d2f(q0), q1f = esdg_d2f(q1), q2f = esdg_d2f(q2), q3f = esdg_d2f(q3);
-        const float irf = esdg_rcpf(q0f);
-        const float hf = 0.5f * irf;
-        const float u0 = q1f * hf, u1 = q2f * hf, u2 = q3f * hf;
-        const float ke = fmaf(q3f, u2, fmaf(q2f, u1, q1f * u0));
-        const double p = gm1 * (fma(-q0, phi, q4) - esdg_f2d(ke));
-        const float pf = esdg_d2f(p);
-        const float rq = 0.25f * q0f;
-        S[0 * NP + n] = rq;
-        S[1 * NP + n] = rq * esdg_rcpf(pf);
-        S[2 * NP + n] = 2.0f * pf * irf;
-        S[3 * NP + n] = u0;
-        S[4 * NP + n] = u1;
-        S[5 * NP + n] = u2;
         const double phi0 = a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP];
-        S[6 * NP + n] = esdg_d2f(0.5 * (phi - phi0));
         if constexpr (BG) {
-          // perturbations in FP64: rho' = rho - rho_bg, b' = rho/(2p) - b_bg
-          const double rb = a.bg[((size_t)e * 3 + 0) * NP + n];
-          const double bb = a.bg[((size_t)e * 3 + 1) * NP + n];
-          const double b = 0.5 * q0 * esdg_rcp(p);
-          const double pbg = a.bg[((size_t)e * 3 + 2) * NP + n];
-          R* Bf = S + SH::F_BG * NP;
-          Bf[0 * NP + n] = esdg_d2f(0.25 * (q0 - rb));
-          Bf[1 * NP + n] = esdg_d2f(0.5 * (b - bb));
-          Bf[2 * NP + n] = esdg_d2f(0.25 * rb);
-          Bf[3 * NP + n] = esdg_d2f(0.5 * bb);
-          Bf[4 * NP + n] = esdg_rcpf(esdg_d2f(bb));
-          Bf[5 * NP + n] = esdg_d2f(pbg);
-          Bf[6 * NP + n] = esdg_d2f(p - pbg);
+          const double* bge = a.bg + (size_t)e * 3 * NP;
+          prims32<NP, true>(q0, q1, q2, q3, q4, phi, phi0, gm1, S, n, bge[n], bge[NP + n],
+                            bge[2 * NP + n], S + SH::F_BG * NP);
+        } else {
+          prims32<NP, false>(q0, q1, q2, q3, q4, phi, phi0, gm1, S, n);
         }
       } else {
         prims64<NP>(q0, q1, q2, q3, q4, phi, gm1, S, n);
@@ -539,6 +583,19 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
     const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
     if (e2 >= E) continue;
     const R* S = sm + (size_t)el2 * NF * NP;
+    if constexpr (MIXED && MODE != 0) {
+      const float iJf = vg[((size_t)e2 * ESDG_NVGEO + 9) * NP + n];
+      float r32[5];
+#pragma unroll
+      for (int v = 0; v < 5; v++)
+        r32[v] = -iJf * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
+      const size_t qb = (size_t)e2 * 5 * NP + n;
+      const double y = rotating ? a.x[((size_t)e2 * 3 + 1) * NP + n] : 0.0;
+      float* dq = reinterpret_cast<float*>(a.dq);
+      stage32<NP, BG>(r32, BG ? a.rhs_bg + (size_t)e2 * 3 * NP + n : nullptr, P, y, a.q_in + qb,
+                      dq + qb, dq + qb, a.q_io + qb, a.rkA, a.rkB, a.dt);
+      continue;
+    }
     // FP64 stage update: dt is folded into the -1/J scale (r then holds dt rhs)
     constexpr bool DT_IN_R = !MIXED && MODE != 0;
     R iJ = vg[((size_t)e2 * ESDG_NVGEO + 9) * NP + n];
@@ -568,14 +625,7 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       for (int v = 0; v < 5; v++) a.rhs[qb + (size_t)v * NP] = r[v];
     } else {
       if constexpr (MIXED) {
-        float* dq = reinterpret_cast<float*>(a.dq);
-        const float A = esdg_d2f(a.rkA), B = esdg_d2f(a.rkB), dt = esdg_d2f(a.dt);
-#pragma unroll
-        for (int v = 0; v < 5; v++) {
-          const float dv = fmaf(A, dq[qb + (size_t)v * NP], dt * esdg_d2f(r[v]));
-          dq[qb + (size_t)v * NP] = dv;
-          a.q_io[qb + (size_t)v * NP] = a.q_in[qb + (size_t)v * NP] + esdg_f2d(B * dv);
-        }
+        // handled above
       } else {
         double* dq = reinterpret_cast<double*>(a.dq);
 #pragma unroll
@@ -637,7 +687,8 @@ __global__ void __launch_bounds__(Shape<N, MIXED, BG, EPB_>::THREADS)
 // completing on two mbarriers.  The arithmetic is that of
 // volume_tile<N, false, MODE, false>, in the same order.
 #define ESDG_WAIT_LIMIT (1u << 20)
-// set when a bounded wait of the pipelined kernel ran out (read by es_dg_sync)
+// set when a bounded wait of a pipelined kernel ran out (one flag per
+// translation unit; read and cleared through es_dg_sync)
 static __device__ int g_esdg_vol_timeout;
 
 template <int N, int MODE>
@@ -672,17 +723,32 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
   const double* dqg = reinterpret_cast<const double*>(a.dq);
   const int tid = threadIdx.x;
 
-  // thread 0 issues the copies of a tile's state and geometry (RAW)
-  auto issue_raw = [&](int tile) {
+  // the block copies of a tile's state and geometry (RAW), and of its dq (CUR)
+  auto raw_blocks = [&](int tile, auto&& f) {
     const int e0 = tile * EPB, ne = min(EPB, E - e0);
-    const double* qs = a.q_in + (size_t)e0 * 5 * NP;
-    const double* gs = vg + (size_t)e0 * ESDG_NVGEO * NP;
-    esdg_mbar_arrive_tx(&bars[0], esdg_block_bytes(qs, ne * 5 * NP) +
-                                      esdg_block_bytes(gs, ne * ESDG_NVGEO * NP));
-    esdg_fence_proxy_async();
-    esdg_block_g2s(sm + PP::RAW_Q, qs, ne * 5 * NP, &bars[0]);
-    esdg_block_g2s(sm + PP::RAW_G, gs, ne * ESDG_NVGEO * NP, &bars[0]);
+    f(sm + PP::RAW_Q, a.q_in + (size_t)e0 * 5 * NP, ne * 5 * NP);
+    f(sm + PP::RAW_G, vg + (size_t)e0 * ESDG_NVGEO * NP, ne * ESDG_NVGEO * NP);
   };
+  auto cur_blocks = [&](int tile, auto&& f) {
+    const int e0 = tile * EPB, ne = min(EPB, E - e0);
+    if constexpr (MODE != 0) f(sm + PP::DQ, dqg + (size_t)e0 * 5 * NP, ne * 5 * NP);
+  };
+  // thread 0: expect_tx on the barrier, then the bulk interiors
+  auto issue_bulk = [&](int tile, auto&& blocks, unsigned long long* bar) {
+    unsigned bytes = 0;
+    blocks(tile, [&](auto* r, const auto* src, int n) { bytes += esdg_block_bytes(src, n); });
+    esdg_mbar_arrive_tx(bar, bytes);
+    esdg_fence_proxy_async();
+    blocks(tile, [&](auto* r, const auto* src, int n) { esdg_block_bulk(r, src, n, bar); });
+  };
+  // every thread: its edge slot (if any) of the blocks, by cp.async
+  auto issue_edges = [&](int tile, auto&& blocks, int& bi) {
+    blocks(tile, [&](auto* r, const auto* src, int n) {
+      const int k = tid - ESDG_EDGE_SLOTS * bi++;
+      if (k >= 0 && k < ESDG_EDGE_SLOTS) esdg_block_edge(r, src, n, k);
+    });
+  };
+  static_assert(T >= 3 * ESDG_EDGE_SLOTS, "edge slots");
 
   if (tid == 0) {
     esdg_mbar_init(&bars[0], 1);
@@ -691,10 +757,15 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
   }
   __syncthreads();
   int tile = blockIdx.x;
-  if (tid == 0 && tile < ntiles) issue_raw(tile);
+  if (tile < ntiles) {
+    if (tid == 0) issue_bulk(tile, raw_blocks, &bars[0]);
+    int bi = 0;
+    issue_edges(tile, raw_blocks, bi);
+  }
   unsigned ph_raw = 0, ph_dq = 0;
   for (; tile < ntiles; tile += gridDim.x) {
     const int e0 = tile * EPB;
+    esdg_cp_async_wait_all();  // this thread's edge copies
     const bool ok = esdg_mbar_wait(&bars[0], ph_raw, ESDG_WAIT_LIMIT);
     ph_raw ^= 1u;
     if (__syncthreads_or(!ok)) {
@@ -732,15 +803,15 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
       }
     }
     __syncthreads();  // RAW consumed
-    if (tid == 0) {
-      if constexpr (MODE != 0) {
-        const int ne = min(EPB, E - e0);
-        const double* ds = dqg + (size_t)e0 * 5 * NP;
-        esdg_mbar_arrive_tx(&bars[1], esdg_block_bytes(ds, ne * 5 * NP));
-        esdg_fence_proxy_async();
-        esdg_block_g2s(sm + PP::DQ, ds, ne * 5 * NP, &bars[1]);
+    {
+      const int next = tile + (int)gridDim.x;
+      if (tid == 0) {
+        if constexpr (MODE != 0) issue_bulk(tile, cur_blocks, &bars[1]);
+        if (next < ntiles) issue_bulk(next, raw_blocks, &bars[0]);
       }
-      if (tile + (int)gridDim.x < ntiles) issue_raw(tile + gridDim.x);
+      int bi = 0;
+      issue_edges(tile, cur_blocks, bi);
+      if (next < ntiles) issue_edges(next, raw_blocks, bi);
     }
 
     int need_logs = 0;
@@ -792,6 +863,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
         for (int v = 0; v < 5; v++) S[(d * 5 + v) * NP + base + i * stride] = acc[i][v];
     }
     if constexpr (MODE != 0) {
+      esdg_cp_async_wait_all();
       const bool okd = esdg_mbar_wait(&bars[1], ph_dq, ESDG_WAIT_LIMIT);  // this tile's dq
       ph_dq ^= 1u;
       if (__syncthreads_or(!okd)) {
@@ -870,6 +942,286 @@ cudaError_t launch_pipe64(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L
   return cudaGetLastError();
 }
 
+// ---- pipelined persistent mixed-precision kernel (with a background) ------
+// The same tile pipeline for the FP32 pairs: the copy engine brings the next
+// tile's FP64 state, FP64 geopotential, FP32 geometry and FP64 background
+// (RAW) and, after this tile's prologue, its dq and background right-hand
+// side (CUR).  The arithmetic is that of volume_tile<N, true, MODE, true>, in
+// the same order.
+// dynamic shared memory a pipelined tile may use (227 KB less static use)
+#define ESDG_PIPE_SMEM_MAX (232448 - 1024)
+
+template <int N, int MODE>
+struct Pipe32 {
+  using SH = Shape<N, true, true>;
+  static constexpr int NP = SH::NP, EPB = SH::EPB, P = NP * EPB;
+  static constexpr int up16(int b) { return (b + 15) & ~15; }
+  // byte offsets, 16-byte aligned; copy targets hold 16 extra bytes
+  static constexpr int RAW_Q = 0;                                  // [el][5][NP]  double
+  static constexpr int PHS = (NP + 2) & ~1;  // even per-element stride: every target 16-byte aligned
+  static constexpr int RAW_PHI = up16(RAW_Q + 8 * (5 * P + 1));    // [el][PHS]    double
+  static constexpr int RAW_BG = up16(RAW_PHI + 8 * EPB * PHS);     // [el][3][NP]  double
+  static constexpr int RAW_G = up16(RAW_BG + 8 * (3 * P + 1));     // [el][11][NP] float
+  static constexpr int S0 = up16(RAW_G + 4 * (ESDG_NVGEO * P + 3));  // [el][NF][NP] float
+  static constexpr int EPI_Q = up16(S0 + 4 * SH::NF * P);         // [el][5][NP]  double
+  static constexpr int EPI_J = up16(EPI_Q + 8 * 5 * P);           // [el][NP]     float
+  static constexpr int CUR_RB = up16(EPI_J + 4 * P);              // [el][3][NP]  double
+  static constexpr int CUR_DQ = up16(CUR_RB + 8 * (3 * P + 1));   // [el][5][NP]  float
+  static constexpr int TOTAL = MODE ? up16(CUR_DQ + 4 * (5 * P + 3)) : CUR_DQ;
+  static constexpr size_t SMEM = (size_t)TOTAL;
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
+    k_volume_pipe32(EsdgGrid g, EsdgPhys P, EsdgLGL L, EsdgVolArgs a, int ntiles) {
+  using SH = Shape<N, true, true>;
+  using PP = Pipe32<N, MODE>;
+  constexpr int Nq = SH::Nq, NP = SH::NP, NPEN = SH::NPEN, EPB = SH::EPB, NF = SH::NF;
+  constexpr int T = SH::THREADS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ unsigned long long bars[2];  // [0] RAW of the next tile, [1] CUR of this tile
+  __shared__ float phi0s[EPB];           // each element's reference geopotential
+  double* const rawq = reinterpret_cast<double*>(smraw + PP::RAW_Q);
+  double* const rawphi = reinterpret_cast<double*>(smraw + PP::RAW_PHI);
+  double* const rawbg = reinterpret_cast<double*>(smraw + PP::RAW_BG);
+  float* const rawg = reinterpret_cast<float*>(smraw + PP::RAW_G);
+  float* const sm = reinterpret_cast<float*>(smraw + PP::S0);
+  double* const epq = reinterpret_cast<double*>(smraw + PP::EPI_Q);
+  float* const epj = reinterpret_cast<float*>(smraw + PP::EPI_J);
+  double* const currb = reinterpret_cast<double*>(smraw + PP::CUR_RB);
+  float* const curdq = reinterpret_cast<float*>(smraw + PP::CUR_DQ);
+  const int E = g.E;
+  const float* vg = reinterpret_cast<const float*>(a.vgeo);
+  const float* dqg = reinterpret_cast<const float*>(a.dq);
+  const int tid = threadIdx.x;
+
+  auto phi_src = [&](int e) { return a.vgeo64 + ((size_t)e * ESDG_NVGEO + 10) * NP; };
+  // the block copies of a tile's RAW and CUR data (EPB + 5 blocks at most)
+  auto raw_blocks = [&](int tile, auto&& f) {
+    const int e0 = tile * EPB, ne = min(EPB, E - e0);
+    f(rawq, a.q_in + (size_t)e0 * 5 * NP, ne * 5 * NP);
+    f(rawbg, a.bg + (size_t)e0 * 3 * NP, ne * 3 * NP);
+    f(rawg, vg + (size_t)e0 * ESDG_NVGEO * NP, ne * ESDG_NVGEO * NP);
+    for (int el = 0; el < ne; el++) f(rawphi + (size_t)el * PP::PHS, phi_src(e0 + el), NP);
+  };
+  auto cur_blocks = [&](int tile, auto&& f) {
+    const int e0 = tile * EPB, ne = min(EPB, E - e0);
+    f(currb, a.rhs_bg + (size_t)e0 * 3 * NP, ne * 3 * NP);
+    if constexpr (MODE != 0) f(curdq, dqg + (size_t)e0 * 5 * NP, ne * 5 * NP);
+  };
+  auto issue_bulk = [&](int tile, auto&& blocks, unsigned long long* bar) {
+    unsigned bytes = 0;
+    blocks(tile, [&](auto* r, const auto* src, int n) { bytes += esdg_block_bytes(src, n); });
+    esdg_mbar_arrive_tx(bar, bytes);
+    esdg_fence_proxy_async();
+    blocks(tile, [&](auto* r, const auto* src, int n) { esdg_block_bulk(r, src, n, bar); });
+  };
+  auto issue_edges = [&](int tile, auto&& blocks, int& bi) {
+    blocks(tile, [&](auto* r, const auto* src, int n) {
+      const int k = tid - ESDG_EDGE_SLOTS * bi++;
+      if (k >= 0 && k < ESDG_EDGE_SLOTS) esdg_block_edge(r, src, n, k);
+    });
+  };
+  static_assert(T >= (EPB + 5) * ESDG_EDGE_SLOTS, "edge slots");
+
+  if (tid == 0) {
+    esdg_mbar_init(&bars[0], 1);
+    esdg_mbar_init(&bars[1], 1);
+    esdg_fence_mbar_init();
+  }
+  __syncthreads();
+  int tile = blockIdx.x;
+  if (tile < ntiles) {
+    if (tid == 0) issue_bulk(tile, raw_blocks, &bars[0]);
+    int bi = 0;
+    issue_edges(tile, raw_blocks, bi);
+  }
+  unsigned ph_raw = 0, ph_cur = 0;
+  const double gm1 = P.gamma - 1.0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int e0 = tile * EPB;
+    esdg_cp_async_wait_all();  // this thread's edge copies
+    const bool ok = esdg_mbar_wait(&bars[0], ph_raw, ESDG_WAIT_LIMIT);
+    ph_raw ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(&g_esdg_vol_timeout, 1);
+      return;
+    }
+    // ---- prologue -------------------------------------------------------------
+    {
+      const double* qr0 = rawq + esdg_block_shift(a.q_in + (size_t)e0 * 5 * NP);
+      const double* br0 = rawbg + esdg_block_shift(a.bg + (size_t)e0 * 3 * NP);
+      const float* gr0 = rawg + esdg_block_shift(vg + (size_t)e0 * ESDG_NVGEO * NP);
+      for (int idx = tid; idx < EPB * NP; idx += T) {
+        const int el2 = idx / NP, n = idx - el2 * NP;
+        float* S = sm + (size_t)el2 * NF * NP;
+        if (e0 + el2 < E) {
+          const double* qr = qr0 + (size_t)el2 * 5 * NP;
+          const double* br = br0 + (size_t)el2 * 3 * NP;
+          const float* gr = gr0 + (size_t)el2 * ESDG_NVGEO * NP;
+          const double* phr = rawphi + (size_t)el2 * PP::PHS + esdg_block_shift(phi_src(e0 + el2));
+          const double q0 = qr[n], q1 = qr[NP + n], q2 = qr[2 * NP + n], q3 = qr[3 * NP + n],
+                       q4 = qr[4 * NP + n];
+          const double phi0 = phr[0];
+          prims32<NP, true>(q0, q1, q2, q3, q4, phr[n], phi0, gm1, S, n, br[n], br[NP + n],
+                            br[2 * NP + n], S + SH::F_BG * NP);
+          if (n == 0) phi0s[el2] = esdg_d2f(phi0);
+#pragma unroll
+          for (int k = 0; k < 9; k++) S[(SH::F_NH + k) * NP + n] = gr[k * NP + n];
+          double* X = epq + (size_t)el2 * 5 * NP;
+          X[n] = q0;
+          X[NP + n] = q1;
+          X[2 * NP + n] = q2;
+          X[3 * NP + n] = q3;
+          X[4 * NP + n] = q4;
+          epj[(size_t)el2 * NP + n] = gr[9 * NP + n];
+        } else {  // padding element: any valid state, results are discarded
+          S[0 * NP + n] = 0.25f;
+          S[1 * NP + n] = 0.5f;
+          S[2 * NP + n] = 1.0f;
+          for (int k = 3; k < NF; k++) S[k * NP + n] = 0.0f;
+        }
+      }
+    }
+    __syncthreads();  // RAW consumed
+    {
+      const int next = tile + (int)gridDim.x;
+      if (tid == 0) {
+        issue_bulk(tile, cur_blocks, &bars[1]);
+        if (next < ntiles) issue_bulk(next, raw_blocks, &bars[0]);
+      }
+      int bi = 0;
+      issue_edges(tile, cur_blocks, bi);
+      if (next < ntiles) issue_edges(next, raw_blocks, bi);
+    }
+
+    int need_logs = 0;
+    for (int idx = tid; idx < EPB * NP; idx += T) {
+      const int el2 = idx / NP, n = idx - el2 * NP;
+      const float* S = sm + (size_t)el2 * NF * NP;
+      const float r0 = S[0], rn = S[n], b0 = S[NP], bn = S[NP + n];
+      // |f| < 0.14 keeps u < ESDG_LOG_EPS32 for every pair
+      if (fabsf(rn - r0) > 0.13f * r0 || fabsf(bn - b0) > 0.13f * b0) need_logs = 1;
+    }
+    need_logs = __syncthreads_or(need_logs);
+
+    // ---- pair pass ------------------------------------------------------------
+    const bool active = tid < SH::PENCILS;
+    const int el = active ? tid / (3 * NPEN) : 0;
+    const int rr = tid - el * 3 * NPEN;
+    const int d = active ? rr / NPEN : 0;
+    const int pen = rr - d * NPEN;
+    const int ps = pen % Nq, pt = pen / Nq;
+    const int stride = (d == 0) ? 1 : ((d == 1) ? Nq : Nq * Nq);
+    const int base = (d == 0) ? Nq * (ps + Nq * pt) : ((d == 1) ? (ps + Nq * Nq * pt) : (ps + Nq * pt));
+    const int e = e0 + el;
+    float acc[Nq][5];
+#pragma unroll
+    for (int i = 0; i < Nq; i++)
+#pragma unroll
+      for (int v = 0; v < 5; v++) acc[i][v] = 0.0f;
+    if (active && e < E) {
+      const float* S = sm + (size_t)el * NF * NP;
+      const float ce = esdg_d2f(0.5 * P.igm1);
+      if (need_logs)
+        pencil_pass<N, true, true, true>(S, d, base, stride, L, ce, acc);
+      else
+        pencil_pass<N, true, false, true>(S, d, base, stride, L, ce, acc);
+      const float phi0 = phi0s[el];
+#pragma unroll
+      for (int i = 0; i < Nq; i++) acc[i][4] = fmaf(phi0, acc[i][0], acc[i][4]);
+      face_lift<false, N, float>(g, a, e, d, ps + Nq * pt, acc);
+    }
+    __syncthreads();
+    if (active && e < E) {
+      float* S = sm + (size_t)el * NF * NP;
+#pragma unroll
+      for (int i = 0; i < Nq; i++)
+#pragma unroll
+        for (int v = 0; v < 5; v++) S[(d * 5 + v) * NP + base + i * stride] = acc[i][v];
+    }
+    esdg_cp_async_wait_all();
+    const bool okc = esdg_mbar_wait(&bars[1], ph_cur, ESDG_WAIT_LIMIT);
+    ph_cur ^= 1u;
+    if (__syncthreads_or(!okc)) {
+      if (tid == 0) atomicExch(&g_esdg_vol_timeout, 1);
+      return;
+    }
+
+    // ---- epilogue: one thread per node ----------------------------------------
+    const double* RB0 = currb + esdg_block_shift(a.rhs_bg + (size_t)e0 * 3 * NP);
+    const float* D0 = curdq + esdg_block_shift(dqg + (size_t)e0 * 5 * NP);
+    for (int idx = tid; idx < EPB * NP; idx += T) {
+      const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
+      if (e2 >= E) continue;
+      const float* S = sm + (size_t)el2 * NF * NP;
+      const double* X = epq + (size_t)el2 * 5 * NP;
+      const float iJ = epj[(size_t)el2 * NP + n];
+      const double* RB = RB0 + (size_t)el2 * 3 * NP;
+      const size_t qb = (size_t)e2 * 5 * NP + n;
+      if constexpr (MODE != 0) {
+        float r32[5];
+#pragma unroll
+        for (int v = 0; v < 5; v++)
+          r32[v] = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
+        const double y = ((P.f0 != 0.0) || (P.beta != 0.0)) ? a.x[((size_t)e2 * 3 + 1) * NP + n] : 0.0;
+        float* dq = reinterpret_cast<float*>(a.dq);
+        stage32<NP, true>(r32, RB + n, P, y, X + n, D0 + (size_t)el2 * 5 * NP + n, dq + qb,
+                          a.q_io + qb, a.rkA, a.rkB, a.dt);
+        continue;
+      }
+      double r[5];
+#pragma unroll
+      for (int v = 0; v < 5; v++) {
+        const float rv = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
+        r[v] = esdg_f2d(rv);
+      }
+      r[1] += RB[n];
+      r[2] += RB[NP + n];
+      r[3] += RB[2 * NP + n];
+      if ((P.f0 != 0.0) || (P.beta != 0.0)) {
+        const double y = a.x[((size_t)e2 * 3 + 1) * NP + n];
+        const double f = P.f0 + P.beta * (y - P.y0);
+        r[1] = fma(f, X[2 * NP + n], r[1]);
+        r[2] = fma(-f, X[NP + n], r[2]);
+      }
+#pragma unroll
+      for (int v = 0; v < 5; v++) a.rhs[qb + (size_t)v * NP] = r[v];
+    }
+  }
+}
+
+template <int N, int MODE>
+cudaError_t launch_pipe32(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
+                          const EsdgVolArgs& a, cudaStream_t s) {
+  using SH = Shape<N, true, true>;
+  using PP = Pipe32<N, MODE>;
+  constexpr int MAXDEV = 64;
+  static int grid_cap[MAXDEV];
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
+  if (grid_cap[dev] == 0) {
+    err = cudaFuncSetAttribute(k_volume_pipe32<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)PP::SMEM);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0, nsm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_volume_pipe32<N, MODE>,
+                                                        SH::THREADS, PP::SMEM);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    grid_cap[dev] = per_sm * nsm;
+  }
+  const int ntiles = (g.E + SH::EPB - 1) / SH::EPB;
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = ntiles < grid_cap[dev] ? ntiles : grid_cap[dev];
+  k_volume_pipe32<N, MODE><<<grid, SH::THREADS, PP::SMEM, s>>>(g, P, L, a, ntiles);
+  return cudaGetLastError();
+}
+
 template <int N, bool MIXED, int MODE, bool BG>
 cudaError_t launch_one(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
                        const EsdgVolArgs& a, cudaStream_t s) {
@@ -897,11 +1249,17 @@ cudaError_t launch_volume_t(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys&
       return mode ? launch_pipe64<NN, 1>(g, P, L, a, s)                        \
                   : launch_pipe64<NN, 0>(g, P, L, a, s);                       \
     }                                                                          \
-    if (MIXED && a.bg)                                                         \
-      return mode ? launch_one<NN, MIXED, 1, MIXED>(g, P, L, a, s)             \
-                  : launch_one<NN, MIXED, 0, MIXED>(g, P, L, a, s);            \
-    return mode ? launch_one<NN, MIXED, 1, false>(g, P, L, a, s)               \
-                : launch_one<NN, MIXED, 0, false>(g, P, L, a, s);
+    if constexpr (MIXED) {                                                     \
+      if (a.bg) {                                                              \
+        if constexpr (Pipe32<NN, 1>::SMEM <= ESDG_PIPE_SMEM_MAX)               \
+          return mode ? launch_pipe32<NN, 1>(g, P, L, a, s)                    \
+                      : launch_pipe32<NN, 0>(g, P, L, a, s);                   \
+        return mode ? launch_one<NN, MIXED, 1, true>(g, P, L, a, s)            \
+                    : launch_one<NN, MIXED, 0, true>(g, P, L, a, s);           \
+      }                                                                        \
+      return mode ? launch_one<NN, MIXED, 1, false>(g, P, L, a, s)             \
+                  : launch_one<NN, MIXED, 0, false>(g, P, L, a, s);            \
+    }
   switch (g.N) {
     ESDG_CASE(1)
     ESDG_CASE(2)
