@@ -249,21 +249,6 @@ __device__ __forceinline__ void face_flux_bg(const Side<float>& M, const Side<fl
   F[4] -= half * ((c1 + c5) * H + a * un * cdif + c2 * k2 + ls * (u0 * t0 + u1 * t1 + u2 * t2));
 }
 
-// FP64 primitives of one side
-struct Side64 {
-  double rho, u0, u1, u2, b;
-};
-__device__ __forceinline__ Side64 side64(const double* q, double phi, double gm1) {
-  const double rho = q[0];
-  const double ir = esdg_rcp(rho);
-  const double u0 = q[1] * ir, u1 = q[2] * ir, u2 = q[3] * ir;
-  double e = fma(-rho, phi, q[4]);
-  e = fma(-0.5 * q[1], u0, e);
-  e = fma(-0.5 * q[2], u1, e);
-  e = fma(-0.5 * q[3], u2, e);
-  return Side64{rho, u0, u1, u2, 0.5 * rho * esdg_rcp(gm1 * e)};
-}
-
 // One face node (global face-node index tid) of one mesh.
 template <typename R, int N, bool BG>
 __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
@@ -327,21 +312,60 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
   const double gm1 = P.gamma - 1.0;
   R F[5];
   if constexpr (BG) {
-    const Side64 m = side64(qm, phi, gm1), p = side64(qp, phi, gm1);
+    // FP64 only where the state cancels (13 instructions): each side's pressure
+    // E - rho phi - KE (KE in FP32), and the jumps of rho, rho u and p.  The
+    // jumps of b, b u, b |u|^2 and the pressure mean follow from them by exact
+    // identities evaluated in FP32, with ({{.}} the two-side average):
+    //   [[b]] = (rho+ p- - rho- p+)/(2 p+ p-),  rho+ p- - rho- p+ = [[rho]] {{p}} - {{rho}} [[p]],
+    //   [[u]] = [[rho u]] {{1/rho}} - {{rho u}} [[rho]]/(rho+ rho-),
+    //   [[x y]] = [[x]] {{y}} + {{x}} [[y]]  (for b u and (b u) . u),
+    //   p* - p_bg = {{p}} - p_bg + [[p]] (rho+ p- - rho- p+)/(2 D),
+    //   D = rho+ p- + rho- p+ = 2 {{rho}} {{p}} - [[rho]] [[p]]/2.
     const int eb = (em >= 0) ? em : ep, nb = (em >= 0) ? nm : npn;
     const double pbg = bg[((size_t)eb * 3 + 2) * NP + nb];
+    float mf[5], pf5[5];
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      mf[v] = esdg_d2f(qm[v]);
+      pf5[v] = esdg_d2f(qp[v]);
+    }
+    const float irm = esdg_rcpf(mf[0]), irp = esdg_rcpf(pf5[0]);
+    const Side<float> M{mf[0], mf[1] * irm, mf[2] * irm, mf[3] * irm, 0.0f};
+    Side<float> Pp{pf5[0], pf5[1] * irp, pf5[2] * irp, pf5[3] * irp, 0.0f};
+    const float kem = 0.5f * fmaf(mf[3], M.u2, fmaf(mf[2], M.u1, mf[1] * M.u0));
+    const float kep = 0.5f * fmaf(pf5[3], Pp.u2, fmaf(pf5[2], Pp.u1, pf5[1] * Pp.u0));
+    const double prm = gm1 * (fma(-qm[0], phi, qm[4]) - esdg_f2d(kem));
+    const double prp = gm1 * (fma(-qp[0], phi, qp[4]) - esdg_f2d(kep));
+    const float pmf = esdg_d2f(prm), ppf = esdg_d2f(prp);
+    Side<float> Mb = M;
+    Mb.b = 0.5f * M.rho * esdg_rcpf(pmf);
+    Pp.b = 0.5f * Pp.rho * esdg_rcpf(ppf);
+    const float dr = esdg_d2f(qp[0] - qm[0]);
+    const float dm0 = esdg_d2f(qp[1] - qm[1]), dm1 = esdg_d2f(qp[2] - qm[2]),
+                dm2 = esdg_d2f(qp[3] - qm[3]);
+    const float dp = esdg_d2f(prp - prm);
+    const float pbar_p = esdg_d2f(esdg_ldexp_n(prp + prm, -1) - pbg);  // {{p}} - p_bg
+    const float rbar = 0.5f * (Pp.rho + Mb.rho), pbar = 0.5f * (ppf + pmf);
+    const float X = fmaf(dr, pbar, -rbar * dp);  // rho+ p- - rho- p+
     BgFace J;
-    J.dr = esdg_d2f(p.rho - m.rho);
-    J.db = esdg_d2f(p.b - m.b);
-    J.dbu0 = esdg_d2f(p.b * p.u0 - m.b * m.u0);
-    J.dbu1 = esdg_d2f(p.b * p.u1 - m.b * m.u1);
-    J.dbu2 = esdg_d2f(p.b * p.u2 - m.b * m.u2);
-    J.dbuu = esdg_d2f(p.b * (p.u0 * p.u0 + p.u1 * p.u1 + p.u2 * p.u2) -
-                      m.b * (m.u0 * m.u0 + m.u1 * m.u1 + m.u2 * m.u2));
-    J.ptp = esdg_d2f(0.5 * (p.rho + m.rho) * esdg_rcp(p.b + m.b) - pbg);  // p* - p_bg
-    const Side<float> M{esdg_d2f(m.rho), esdg_d2f(m.u0), esdg_d2f(m.u1), esdg_d2f(m.u2), esdg_d2f(m.b)};
-    const Side<float> Pp{esdg_d2f(p.rho), esdg_d2f(p.u0), esdg_d2f(p.u1), esdg_d2f(p.u2), esdg_d2f(p.b)};
-    face_flux_bg(M, Pp, esdg_d2f(phi), esdg_d2f(n0), esdg_d2f(n1), esdg_d2f(n2), esdg_d2f(P.gamma),
+    J.dr = dr;
+    J.db = X * esdg_rcpf(2.0f * ppf * pmf);
+    const float irbar = 0.5f * (irp + irm), dirr = dr * irp * irm;
+    const float du0 = fmaf(dm0, irbar, -0.5f * (pf5[1] + mf[1]) * dirr);
+    const float du1 = fmaf(dm1, irbar, -0.5f * (pf5[2] + mf[2]) * dirr);
+    const float du2 = fmaf(dm2, irbar, -0.5f * (pf5[3] + mf[3]) * dirr);
+    const float ub0 = 0.5f * (Pp.u0 + Mb.u0), ub1 = 0.5f * (Pp.u1 + Mb.u1), ub2 = 0.5f * (Pp.u2 + Mb.u2);
+    const float bbar = 0.5f * (Pp.b + Mb.b);
+    J.dbu0 = fmaf(J.db, ub0, bbar * du0);
+    J.dbu1 = fmaf(J.db, ub1, bbar * du1);
+    J.dbu2 = fmaf(J.db, ub2, bbar * du2);
+    const float bu0 = 0.5f * (Pp.b * Pp.u0 + Mb.b * Mb.u0), bu1 = 0.5f * (Pp.b * Pp.u1 + Mb.b * Mb.u1),
+                bu2 = 0.5f * (Pp.b * Pp.u2 + Mb.b * Mb.u2);
+    J.dbuu = fmaf(J.dbu0, ub0, fmaf(J.dbu1, ub1, fmaf(J.dbu2, ub2,
+                  fmaf(bu0, du0, fmaf(bu1, du1, bu2 * du2)))));
+    const float D = fmaf(2.0f * rbar, pbar, -0.5f * dr * dp);
+    J.ptp = fmaf(dp * X, esdg_rcpf(2.0f * D), pbar_p);
+    face_flux_bg(Mb, Pp, esdg_d2f(phi), esdg_d2f(n0), esdg_d2f(n1), esdg_d2f(n2), esdg_d2f(P.gamma),
                  esdg_d2f(P.igm1), esdg_d2f(P.igamma), P.dissipation, J, F);
   } else {
     const Side<R> M = side_from<R>(qm, phi, gm1), Pp = side_from<R>(qp, phi, gm1);
