@@ -1168,25 +1168,25 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
         float* dq = reinterpret_cast<float*>(a.dq);
         stage32<NP, true>(r32, RB + n, P, y, X + n, D0 + (size_t)el2 * 5 * NP + n, dq + qb,
                           a.q_io + qb, a.rkA, a.rkB, a.dt);
-        continue;
-      }
-      double r[5];
+      } else {  // right-hand side in FP64
+        double r[5];
 #pragma unroll
-      for (int v = 0; v < 5; v++) {
-        const float rv = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
-        r[v] = esdg_f2d(rv);
-      }
-      r[1] += RB[n];
-      r[2] += RB[NP + n];
-      r[3] += RB[2 * NP + n];
-      if ((P.f0 != 0.0) || (P.beta != 0.0)) {
-        const double y = a.x[((size_t)e2 * 3 + 1) * NP + n];
-        const double f = P.f0 + P.beta * (y - P.y0);
-        r[1] = fma(f, X[2 * NP + n], r[1]);
-        r[2] = fma(-f, X[NP + n], r[2]);
-      }
+        for (int v = 0; v < 5; v++) {
+          const float rv = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
+          r[v] = esdg_f2d(rv);
+        }
+        r[1] += RB[n];
+        r[2] += RB[NP + n];
+        r[3] += RB[2 * NP + n];
+        if ((P.f0 != 0.0) || (P.beta != 0.0)) {
+          const double y = a.x[((size_t)e2 * 3 + 1) * NP + n];
+          const double f = P.f0 + P.beta * (y - P.y0);
+          r[1] = fma(f, X[2 * NP + n], r[1]);
+          r[2] = fma(-f, X[NP + n], r[2]);
+        }
 #pragma unroll
-      for (int v = 0; v < 5; v++) a.rhs[qb + (size_t)v * NP] = r[v];
+        for (int v = 0; v < 5; v++) a.rhs[qb + (size_t)v * NP] = r[v];
+      }
     }
   }
 }
