@@ -79,12 +79,14 @@ __global__ void k_geometry(EsdgGrid g, EsdgLGL L, EsdgPhys P, double* __restrict
     Jd = dd_add(Jd, dd_mul(a1, dd_sub(dd_mul(b2, c0), dd_mul(b0, c2))));
     Jd = dd_add(Jd, dd_mul(a2, dd_sub(dd_mul(b0, c1), dd_mul(b1, c0))));
     const double J = Jd.hi;
-    const double z = X[2 * np + n].hi;
+    const double z = X[2 * np + n].hi, z0 = X[2 * np].hi;
     Jo[(size_t)e * np + n] = J;
     vgeo[((size_t)e * ESDG_NVGEO + 9) * np + n] = 1.0 / J;
     vgeo[((size_t)e * ESDG_NVGEO + 10) * np + n] = P.g * z;
     vgeo32[((size_t)e * ESDG_NVGEO + 9) * np + n] = (float)(1.0 / J);
-    vgeo32[((size_t)e * ESDG_NVGEO + 10) * np + n] = (float)(P.g * z);
+    // FP32 geometry carries (phi - phi_0)/2, phi_0 at the element's first node
+    // (the mixed kernels' pair geopotential)
+    vgeo32[((size_t)e * ESDG_NVGEO + 10) * np + n] = 0.5f * (float)(P.g * z - P.g * z0);
   }
   // curl form, one physical component c at a time
   for (int c = 0; c < 3; c++) {

@@ -391,15 +391,16 @@ __device__ __forceinline__ bool out_of_series64(const double* S, int n) {
 }
 
 // Mixed-precision node prologue: FP32 primitives, the pressure recovered in
-// FP64 (E - rho phi cancels there), the geopotential relative to the
-// element's first node and, with a background, the FP64 perturbations
-// rho' = rho - rho_bg, b' = b - b_bg, p' = p - p_bg rounded to FP32.
-// Power-of-two factors are applied after rounding to FP32 (exact), so the
-// FP64 pipe only carries the cancelling differences: 11 FP64 instructions per
-// node with a background.
+// FP64 (E - rho phi cancels there) and, with a background, the FP64
+// perturbations rho' = rho - rho_bg and p' = p - p_bg rounded to FP32; the
+// perturbation of b = rho/(2p) follows exactly from them,
+//   b - b_bg = (rho' p_bg - rho_bg p') / (2 p p_bg),
+// evaluated in FP32 (its rounding is relative to the perturbations).  phh is
+// the geopotential relative to the element's first node, halved (FP32
+// geometry).  5 FP64 instructions per node with a background.
 template <int NP, bool BG>
 __device__ __forceinline__ void prims32(double q0, double q1, double q2, double q3, double q4,
-                                        double phi, double phi0, double gm1, float* S, int n,
+                                        double phi, float phh, double gm1, float* S, int n,
                                         double rb = 0.0, double bb = 0.0, double pbg = 0.0,
                                         float* Bf = nullptr) {
   const float q0f = esdg_d2f(q0), q1f = esdg_d2f(q1), q2f = esdg_d2f(q2), q3f = esdg_d2f(q3);
@@ -416,17 +417,17 @@ __device__ __forceinline__ void prims32(double q0, double q1, double q2, double 
   S[3 * NP + n] = u0;
   S[4 * NP + n] = u1;
   S[5 * NP + n] = u2;
-  S[6 * NP + n] = 0.5f * esdg_d2f(phi - phi0);
+  S[6 * NP + n] = phh;
   if constexpr (BG) {
-    const double b = esdg_ldexp_n(q0, -1) * esdg_rcp(p);  // rho/(2p)
-    Bf[0 * NP + n] = 0.25f * esdg_d2f(q0 - rb);
-    Bf[1 * NP + n] = 0.5f * esdg_d2f(b - bb);
-    const float rbf = esdg_d2f(rb), bbf = esdg_d2f(bb);
+    const float rpf = esdg_d2f(q0 - rb), ppf = esdg_d2f(p - pbg);
+    const float rbf = esdg_d2f(rb), bbf = esdg_d2f(bb), pbf = esdg_d2f(pbg);
+    Bf[0 * NP + n] = 0.25f * rpf;
+    Bf[1 * NP + n] = 0.25f * fmaf(rpf, pbf, -rbf * ppf) * esdg_rcpf(pf * pbf);  // b'/2
     Bf[2 * NP + n] = 0.25f * rbf;
     Bf[3 * NP + n] = 0.5f * bbf;
     Bf[4 * NP + n] = esdg_rcpf(bbf);
-    Bf[5 * NP + n] = esdg_d2f(pbg);
-    Bf[6 * NP + n] = esdg_d2f(p - pbg);
+    Bf[5 * NP + n] = pbf;
+    Bf[6 * NP + n] = ppf;
   }
 }
 
@@ -484,13 +485,13 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
                    q4 = qe[4 * NP + n];
       const double phi = a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP + n];
       if constexpr (MIXED) {
-        const double phi0 = a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP];
+        const float phh = vg[((size_t)e * ESDG_NVGEO + 10) * NP + n];
         if constexpr (BG) {
           const double* bge = a.bg + (size_t)e * 3 * NP;
-          prims32<NP, true>(q0, q1, q2, q3, q4, phi, phi0, gm1, S, n, bge[n], bge[NP + n],
+          prims32<NP, true>(q0, q1, q2, q3, q4, phi, phh, gm1, S, n, bge[n], bge[NP + n],
                             bge[2 * NP + n], S + SH::F_BG * NP);
         } else {
-          prims32<NP, false>(q0, q1, q2, q3, q4, phi, phi0, gm1, S, n);
+          prims32<NP, false>(q0, q1, q2, q3, q4, phi, phh, gm1, S, n);
         }
       } else {
         prims64<NP>(q0, q1, q2, q3, q4, phi, gm1, S, n);
@@ -722,6 +723,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
   const double* vg = reinterpret_cast<const double*>(a.vgeo);
   const double* dqg = reinterpret_cast<const double*>(a.dq);
   const int tid = threadIdx.x;
+  constexpr int ISSUER = SH::PENCILS < T ? T - 1 : 0;
 
   // the block copies of a tile's state and geometry (RAW), and of its dq (CUR)
   auto raw_blocks = [&](int tile, auto&& f) {
@@ -758,7 +760,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
   __syncthreads();
   int tile = blockIdx.x;
   if (tile < ntiles) {
-    if (tid == 0) issue_bulk(tile, raw_blocks, &bars[0]);
+    if (tid == ISSUER) issue_bulk(tile, raw_blocks, &bars[0]);
     int bi = 0;
     issue_edges(tile, raw_blocks, bi);
   }
@@ -803,17 +805,12 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
       }
     }
     __syncthreads();  // RAW consumed
+    const int next = tile + (int)gridDim.x;
     {
-      const int next = tile + (int)gridDim.x;
-      if (tid == 0) {
-        if constexpr (MODE != 0) issue_bulk(tile, cur_blocks, &bars[1]);
-        if (next < ntiles) issue_bulk(next, raw_blocks, &bars[0]);
-      }
       int bi = 0;
       issue_edges(tile, cur_blocks, bi);
       if (next < ntiles) issue_edges(next, raw_blocks, bi);
     }
-
     int need_logs = 0;
     for (int idx = tid; idx < EPB * NP; idx += T) {
       const int el2 = idx / NP, n = idx - el2 * NP;
@@ -828,6 +825,12 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
         S[SH::F_LB * NP + n] = log(2.0 * S[NP + n]);
       }
       __syncthreads();
+    }
+
+    // the bulk copies, from a thread that has no pencil (else thread 0)
+    if (tid == ISSUER) {
+      if constexpr (MODE != 0) issue_bulk(tile, cur_blocks, &bars[1]);
+      if (next < ntiles) issue_bulk(next, raw_blocks, &bars[0]);
     }
 
     // ---- pair pass: this thread's pencil (index arithmetic redone per tile
@@ -994,6 +997,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
   const float* vg = reinterpret_cast<const float*>(a.vgeo);
   const float* dqg = reinterpret_cast<const float*>(a.dq);
   const int tid = threadIdx.x;
+  constexpr int ISSUER = SH::PENCILS < T ? T - 1 : 0;
 
   auto phi_src = [&](int e) { return a.vgeo64 + ((size_t)e * ESDG_NVGEO + 10) * NP; };
   // the block copies of a tile's RAW and CUR data (EPB + 5 blocks at most)
@@ -1032,7 +1036,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
   __syncthreads();
   int tile = blockIdx.x;
   if (tile < ntiles) {
-    if (tid == 0) issue_bulk(tile, raw_blocks, &bars[0]);
+    if (tid == ISSUER) issue_bulk(tile, raw_blocks, &bars[0]);
     int bi = 0;
     issue_edges(tile, raw_blocks, bi);
   }
@@ -1062,10 +1066,9 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
           const double* phr = rawphi + (size_t)el2 * PP::PHS + esdg_block_shift(phi_src(e0 + el2));
           const double q0 = qr[n], q1 = qr[NP + n], q2 = qr[2 * NP + n], q3 = qr[3 * NP + n],
                        q4 = qr[4 * NP + n];
-          const double phi0 = phr[0];
-          prims32<NP, true>(q0, q1, q2, q3, q4, phr[n], phi0, gm1, S, n, br[n], br[NP + n],
-                            br[2 * NP + n], S + SH::F_BG * NP);
-          if (n == 0) phi0s[el2] = esdg_d2f(phi0);
+          prims32<NP, true>(q0, q1, q2, q3, q4, phr[n], gr[10 * NP + n], gm1, S, n, br[n],
+                            br[NP + n], br[2 * NP + n], S + SH::F_BG * NP);
+          if (n == 0) phi0s[el2] = esdg_d2f(phr[0]);
 #pragma unroll
           for (int k = 0; k < 9; k++) S[(SH::F_NH + k) * NP + n] = gr[k * NP + n];
           double* X = epq + (size_t)el2 * 5 * NP;
@@ -1084,17 +1087,12 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
       }
     }
     __syncthreads();  // RAW consumed
+    const int next = tile + (int)gridDim.x;
     {
-      const int next = tile + (int)gridDim.x;
-      if (tid == 0) {
-        issue_bulk(tile, cur_blocks, &bars[1]);
-        if (next < ntiles) issue_bulk(next, raw_blocks, &bars[0]);
-      }
       int bi = 0;
       issue_edges(tile, cur_blocks, bi);
       if (next < ntiles) issue_edges(next, raw_blocks, bi);
     }
-
     int need_logs = 0;
     for (int idx = tid; idx < EPB * NP; idx += T) {
       const int el2 = idx / NP, n = idx - el2 * NP;
@@ -1104,6 +1102,12 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
       if (fabsf(rn - r0) > 0.13f * r0 || fabsf(bn - b0) > 0.13f * b0) need_logs = 1;
     }
     need_logs = __syncthreads_or(need_logs);
+
+    // the bulk copies, from a thread that has no pencil (else thread 0)
+    if (tid == ISSUER) {
+      if constexpr (true) issue_bulk(tile, cur_blocks, &bars[1]);
+      if (next < ntiles) issue_bulk(next, raw_blocks, &bars[0]);
+    }
 
     // ---- pair pass ------------------------------------------------------------
     const bool active = tid < SH::PENCILS;
