@@ -50,10 +50,11 @@ FLOPS_PER_NODE = 45
 # is fused into the volume kernel.
 FACE_BYTES_PER_NODE = {"fp64": 160, "mixed": 140}
 
-# DRAM traffic of one FP64 volume launch: ncu capture of the same kernel on the 16^3 case
-# (dram__bytes_read.sum + dram__bytes_write.sum = 98.69 MB + 5.50 MB for 4096 elements),
-# scaled to the 32^3 launch by the element count (profiles/volume_fp64_N4_16cubed.md).
-VOLUME_FP64_TRAFFIC_BYTES = (98.69e6 + 5.50e6) * 8
+# DRAM traffic of one FP64 volume launch (k_volume_pipe64<4, 1>): ncu capture of the same
+# kernel on the 24^3 case (dram__bytes_read.sum + dram__bytes_write.sum = 332.60 MB +
+# 99.18 MB for 13 824 elements), scaled to the 32^3 launch by the element count
+# (profiles/volume_fp64_N4_24cubed.md).
+VOLUME_FP64_TRAFFIC_BYTES = (332.60e6 + 99.18e6) * 32768 / 13824
 
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2     # 2 DFMA / clk / SM -> 1.258 TFLOP/s
@@ -67,6 +68,23 @@ def measured_peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def max_over_ranks(x, dist, device="cuda"):
+    """The job time of a replica run: the slowest rank's (all-reduce MAX).  dist is
+    torch.distributed (NCCL on the GPU box, gloo with device="cpu" in tests) or None."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, ndof, steps, seconds):
+    """DOF-updates/s per RK stage of `world` independent replicas timed together: each
+    advances ndof nodes through 5 stages per step; the job time is the slowest rank's."""
+    return world * ndof * 5 * steps / seconds
 
 
 def pairs_per_element(N):
@@ -175,10 +193,7 @@ def run_gpu_arm(args, rank, world, dist):
         ms = t0.elapsed_time(t1)
         t_face = sum(e[0].elapsed_time(e[1]) for e in ev) / len(ev)
         t_vol = sum(e[1].elapsed_time(e[2]) for e in ev) / len(ev)
-        if dist is not None:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ms, dist)
         # e2e: the C-ABI call with host buffers, copies inside the timed region
         qh = torch.empty(s.shape(), dtype=torch.float64, pin_memory=True)
         s.get_state(qh)
@@ -196,10 +211,7 @@ def run_gpu_arm(args, rank, world, dist):
             s.get_state(qh)
         torch.cuda.synchronize()
         te = time.perf_counter() - te
-        if dist is not None:
-            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(te, dist)
         q = qh.numpy()
         finite = bool(np.isfinite(q).all())
         ndof = info.ndof
@@ -275,9 +287,8 @@ def main_ours(args):
     peaks, peak_src = measured_peaks()
     r64, r32 = res["fp64"], res["mixed"]
     w = WORKLOAD
-    stage_updates = r64["ndof"] * 5 * args.steps
-    value = world * stage_updates / (r64["ms"] * 1e-3)
-    value32 = world * r32["ndof"] * 5 * args.steps / (r32["ms"] * 1e-3)
+    value = replica_throughput(world, r64["ndof"], args.steps, r64["ms"] * 1e-3)
+    value32 = replica_throughput(world, r32["ndof"], args.steps, r32["ms"] * 1e-3)
     vflops = volume_flops(r64["E"], w["N"])
     achieved = vflops / (r64["t_vol"] * 1e-3)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -299,9 +310,11 @@ def main_ours(args):
                   "volume_fp32_tflops": vflops / (r32["t_vol"] * 1e-3) / 1e12,
                   "volume_fp32_frac": vflops / (r32["t_vol"] * 1e-3) / FP32_PEAK,
                   "speedup_vs_fp64": value32 / value,
-                  "e2e": {"value": world * r32["ndof"] * 5 * r32["e2e_steps"] / r32["e2e_s"],
+                  "e2e": {"value": replica_throughput(world, r32["ndof"], r32["e2e_steps"],
+                                                      r32["e2e_s"]),
                           "unit": UNIT}},
-        "e2e": {"value": world * r64["ndof"] * 5 * r64["e2e_steps"] / r64["e2e_s"], "unit": UNIT,
+        "e2e": {"value": replica_throughput(world, r64["ndof"], r64["e2e_steps"], r64["e2e_s"]),
+                "unit": UNIT,
                 "h2d_bytes_per_step": r64["state_bytes"], "d2h_bytes_per_step": r64["state_bytes"],
                 "steps": r64["e2e_steps"]},
         "gpu_launches": 10 * args.steps,
