@@ -215,20 +215,15 @@ __device__ __forceinline__ void esdg_block_bulk(T* region, const T* src, int n,
   if (body > 0)
     esdg_bulk_g2s(region + sh + head, src + head, (unsigned)body * (unsigned)sizeof(T), bar);
 }
-// the k-th of the block's elements outside the bulk interior (k < 2 (16/sizeof(T) - 1)),
-// copied with cp.async by the calling thread; nothing for k past the last
+// all of the block's elements outside the bulk interior, by the calling thread
 template <typename T>
-__device__ __forceinline__ void esdg_block_edge(T* region, const T* src, int n, int k) {
+__device__ __forceinline__ void esdg_block_edges(T* region, const T* src, int n) {
   if (n <= 0) return;
   int sh, head, body;
   esdg_block_split(src, n, sh, head, body);
-  const int tail = n - head - body;
-  if (k < 0 || k >= head + tail) return;
-  const int i = k < head ? k : head + body + (k - head);
-  esdg_cp_async(region + sh + i, src + i);
+  for (int i = 0; i < head; i++) esdg_cp_async(region + sh + i, src + i);
+  for (int i = head + body; i < n; i++) esdg_cp_async(region + sh + i, src + i);
 }
-// edge slots per block: 2 (16/4 - 1) = 6 for float, rounded up
-#define ESDG_EDGE_SLOTS 8
 
 // x < y for non-negative doubles, compared as integers (no FP64-pipe compare)
 __device__ __forceinline__ bool esdg_lt_pos(double x, double y) {

@@ -1,6 +1,7 @@
 // volume32.cu -- mixed-precision instantiations (FP32 pairs, FP64 state and
 // pressure recovery) of the flux-differencing volume kernel: single-mesh
-// launches and the persistent batched kernel with a background (two tile shapes).
+// launches and the batched variants with a background (pipelined persistent
+// kernel, per-tile kernel at two tile shapes).
 #include "volume_impl.cuh"
 
 int esdg_volume_mixed_take_timeout() {
@@ -29,28 +30,62 @@ template <> struct Alt32<6> { static constexpr int EPB = 1; };
 template <> struct Alt32<7> { static constexpr int EPB = 1; };
 }  // namespace
 
-int esdg_volume_batch_variants_mixed(int N) { return (N >= 1 && N <= 7) ? 2 : 1; }
+namespace {
+// Batched volume variants offered to the autotuner, in order: the pipelined
+// persistent kernel (when its tile fits in shared memory), the per-tile kernel
+// at the default tile shape, and at the alternative shape (when there is one).
+template <int NN>
+int batch_variant(int what, int variant, const EsdgMember* members, const int2* tiles,
+                  const int* ntiles, int grid, const EsdgLGL& L, double A, double B, cudaStream_t s) {
+  constexpr bool pipe_ok = esdg_vol::Pipe32<NN, 1>::SMEM <= ESDG_PIPE_SMEM_MAX;
+  constexpr bool alt_ok = Alt32<NN>::EPB > 0;
+  int kinds[3], nk = 0;
+  if (pipe_ok) kinds[nk++] = 0;
+  kinds[nk++] = 1;
+  if (alt_ok) kinds[nk++] = 2;
+  if (what == 3) return nk;
+  if (variant < 0 || variant >= nk) return -1;
+  switch (kinds[variant]) {
+    case 0:
+      if constexpr (pipe_ok) return esdg_vol::pipe_batch<NN, true>(what, members, tiles, ntiles, grid, L, A, B, s);
+      return -1;
+    case 1:
+      if (what == 0) return esdg_vol::launch_batch_one<NN, true, true, 0>(members, tiles, ntiles, grid, L, A, B, s) == cudaSuccess ? 0 : -1;
+      if (what == 1) return esdg_vol::Shape<NN, true, true, 0>::EPB;
+      return esdg_vol::batch_occupancy<NN, true, true, 0>();
+    default:
+      if constexpr (alt_ok) {
+        if (what == 0) return esdg_vol::launch_batch_one<NN, true, true, Alt32<NN>::EPB>(members, tiles, ntiles, grid, L, A, B, s) == cudaSuccess ? 0 : -1;
+        if (what == 1) return esdg_vol::Shape<NN, true, true, Alt32<NN>::EPB>::EPB;
+        return esdg_vol::batch_occupancy<NN, true, true, Alt32<NN>::EPB>();
+      }
+      return -1;
+  }
+}
 
-#define ESDG_V32(NN)                                                                          \
-  case NN:                                                                                    \
-    if (variant == 1 && Alt32<NN>::EPB > 0) {                                                 \
-      if (what == 0) return esdg_vol::launch_batch_one<NN, true, true, Alt32<NN>::EPB>(      \
-                                members, tiles, ntiles, grid, L, A, B, s) == cudaSuccess ? 0 : -1; \
-      if (what == 1) return esdg_vol::Shape<NN, true, true, Alt32<NN>::EPB>::EPB;             \
-      return esdg_vol::batch_occupancy<NN, true, true, Alt32<NN>::EPB>();                     \
-    }                                                                                         \
-    if (what == 0) return esdg_vol::launch_batch_one<NN, true, true, 0>(                     \
-                              members, tiles, ntiles, grid, L, A, B, s) == cudaSuccess ? 0 : -1; \
-    if (what == 1) return esdg_vol::Shape<NN, true, true, 0>::EPB;                            \
-    return esdg_vol::batch_occupancy<NN, true, true, 0>();
-
-// mixed members of a batch always carry a background (set by their initial state)
-int esdg_volume_batch_mixed(int what, int N, int variant, const EsdgMember* members,
-                            const int2* tiles, const int* ntiles, int grid, const EsdgLGL& L,
-                            double A, double B, cudaStream_t s) {
+int batch_dispatch(int what, int N, int variant, const EsdgMember* members, const int2* tiles,
+                   const int* ntiles, int grid, const EsdgLGL& L, double A, double B, cudaStream_t s) {
   switch (N) {
-    ESDG_V32(1) ESDG_V32(2) ESDG_V32(3) ESDG_V32(4) ESDG_V32(5) ESDG_V32(6) ESDG_V32(7)
+    case 1: return batch_variant<1>(what, variant, members, tiles, ntiles, grid, L, A, B, s);
+    case 2: return batch_variant<2>(what, variant, members, tiles, ntiles, grid, L, A, B, s);
+    case 3: return batch_variant<3>(what, variant, members, tiles, ntiles, grid, L, A, B, s);
+    case 4: return batch_variant<4>(what, variant, members, tiles, ntiles, grid, L, A, B, s);
+    case 5: return batch_variant<5>(what, variant, members, tiles, ntiles, grid, L, A, B, s);
+    case 6: return batch_variant<6>(what, variant, members, tiles, ntiles, grid, L, A, B, s);
+    case 7: return batch_variant<7>(what, variant, members, tiles, ntiles, grid, L, A, B, s);
     default: return -1;
   }
 }
-#undef ESDG_V32
+}  // namespace
+
+int esdg_volume_batch_variants_mixed(int N) {
+  const int n = batch_dispatch(3, N, 0, nullptr, nullptr, nullptr, 0, EsdgLGL{}, 0, 0, 0);
+  return n > 0 ? n : 1;
+}
+
+// what: 0 launch (returns 0 / -1), 1 elements per tile, 2 CTAs per SM
+int esdg_volume_batch_mixed(int what, int N, int variant, const EsdgMember* members,
+                          const int2* tiles, const int* ntiles, int grid, const EsdgLGL& L,
+                          double A, double B, cudaStream_t s) {
+  return batch_dispatch(what, N, variant, members, tiles, ntiles, grid, L, A, B, s);
+}
