@@ -50,11 +50,11 @@ FLOPS_PER_NODE = 45
 # is fused into the volume kernel.
 FACE_BYTES_PER_NODE = {"fp64": 160, "mixed": 140}
 
-# DRAM traffic of one FP64 volume launch (k_volume_pipe64<4, 1>): ncu capture of the same
-# kernel on the 24^3 case (dram__bytes_read.sum + dram__bytes_write.sum = 332.60 MB +
-# 99.18 MB for 13 824 elements), scaled to the 32^3 launch by the element count
+# DRAM traffic of one FP64 volume launch (k_volume_pipe64<4, 1, 0>): ncu capture of the same
+# kernel on the 24^3 case (dram__bytes_read.sum + dram__bytes_write.sum = 332.89 MB +
+# 99.10 MB for 13 824 elements), scaled to the 32^3 launch by the element count
 # (profiles/volume_fp64_N4_24cubed.md).
-VOLUME_FP64_TRAFFIC_BYTES = (332.60e6 + 99.18e6) * 32768 / 13824
+VOLUME_FP64_TRAFFIC_BYTES = (332.89e6 + 99.10e6) * 32768 / 13824
 
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2     # 2 DFMA / clk / SM -> 1.258 TFLOP/s
@@ -436,6 +436,68 @@ def run_ensemble(args):
     print(json.dumps(out))
 
 
+CHANNEL = dict(K=(120, 24, 12), N=4, lo=(0.0, 0.0, 0.0), hi=(40000e3, 6000e3, 30e3),
+               periodic=(1, 0, 0), f0=1e-4, cfl=0.5)
+
+
+def run_channel(args):
+    """The channel configuration: mixed precision against plain FP64 on the GPU over
+    `steps` LSRK steps (the FP64 path is the oracle-matched one: parity tests hold its
+    right-hand sides to the CPU oracle; the oracle itself would need ~2 h for 500 steps of
+    this mesh).  Reports per-variable relative errors of the state and of the flow (state
+    minus initial state, momentum as one vector), relative drift of mass and total energy
+    for both precisions, and DOF-updates/s per RK stage."""
+    import numpy as np
+    import torch
+    from paper_2605_16684_gb300 import _build, _lib
+    _build.build()
+    c = CHANNEL
+    res = {}
+    dt = None
+    for prec in ("fp64", "mixed"):
+        s = _lib.Solver(*c["K"], c["N"], lo=c["lo"], hi=c["hi"], periodic=c["periodic"],
+                        precision=prec, f0=c["f0"])
+        s.init_channel()
+        q0 = s.get_state()
+        if dt is None:
+            dt = s.cfl_dt(c["cfl"])
+        i0 = s.integrals()
+        s.step(dt, 2)  # warm-up (state re-set below)
+        s.set_state(q0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s.step(dt, args.steps)
+        s.sync()
+        el = time.perf_counter() - t
+        i1 = s.integrals()
+        q = s.get_state()
+        res[prec] = dict(q=q, q0=q0, s=el, ndof=s.E * s.np,
+                         drift=[float((i1[k] - i0[k]) / abs(i0[k])) for k in (0, 1)])
+        s.close()
+    q64, q32, q0 = res["fp64"]["q"], res["mixed"]["q"], res["fp64"]["q0"]
+    state_err = [float(np.linalg.norm(q32[:, v] - q64[:, v]) / np.linalg.norm(q64[:, v]))
+                 for v in range(5)]
+    f64, f32 = q64 - q0, q32 - q0
+    mom = np.sqrt(sum(np.linalg.norm(f64[:, v]) ** 2 for v in (1, 2, 3)))
+    flow_err = [float(np.linalg.norm(f32[:, v] - f64[:, v]) /
+                      (mom if v in (1, 2, 3) else np.linalg.norm(f64[:, v]))) for v in range(5)]
+    out = {"metric": "channel: mixed vs FP64 per-variable error, conservation drift, "
+                     "DOF-updates/s per RK stage",
+           "unit": "relative / DOF-updates/s", "n_gpus": 1, "steps": args.steps, "dt_s": dt,
+           "config": {"workload": "baroclinic_channel_120x24x12_N4", "box_km": [40000, 6000, 30],
+                      "boundaries": "periodic x, walls y and z", "f0": c["f0"],
+                      "initial_state": "balanced zonal jet (synthetic stand-in) + 1 m/s "
+                                       "Gaussian wind perturbation",
+                      "reference": "FP64 GPU path (RHS parity with the CPU oracle <= 1e-12)"},
+           "state_rel_err_rho_rhou_rhov_rhow_E": state_err,
+           "flow_rel_err_rho_rhou_rhov_rhow_E": flow_err,
+           "mass_energy_drift_fp64": res["fp64"]["drift"],
+           "mass_energy_drift_mixed": res["mixed"]["drift"],
+           "fp64_value": res["fp64"]["ndof"] * 5 * args.steps / res["fp64"]["s"],
+           "mixed_value": res["mixed"]["ndof"] * 5 * args.steps / res["mixed"]["s"]}
+    print(json.dumps(out))
+
+
 def run_serving(args):
     import threading
     import numpy as np
@@ -502,7 +564,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--K", type=int, default=0, help="elements per direction (small profiling cases)")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
-    ap.add_argument("--workload", default="bubble32", choices=["bubble32", "ensemble", "serving"])
+    ap.add_argument("--workload", default="bubble32",
+                    choices=["bubble32", "ensemble", "serving", "channel"])
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--check", type=int, default=4, help="ensemble members compared with FP64")
     ap.add_argument("--requests", type=int, default=60)
@@ -516,6 +579,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "channel":
+        run_channel(args)
         return
     if args.warmup < 3:
         args.warmup = 3
