@@ -197,11 +197,22 @@ int esdg_member_descriptor(es_dg_t* h, double dt, EsdgMember* out, EsdgLGL* L, i
   return ES_DG_OK;
 }
 
-extern "C" {
+namespace {
 
-int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,
-                 const es_dg_physics* physics, const es_dg_allocator* allocator,
-                 void* cuda_stream, es_dg_t** out) {
+// Same mesh, order and gravity: the geometry (coordinates, metric terms,
+// Jacobian, geopotential, face normals and scalings) is identical.
+bool same_geometry(const es_dg_t* a, const EsdgGrid& g, double gravity) {
+  if (!a || a->g.N != g.N || a->g.warp != g.warp || a->P.g != gravity) return false;
+  for (int d = 0; d < 3; d++)
+    if (a->g.K[d] != g.K[d] || a->g.periodic[d] != g.periodic[d] || a->g.lo[d] != g.lo[d] ||
+        a->g.hi[d] != g.hi[d])
+      return false;
+  return true;
+}
+
+int create_impl(const es_dg_mesh* mesh, int N, es_dg_precision precision,
+                const es_dg_physics* physics, const es_dg_allocator* allocator, void* cuda_stream,
+                const es_dg_t* geometry_of, es_dg_t** out) {
   if (!out) return ES_DG_EINVAL;
   *out = nullptr;
   if (precision != ES_DG_FP64 && precision != ES_DG_FP32_MIXED) return ES_DG_EINVAL;
@@ -270,9 +281,25 @@ int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,
   }
   cudaError_t e = cudaMemsetAsync(h->dq, 0, nq * (h->mixed ? sizeof(float) : sizeof(double)), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->q, 0, nq * sizeof(double), h->stream);
-  if (e == cudaSuccess)
-    e = esdg_launch_geometry(h->g, h->L, h->x, h->J, h->Ja, h->vgeo, h->vgeo32, h->fgeo, h->P,
-                             h->stream);
+  if (e == cudaSuccess) {
+    if (same_geometry(geometry_of, h->g, h->P.g)) {
+      // device-to-device copies of an identical mesh's geometry
+      const es_dg_t* o = geometry_of;
+      const size_t nfg = (size_t)g.nfaces * 5 * nf2;
+      const struct { void* d; const void* s; size_t b; } cp[6] = {
+          {h->x, o->x, E * 3 * np * sizeof(double)},
+          {h->J, o->J, E * np * sizeof(double)},
+          {h->Ja, o->Ja, E * 9 * np * sizeof(double)},
+          {h->vgeo, o->vgeo, E * ESDG_NVGEO * np * sizeof(double)},
+          {h->vgeo32, o->vgeo32, E * ESDG_NVGEO * np * sizeof(float)},
+          {h->fgeo, o->fgeo, nfg * sizeof(double)}};
+      for (int k = 0; k < 6 && e == cudaSuccess; k++)
+        e = cudaMemcpyAsync(cp[k].d, cp[k].s, cp[k].b, cudaMemcpyDeviceToDevice, h->stream);
+    } else {
+      e = esdg_launch_geometry(h->g, h->L, h->x, h->J, h->Ja, h->vgeo, h->vgeo32, h->fgeo, h->P,
+                               h->stream);
+    }
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     es_dg_destroy(h);
@@ -280,6 +307,24 @@ int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,
   }
   *out = h;
   return ES_DG_OK;
+}
+
+}  // namespace
+
+// Internal (server): create a handle whose geometry is copied from `geometry_of`
+// when that handle has the same mesh, order and gravity (else computed).
+int esdg_create_from(const es_dg_mesh* mesh, int N, es_dg_precision precision,
+                     const es_dg_physics* physics, void* cuda_stream, const es_dg_t* geometry_of,
+                     es_dg_t** out) {
+  return create_impl(mesh, N, precision, physics, nullptr, cuda_stream, geometry_of, out);
+}
+
+extern "C" {
+
+int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,
+                 const es_dg_physics* physics, const es_dg_allocator* allocator,
+                 void* cuda_stream, es_dg_t** out) {
+  return create_impl(mesh, N, precision, physics, allocator, cuda_stream, nullptr, out);
 }
 
 void es_dg_destroy(es_dg_t* h) {

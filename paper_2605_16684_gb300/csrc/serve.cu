@@ -34,6 +34,9 @@
 
 // provided by api.cu for the server (internal, not part of the C ABI)
 int esdg_member_descriptor(es_dg_t* h, double dt, EsdgMember* out, EsdgLGL* L, int* mixed);
+int esdg_create_from(const es_dg_mesh* mesh, int N, es_dg_precision precision,
+                     const es_dg_physics* physics, void* cuda_stream, const es_dg_t* geometry_of,
+                     es_dg_t** out);
 
 namespace {
 
@@ -360,7 +363,16 @@ int admit_one(es_dg_server* s, Member& m) {
     mesh.periodic[0] = 1;
     ph.f0 = 1e-4;
   }
-  int st = es_dg_create(&mesh, q.N, q.precision, &ph, nullptr, s->stream, &m.h);
+  // a resident member with the same mesh and order lends its geometry (a device
+  // copy instead of the double-double metric computation)
+  const es_dg_t* twin = nullptr;
+  for (const auto& a : s->active)
+    if (a->h && a->req.kind == q.kind && a->req.kx == q.kx && a->req.ky == q.ky &&
+        a->req.kz == q.kz && a->req.N == q.N && (q.kind != 0 || a->req.warp == q.warp)) {
+      twin = a->h;
+      break;
+    }
+  int st = esdg_create_from(&mesh, q.N, q.precision, &ph, s->stream, twin, &m.h);
   if (st) {
     std::snprintf(s->msg, sizeof(s->msg), "es_dg_create: %s", es_dg_strerror(st));
     return st;

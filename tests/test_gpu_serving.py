@@ -77,6 +77,20 @@ def test_result_same_alone_and_in_mix(lib):
     assert np.array_equal(qa, qm)
 
 
+def test_twin_meshes_share_geometry_exactly(lib):
+    # members with the same mesh and order copy the first one's geometry at
+    # admission; every result still equals its own single-handle solve bit for bit
+    reqs = [dict(K=(4, 4, 3), N=4, precision=p, nsteps=3, warp=0.05, amp=a)
+            for p, a in (("mixed", 0.5), ("mixed", 0.9), ("fp64", 0.7))]
+    srv = lib.Server()
+    tickets = [srv.submit(**r) for r in reqs]
+    for t, r in zip(tickets, reqs):
+        res = srv.wait(t)
+        assert res["status"] == 0, srv.stats()["error"]
+        assert np.array_equal(res["q"], single_handle(lib, r)[0])
+    srv.close()
+
+
 def test_admission_by_footprint_serialises_large_requests(lib):
     # budget for one 4^3 N=3 FP64 request at a time (estimated 1.7 MiB each)
     srv = lib.Server(hbm_budget_bytes=3 << 20, max_slots=8)
