@@ -145,6 +145,12 @@ int es_dg_cfl_dt(es_dg_t* h, double C, double* dt);
  * Asynchronous on the handle's stream; each stage is one interface-flux launch
  * and one volume launch with the RK update fused in. */
 int es_dg_step(es_dg_t* h, double dt, int nsteps);
+
+/* Wait for the handle's stream.  Returns ES_DG_ETIMEOUT if, since the last
+ * call, a bounded device wait of the pipelined volume kernels ran out (their
+ * tile copies never completed; the kernel stopped and the state is not
+ * valid), ES_DG_ECUDA on a CUDA error, else ES_DG_OK.  The timeout flag is
+ * process-wide per device and cleared by the call. */
 int es_dg_sync(es_dg_t* h);
 
 /* Global integrals of the handle's state: mass, total energy, entropy
