@@ -153,6 +153,14 @@ int es_dg_step(es_dg_t* h, double dt, int nsteps);
  * process-wide per device and cleared by the call. */
 int es_dg_sync(es_dg_t* h);
 
+/* Test hook for the failure path above: the next single-mesh volume launch
+ * (any handle, this process) registers 16 bytes more on its first tile
+ * barrier than its copies deliver, so every CTA's bounded wait runs out
+ * (about a second), the kernel stops without touching memory further, and
+ * the next es_dg_sync returns ES_DG_ETIMEOUT.  The state of that handle is
+ * then undefined; the context stays usable.  One-shot. */
+void es_dg_debug_inject_wait_timeout(void);
+
 /* Global integrals of the handle's state: mass, total energy, entropy
  * (sum over elements of the quadrature of rho, E and -rho s/(gamma-1)).
  * Synchronous. */

@@ -87,6 +87,7 @@ SIGNATURES = {
     "es_dg_cfl_dt": (C.c_int, [_VP, C.c_double, _DP]),
     "es_dg_step": (C.c_int, [_VP, C.c_double, C.c_int]),
     "es_dg_sync": (C.c_int, [_VP]),
+    "es_dg_debug_inject_wait_timeout": (None, []),
     "es_dg_integrals": (C.c_int, [_VP, _DP]),
     "es_dg_geometry": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int]),
     "es_dg_launch": (C.c_int, [_VP, C.c_int, C.c_int, C.c_double]),

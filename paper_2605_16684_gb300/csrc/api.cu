@@ -3,6 +3,7 @@
 // arguments, owns device memory and orders launches on the handle's stream.
 #include <cstdio>
 #include <cstdlib>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -311,6 +312,11 @@ int create_impl(const es_dg_mesh* mesh, int N, es_dg_precision precision,
 
 }  // namespace
 
+namespace {
+std::atomic<unsigned> g_phantom_tx{0};
+}
+unsigned esdg_take_phantom() { return g_phantom_tx.exchange(0u); }
+
 // Internal (server): create a handle whose geometry is copied from `geometry_of`
 // when that handle has the same mesh, order and gravity (else computed).
 int esdg_create_from(const es_dg_mesh* mesh, int N, es_dg_precision precision,
@@ -463,6 +469,8 @@ int es_dg_step(es_dg_t* h, double dt, int nsteps) {
     }
   return ES_DG_OK;
 }
+
+void es_dg_debug_inject_wait_timeout(void) { g_phantom_tx.store(16u); }
 
 int es_dg_sync(es_dg_t* h) {
   if (!h) return ES_DG_EINVAL;

@@ -345,6 +345,10 @@ int esdg_volume_batch_mixed(int what, int N, int variant, const EsdgMember* memb
 int esdg_volume_batch_variants_f64(int N);
 int esdg_volume_batch_variants_mixed(int N);
 
+// Test hook (es_dg_debug_inject_wait_timeout): bytes the next single-mesh
+// pipelined volume launch registers on its first barrier without copying them;
+// read and cleared by the launcher.
+unsigned esdg_take_phantom();
 // 1 if a bounded wait of the pipelined FP64 / mixed volume kernels ran out
 // since the last call (the flag is cleared), 0 if not, -1 on a CUDA error
 int esdg_volume_f64_take_timeout();

@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(Shape<N, MIXED, BG, EPB_>::THREADS)
 // entries over member descriptors (TABLE: the batched server).  In TABLE mode
 // each tile's descriptor is bulk-copied into one of two shared slots with its
 // RAW data.  The arithmetic is that of volume_tile, in the same order.
-#define ESDG_WAIT_LIMIT (1u << 20)
+#define ESDG_WAIT_LIMIT (1u << 18)  // polls; about 1 s on GB300
 // set when a bounded wait of a pipelined kernel ran out (one flag per
 // translation unit; read and cleared through es_dg_sync)
 static __device__ int g_esdg_vol_timeout;
@@ -785,10 +785,13 @@ struct Issuers {
   }
   static __device__ __forceinline__ bool is(int tid) { return tid >= FIRST && tid < FIRST + COUNT; }
 };
+// phantom: bytes registered but never copied (a test hook that makes the
+// barrier's bounded wait run out; 0 in normal operation)
 template <typename ISS, int MAXB>
 __device__ __forceinline__ void pipe_issue(int tid, const BlockCopy (&bl)[MAXB], int nb,
                                            unsigned long long* bar, unsigned extra = 0,
-                                           const void* xsrc = nullptr, void* xdst = nullptr) {
+                                           const void* xsrc = nullptr, void* xdst = nullptr,
+                                           unsigned phantom = 0) {
   constexpr int PER = (MAXB + ISS::COUNT - 1) / ISS::COUNT;
   const int il = tid - ISS::FIRST;
   BlockSpan sp[PER];
@@ -801,7 +804,8 @@ __device__ __forceinline__ void pipe_issue(int tid, const BlockCopy (&bl)[MAXB],
       mine += (unsigned)(sp[k].b - sp[k].a);
     }
   }
-  const unsigned total = (ISS::COUNT > 1 ? __reduce_add_sync(ISS::mask(), mine) : mine) + extra;
+  const unsigned total =
+      (ISS::COUNT > 1 ? __reduce_add_sync(ISS::mask(), mine) : mine) + extra + phantom;
   if (il == 0) esdg_mbar_arrive_tx(bar, total);
   if (ISS::COUNT > 1) __syncwarp(ISS::mask());
   esdg_fence_proxy_async();
@@ -827,7 +831,7 @@ template <int N, int MODE, bool TABLE>
 __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
     k_volume_pipe64(const EsdgMember one, const EsdgMember* __restrict__ members,
                     const int2* __restrict__ tiles, const int* __restrict__ ntiles_d, int ntiles_1,
-                    EsdgLGL L, double rkA, double rkB) {
+                    EsdgLGL L, double rkA, double rkB, unsigned phantom) {
   static_assert(!TABLE || MODE == 1, "the batched kernel applies an RK stage");
   using SH = Shape<N, false, false>;
   using PP = Pipe64<N, MODE>;
@@ -859,7 +863,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
     return x;
   };
   // issuing lanes: the next tile's (member, e0), descriptor and RAW blocks into slot s
-  auto issue_next = [&](const Next& x, int s) {
+  auto issue_next = [&](const Next& x, int s, unsigned ph = 0) {
     if (tid == ISS::FIRST) ctl.info[s] = x.tr;
     const int e0 = x.tr.y, ne = min(EPB, x.E - e0);
     const BlockCopy bl[2] = {
@@ -867,9 +871,9 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
         {sm + PP::RAW_G, x.vg + (size_t)e0 * ESDG_NVGEO * NP, x.vg + (size_t)x.E * ESDG_NVGEO * NP,
          ne * ESDG_NVGEO * NP, 8}};
     if constexpr (TABLE)
-      pipe_issue<ISS>(tid, bl, 2, &ctl.bars[0], (unsigned)sizeof(EsdgMember), x.Mg, &ctl.desc[s]);
+      pipe_issue<ISS>(tid, bl, 2, &ctl.bars[0], (unsigned)sizeof(EsdgMember), x.Mg, &ctl.desc[s], ph);
     else
-      pipe_issue<ISS>(tid, bl, 2, &ctl.bars[0]);
+      pipe_issue<ISS>(tid, bl, 2, &ctl.bars[0], 0, nullptr, nullptr, ph);
   };
 
   if (tid == 0) {
@@ -879,7 +883,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
     if constexpr (!TABLE) ctl.desc[0] = one;
   }
   __syncthreads();
-  if (ISS::is(tid) && (int)blockIdx.x < ntiles) issue_next(fetch(blockIdx.x), 0);
+  if (ISS::is(tid) && (int)blockIdx.x < ntiles) issue_next(fetch(blockIdx.x), 0, phantom);
   unsigned ph_raw = 0, ph_cur = 0;
   int slot = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, slot ^= 1) {
@@ -1073,7 +1077,7 @@ template <int N, int MODE, bool TABLE>
 __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     k_volume_pipe32(const EsdgMember one, const EsdgMember* __restrict__ members,
                     const int2* __restrict__ tiles, const int* __restrict__ ntiles_d, int ntiles_1,
-                    EsdgLGL L, double rkA, double rkB) {
+                    EsdgLGL L, double rkA, double rkB, unsigned phantom) {
   static_assert(!TABLE || MODE == 1, "the batched kernel applies an RK stage");
   using SH = Shape<N, true, true>;
   using PP = Pipe32<N, MODE>;
@@ -1119,7 +1123,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     return x;
   };
   // issuing lanes: the next tile's (member, e0), descriptor and RAW blocks into slot s
-  auto issue_next = [&](const Next& x, int s) {
+  auto issue_next = [&](const Next& x, int s, unsigned ph = 0) {
     if (tid == ISS::FIRST) ctl.info[s] = x.tr;
     const int e0 = x.tr.y, ne = min(EPB, x.E - e0);
     const double* v64end = x.v64 + (size_t)x.E * ESDG_NVGEO * NP;
@@ -1133,9 +1137,9 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
       bl[3 + el] = {rawphi + (size_t)el * PP::PHS, x.v64 + ((size_t)(e0 + el) * ESDG_NVGEO + 10) * NP,
                     v64end, el < ne ? NP : 0, 8};
     if constexpr (TABLE)
-      pipe_issue<ISS>(tid, bl, 3 + EPB, &ctl.bars[0], (unsigned)sizeof(EsdgMember), x.Mg, &ctl.desc[s]);
+      pipe_issue<ISS>(tid, bl, 3 + EPB, &ctl.bars[0], (unsigned)sizeof(EsdgMember), x.Mg, &ctl.desc[s], ph);
     else
-      pipe_issue<ISS>(tid, bl, 3 + EPB, &ctl.bars[0]);
+      pipe_issue<ISS>(tid, bl, 3 + EPB, &ctl.bars[0], 0, nullptr, nullptr, ph);
   };
 
   if (tid == 0) {
@@ -1145,7 +1149,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     if constexpr (!TABLE) ctl.desc[0] = one;
   }
   __syncthreads();
-  if (ISS::is(tid) && (int)blockIdx.x < ntiles) issue_next(fetch(blockIdx.x), 0);
+  if (ISS::is(tid) && (int)blockIdx.x < ntiles) issue_next(fetch(blockIdx.x), 0, phantom);
   unsigned ph_raw = 0, ph_cur = 0;
   int slot = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, slot ^= 1) {
@@ -1360,7 +1364,7 @@ cudaError_t launch_pipe64(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L
   const int ntiles = (g.E + SH::EPB - 1) / SH::EPB;
   if (ntiles == 0) return cudaSuccess;
   k<<<ntiles < cap ? ntiles : cap, SH::THREADS, Pipe64<N, MODE>::SMEM, s>>>(
-      pipe_member(g, P, a), nullptr, nullptr, nullptr, ntiles, L, a.rkA, a.rkB);
+      pipe_member(g, P, a), nullptr, nullptr, nullptr, ntiles, L, a.rkA, a.rkB, esdg_take_phantom());
   return cudaGetLastError();
 }
 
@@ -1374,7 +1378,7 @@ cudaError_t launch_pipe32(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L
   const int ntiles = (g.E + SH::EPB - 1) / SH::EPB;
   if (ntiles == 0) return cudaSuccess;
   k<<<ntiles < cap ? ntiles : cap, SH::THREADS, Pipe32<N, MODE>::SMEM, s>>>(
-      pipe_member(g, P, a), nullptr, nullptr, nullptr, ntiles, L, a.rkA, a.rkB);
+      pipe_member(g, P, a), nullptr, nullptr, nullptr, ntiles, L, a.rkA, a.rkB, esdg_take_phantom());
   return cudaGetLastError();
 }
 
@@ -1406,7 +1410,7 @@ int pipe_batch(int what, const EsdgMember* members, const int2* tiles, const int
   }
   EsdgMember none;
   memset(&none, 0, sizeof(none));
-  k<<<grid, SH::THREADS, SMEM, s>>>(none, members, tiles, ntiles, 0, L, A, B);
+  k<<<grid, SH::THREADS, SMEM, s>>>(none, members, tiles, ntiles, 0, L, A, B, 0u);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

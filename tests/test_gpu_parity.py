@@ -198,3 +198,26 @@ def test_rhs_parity_full_size_32cubed_N4(lib):
     # at rest the plain double oracle is exact up to its term rounding
     check_floor(s.rhs(qb), o.rhs(qb), o.rhs_scale(qb))
     assert s.cfl_dt(0.5) == pytest.approx(o.cfl_dt(qb, 0.5), rel=1e-13)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bounded_wait_timeout_is_reported_and_context_survives(lib, precision):
+    # failure path without a fault: the test hook registers bytes no copy delivers,
+    # the pipelined kernel's bounded wait runs out, es_dg_sync reports it, and the
+    # next step on a reset state runs normally
+    s = lib.Solver(3, 3, 3, 4, precision=precision, **CUBE)
+    s.init_bubble()
+    q0 = s.get_state()
+    dt = s.cfl_dt(0.5)
+    s.lib.es_dg_debug_inject_wait_timeout()
+    s.step(dt, 1)
+    with pytest.raises(lib.EsDgError) as err:
+        s.sync()
+    assert err.value.code == -5  # ES_DG_ETIMEOUT
+    s.set_state(q0)
+    s.step(dt, 1)
+    s.sync()
+    ref = lib.Solver(3, 3, 3, 4, precision=precision, **CUBE)
+    ref.init_bubble()
+    ref.step(dt, 1)
+    assert np.array_equal(s.get_state(), ref.get_state())
