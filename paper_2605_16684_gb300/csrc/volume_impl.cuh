@@ -110,13 +110,29 @@ __device__ __forceinline__ Node<R> load_node(const R* __restrict__ S, int n, int
   return a;
 }
 
-// One unordered pair (i = A, l = B) in FP64: 62 FP64 instructions on the
+// The artanh series of 1/<b>_log scaled by ce = 1/(2(gamma - 1)): the energy
+// flux only needs ce/<b>_log, so ce goes into the coefficients (computed once
+// per thread) and one FMA per pair folds the term into the energy bracket.
+// Tail beyond u^1 in FP32 (see esdg_A_t).
+struct CeSeries {
+  double c0, c1;    // ce, ce/3
+  float c2f, c3f;   // ce/5, ce/7
+};
+__device__ __forceinline__ CeSeries ce_series(double ce) {
+  return CeSeries{ce, ce * (1.0 / 3.0), esdg_d2f(ce * 0.2), esdg_d2f(ce * (1.0 / 7.0))};
+}
+__device__ __forceinline__ double esdg_Ace_t(double u, const CeSeries& c) {
+  const float tail = fmaf(esdg_d2f_tail(u), c.c3f, c.c2f);
+  return fma(u, fma(u, esdg_f2d_pos(tail), c.c1), c.c0);
+}
+
+// One unordered pair (i = A, l = B) in FP64: 61 FP64 instructions on the
 // series path.  ai += Dt_il H(i,l), al += Dt_li H(l,i).  The momentum flux is
 // regrouped as Fr {{u}} + (p* + g_own) {{n}}, so the gravity coefficient of
 // each side folds into its pressure term with one FMA.
 template <bool LOGS>
 __device__ __forceinline__ void pair64(const Node<double>& A, const Node<double>& B, double dil,
-                                       double dli, double ce, double* ai, double* al) {
+                                       double dli, const CeSeries& cs, double* ai, double* al) {
   const double sr = A.rq + B.rq;  // {{rho}}/2
   const double sb = A.bh + B.bh;  // {{b}}
   const double rsb = esdg_rcp(sb);
@@ -124,24 +140,24 @@ __device__ __forceinline__ void pair64(const Node<double>& A, const Node<double>
   const double dr = A.rq - B.rq, db = A.bh - B.bh;
   const double fr = dr * esdg_rcp_lo(sr), ur = fr * fr;
   const double fb = db * rsb, ub = fb * fb;
-  double rlog, iblog;
+  const double uu = fma(A.u2, B.u2, fma(A.u1, B.u1, A.u0 * B.u0));  // u_i . u_l / 4
+  const double t = fma(2.0, uu, A.ph + B.ph);                        // u_i.u_l/2 + {{phi}}
+  double rlog, bracket;  // <rho>_log and ce/<b>_log + t
   if (!LOGS) {
-    rlog = sr * esdg_Q2_t(ur);     // <rho>_log
-    iblog = rsb * esdg_A_t(ub);    // 1/<b>_log
+    rlog = sr * esdg_Q2_t(ur);
+    bracket = fma(rsb, esdg_Ace_t(ub, cs), t);
   } else {
     if (esdg_lt_pos(ur, ESDG_LOG_EPS)) rlog = sr * esdg_Q2_t(ur);
     else rlog = (4.0 * dr) * esdg_rcp(A.lr - B.lr);
-    if (esdg_lt_pos(ub, ESDG_LOG_EPS)) iblog = rsb * esdg_A_t(ub);
-    else iblog = (A.lb - B.lb) * esdg_rcp(2.0 * db);
+    if (esdg_lt_pos(ub, ESDG_LOG_EPS)) bracket = fma(rsb, esdg_Ace_t(ub, cs), t);
+    else bracket = fma((A.lb - B.lb) * esdg_rcp(2.0 * db), cs.c0, t);
   }
   const double n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;  // {{Ja^d}}
   const double u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;  // {{u}}
   const double un = fma(u2, n2, fma(u1, n1, u0 * n0));
   const double Fr = rlog * un;
   const double f0 = Fr * u0, f1 = Fr * u1, f2 = Fr * u2;
-  const double uu = fma(A.u2, B.u2, fma(A.u1, B.u1, A.u0 * B.u0));  // u_i . u_l / 4
-  const double t = fma(2.0, uu, A.ph + B.ph);                        // u_i.u_l/2 + {{phi}}
-  const double FE = un * fma(rlog, fma(iblog, ce, t), pt);
+  const double FE = un * fma(rlog, bracket, pt);
   // gravity: 1/2 rho_hat [[phi]] with rho_hat = {{b}} <rho>_log / b_(own node)
   const double gq = sb * rlog * (B.ph - A.ph);
   const double pi = fma(gq, A.ib, pt), pl = fma(-gq, B.ib, pt);
@@ -297,10 +313,11 @@ __device__ __forceinline__ void pair32bg(const Node<float>& A, const Node<float>
   al[4] = fmaf(dli, FE, al[4]);
 }
 
-template <int N, bool MIXED, bool LOGS, bool BG>
+// ce: 1/(2(gamma - 1)) as float (mixed) or as the scaled series (FP64)
+template <int N, bool MIXED, bool LOGS, bool BG, typename CE>
 __device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED, BG>::R* __restrict__ S,
                                             int d, int base, int stride, const EsdgLGL& L,
-                                            typename Shape<N, MIXED, BG>::R ce,
+                                            const CE& ce,
                                             typename Shape<N, MIXED, BG>::R (&acc)[N + 1][5]) {
   using SH = Shape<N, MIXED, BG>;
   using R = typename SH::R;
@@ -554,9 +571,10 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
     if (active && e < E) face_lift<true, N, R>(g, a, e, d, s + Nq * t, acc);
   if (active && e < E) {
     const R* S = sm + (size_t)el * NF * NP;
-    R ce;
-    if constexpr (MIXED) ce = esdg_d2f(0.5 * P.igm1);
-    else ce = 0.5 * P.igm1;
+    const auto ce = [&] {
+      if constexpr (MIXED) return esdg_d2f(0.5 * P.igm1);
+      else return ce_series(0.5 * P.igm1);
+    }();
     if (need_logs)
       pencil_pass<N, MIXED, true, BG>(S, d, base, stride, L, ce, acc);
     else
@@ -983,9 +1001,9 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
       face_lift<true, N, double>(g, a, e, d, ps + Nq * pt, acc);
       const double* S = sm + PP::S0 + (size_t)el * NF * NP;
       if (need_logs)
-        pencil_pass<N, false, true, false>(S, d, base, stride, L, 0.5 * P.igm1, acc);
+        pencil_pass<N, false, true, false>(S, d, base, stride, L, ce_series(0.5 * P.igm1), acc);
       else
-        pencil_pass<N, false, false, false>(S, d, base, stride, L, 0.5 * P.igm1, acc);
+        pencil_pass<N, false, false, false>(S, d, base, stride, L, ce_series(0.5 * P.igm1), acc);
     }
     __syncthreads();
     if (active && e < E) {
