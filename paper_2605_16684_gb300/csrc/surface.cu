@@ -23,8 +23,16 @@ struct FaceMath;
 template <>
 struct FaceMath<double> {
   static __device__ __forceinline__ double rcp(double x) { return esdg_rcp(x); }
-  static __device__ __forceinline__ double A(double u) { return esdg_A(u); }
-  static __device__ __forceinline__ double Q(double u) { return esdg_Q(u); }
+  // 2 A(u) and Q(u)/2 with the tails beyond u^1 in FP32 (u < 1e-4: the tails are
+  // below 4e-9, their FP32 rounding below 1e-16 of the result)
+  static __device__ __forceinline__ double A2(double u) {
+    const float tail = fmaf(esdg_d2f_tail(u), 2.0f / 7.0f, 2.0f / 5.0f);
+    return fma(u, fma(u, esdg_f2d_pos(tail), 2.0 / 3.0), 2.0);
+  }
+  static __device__ __forceinline__ double Qh(double u) {
+    const float tail = fmaf(esdg_d2f_tail(u), 22.0f / 945.0f, 2.0f / 45.0f);
+    return fma(-u, fma(u, esdg_f2d_pos(tail), 1.0 / 6.0), 0.5);
+  }
   static __device__ __forceinline__ bool small(double u) { return esdg_lt_pos(u, ESDG_LOG_EPS); }
   // ln(p/m) by per-side logarithms (the log branch of the log mean)
   static __device__ __forceinline__ double ljump(double p, double m, double diff) {
@@ -38,6 +46,8 @@ struct FaceMath<float> {
   static __device__ __forceinline__ float rcp(float x) { return esdg_rcpf(x); }
   static __device__ __forceinline__ float A(float u) { return esdg_Af(u); }
   static __device__ __forceinline__ float Q(float u) { return esdg_Qf(u); }
+  static __device__ __forceinline__ float A2(float u) { return 2.0f * esdg_Af(u); }
+  static __device__ __forceinline__ float Qh(float u) { return 0.5f * esdg_Qf(u); }
   static __device__ __forceinline__ bool small(float u) { return u < ESDG_LOG_EPS32; }
   // ln(p/m) = log1p((p - m)/m): no cancellation between two large logarithms
   static __device__ __forceinline__ float ljump(float p, float m, float diff) {
@@ -100,18 +110,19 @@ __device__ __forceinline__ void face_flux(const Side<R>& M, const Side<R>& Pp, R
   const R fr = dr * rsr, ur = fr * fr;
   const R fb = db * rsb, ub = fb * fb;
   R rho_log, lnr_jump, iblog, lnb_jump;
-  if (Mth::small(ur)) {
-    const R Ar = Mth::A(ur);
-    rho_log = half * sr * Mth::Q(ur);
-    lnr_jump = (R)2 * fr * Ar;
+  const bool sr_small = Mth::small(ur);
+  const R A2r = Mth::A2(ur);  // 2 A(u_rho), also 1/<rho>_log below
+  if (sr_small) {
+    rho_log = sr * Mth::Qh(ur);
+    lnr_jump = fr * A2r;
   } else {
     lnr_jump = Mth::ljump(Pp.rho, M.rho, dr);
     rho_log = dr / lnr_jump;
   }
   if (Mth::small(ub)) {
-    const R Ab = Mth::A(ub);
-    iblog = (R)2 * rsb * Ab;
-    lnb_jump = (R)2 * fb * Ab;
+    const R A2b = Mth::A2(ub);
+    iblog = rsb * A2b;
+    lnb_jump = fb * A2b;
   } else {
     lnb_jump = Mth::ljump(Pp.b, M.b, db);
     iblog = lnb_jump / db;
@@ -136,8 +147,7 @@ __device__ __forceinline__ void face_flux(const Side<R>& M, const Side<R>& Pp, R
   const R jm2 = (R)2 * (Pp.b * Pp.u2 - M.b * M.u2);
   const R jv5 = (R)-2 * db;
   // averaged state and wave strengths
-  const R irho_hat = (R)2 * rsr * Mth::A(ur);  // 1/<rho>_log (series branch)
-  const R irh = Mth::small(ur) ? irho_hat : lnr_jump / dr;
+  const R irh = sr_small ? rsr * A2r : lnr_jump / dr;  // 1/<rho>_log
   const R a2 = gamma * pt * irh;
   const R a = Mth::sq(a2);
   const R k2 = half * (u0 * u0 + u1 * u1 + u2 * u2) + phi;
