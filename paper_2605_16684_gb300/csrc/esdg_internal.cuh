@@ -110,14 +110,20 @@ __device__ __forceinline__ double esdg_f2d(float f) {
   const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
   return (e == 0) ? 0.0 : __longlong_as_double((long long)(((unsigned long long)hi << 32) | (m << 29)));
 }
-// x * 2^k, exact, for a normal x whose result stays normal: an integer add on
-// the exponent field instead of an FP64-pipe multiply.
-__device__ __forceinline__ double esdg_ldexp_n(double x, int k) {
-  return __hiloint2double(__double2hiint(x) + (k << 20), __double2loint(x));
-}
-// the same where x may also be +-0
-__device__ __forceinline__ double esdg_ldexp_z(double x, int k) {
-  return (__double_as_longlong(x) << 1) == 0 ? x : esdg_ldexp_n(x, k);
+// x * 2^k (|k| small) with an integer add on the exponent field instead of an
+// FP64-pipe multiply: exact for normal x and normal results; infinities and
+// NaNs pass through; zero and subnormal inputs, and results below the normal
+// range, give a signed zero (flush to zero); overflow gives a signed infinity.
+// (Velocities in the far tail of a Gaussian perturbation do reach the
+// subnormal range, so the guards are needed.)
+__device__ __forceinline__ double esdg_ldexp(double x, int k) {
+  const int hi = __double2hiint(x);
+  const int ef = (hi >> 20) & 0x7ff, nf = ef + k;
+  const int sign = hi & (int)0x80000000;
+  if (ef == 0x7ff) return x;
+  if (ef == 0 || nf <= 0) return __hiloint2double(sign, 0);
+  if (nf >= 0x7ff) return __hiloint2double(sign | 0x7ff00000, 0);
+  return __hiloint2double(hi + k * (1 << 20), __double2loint(x));
 }
 
 // ---- 1-D bulk copies (the TMA engine) completing on a shared-memory mbarrier

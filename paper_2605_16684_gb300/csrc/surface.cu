@@ -97,12 +97,24 @@ __device__ __forceinline__ Side<R> side_from(const double* q, double phi, double
   return s;
 }
 
+// x * 2 and x / 2 on the exponent field for doubles (no FP64-pipe instruction;
+// esdg_ldexp: exact for normal values, subnormals flushed to zero)
+template <typename R>
+__device__ __forceinline__ R twice(R x) {
+  if constexpr (sizeof(R) == sizeof(double)) return esdg_ldexp(x, 1);
+  else return 2.0f * x;
+}
+template <typename R>
+__device__ __forceinline__ R halfof(R x) {
+  if constexpr (sizeof(R) == sizeof(double)) return esdg_ldexp(x, -1);
+  else return 0.5f * x;
+}
+
 template <typename R>
 __device__ __forceinline__ void face_flux(const Side<R>& M, const Side<R>& Pp, R phi, R n0, R n1,
                                           R n2, R gamma, R igm1, R igamma, int dissipation, R* F) {
   using Mth = FaceMath<R>;
   const R gm1 = gamma - (R)1;
-  const R half = (R)0.5;
   // log means and log jumps of rho and b
   const R sr = Pp.rho + M.rho, dr = Pp.rho - M.rho;
   const R sb = Pp.b + M.b, db = Pp.b - M.b;
@@ -127,57 +139,60 @@ __device__ __forceinline__ void face_flux(const Side<R>& M, const Side<R>& Pp, R
     lnb_jump = Mth::ljump(Pp.b, M.b, db);
     iblog = lnb_jump / db;
   }
-  const R u0 = half * (M.u0 + Pp.u0), u1 = half * (M.u1 + Pp.u1), u2 = half * (M.u2 + Pp.u2);
-  const R un = u0 * n0 + u1 * n1 + u2 * n2;
-  const R pt = sr * rsb * half;  // {{rho}} / (2 {{b}})
-  const R uu = M.u0 * Pp.u0 + M.u1 * Pp.u1 + M.u2 * Pp.u2;
+  const R u0 = halfof(M.u0 + Pp.u0), u1 = halfof(M.u1 + Pp.u1), u2 = halfof(M.u2 + Pp.u2);
+  const R un = fma(u2, n2, fma(u1, n1, u0 * n0));
+  const R pt = halfof(sr * rsb);  // {{rho}} / (2 {{b}})
+  const R uu = fma(M.u2, Pp.u2, fma(M.u1, Pp.u1, M.u0 * Pp.u0));
   const R Fr = rho_log * un;
   F[0] = Fr;
-  F[1] = Fr * u0 + pt * n0;
-  F[2] = Fr * u1 + pt * n1;
-  F[3] = Fr * u2 + pt * n2;
-  F[4] = Fr * (iblog * half * igm1 + half * uu + phi) + pt * un;
+  F[1] = fma(Fr, u0, pt * n0);
+  F[2] = fma(Fr, u1, pt * n1);
+  F[3] = fma(Fr, u2, pt * n2);
+  // F^E = F^rho (1/(2 (gamma-1) <b>_log) + u-.u+/2 + phi) + p* u_n
+  F[4] = fma(Fr, fma(iblog, halfof(igm1), fma((R)0.5, uu, phi)), pt * un);
   if (!dissipation) return;
   // entropy-variable jumps
-  const R bu2m = M.b * (M.u0 * M.u0 + M.u1 * M.u1 + M.u2 * M.u2);
-  const R bu2p = Pp.b * (Pp.u0 * Pp.u0 + Pp.u1 * Pp.u1 + Pp.u2 * Pp.u2);
-  const R jv1 = lnr_jump + lnb_jump * igm1 - (bu2p - bu2m) + (R)2 * phi * db;
-  const R jm0 = (R)2 * (Pp.b * Pp.u0 - M.b * M.u0);
-  const R jm1 = (R)2 * (Pp.b * Pp.u1 - M.b * M.u1);
-  const R jm2 = (R)2 * (Pp.b * Pp.u2 - M.b * M.u2);
-  const R jv5 = (R)-2 * db;
+  const R bu2m = M.b * fma(M.u2, M.u2, fma(M.u1, M.u1, M.u0 * M.u0));
+  const R bu2p = Pp.b * fma(Pp.u2, Pp.u2, fma(Pp.u1, Pp.u1, Pp.u0 * Pp.u0));
+  const R jv1 = fma(twice(phi), db, fma(lnb_jump, igm1, lnr_jump) - (bu2p - bu2m));
+  const R jm0 = twice(fma(Pp.b, Pp.u0, -M.b * M.u0));
+  const R jm1 = twice(fma(Pp.b, Pp.u1, -M.b * M.u1));
+  const R jm2 = twice(fma(Pp.b, Pp.u2, -M.b * M.u2));
+  const R jv5 = -twice(db);
   // averaged state and wave strengths
   const R irh = sr_small ? rsr * A2r : lnr_jump / dr;  // 1/<rho>_log
   const R a2 = gamma * pt * irh;
   const R a = Mth::sq(a2);
-  const R k2 = half * (u0 * u0 + u1 * u1 + u2 * u2) + phi;
+  const R k2 = fma((R)0.5, fma(u2, u2, fma(u1, u1, u0 * u0)), phi);
   const R a2g = a2 * igm1;
   const R H = a2g + k2;
-  const R njm = n0 * jm0 + n1 * jm1 + n2 * jm2;
-  const R w2 = jv1 + u0 * jm0 + u1 * jm1 + u2 * jm2 + k2 * jv5;
-  const R ac = a2g * jv5;
-  const R w1 = w2 - a * njm + ac - a * un * jv5;
-  const R w5 = w2 + a * njm + ac + a * un * jv5;
-  const R ig = igamma;
-  const R c1 = fabs(un - a) * rho_log * half * ig * w1;
-  const R c2 = fabs(un) * rho_log * gm1 * ig * w2;
-  const R c5 = fabs(un + a) * rho_log * half * ig * w5;
+  const R njm = fma(n2, jm2, fma(n1, jm1, n0 * jm0));
+  const R w2 = fma(k2, jv5, fma(u2, jm2, fma(u1, jm1, fma(u0, jm0, jv1))));
+  const R aun = a * un, anjm = a * njm;
+  const R w2a = fma(a2g, jv5, w2);
+  const R w1 = fma(-aun, jv5, w2a - anjm);
+  const R w5 = fma(aun, jv5, w2a + anjm);
+  const R rlh = rho_log * halfof(igamma), rlg = rho_log * (gm1 * igamma);
+  const R c1 = fabs(un - a) * rlh * w1;
+  const R c2 = fabs(un) * rlg * w2;
+  const R c5 = fabs(un + a) * rlh * w5;
   const R ls = fabs(un) * pt;
   // shear part, tangent-free
-  const R y0 = jm0 + u0 * jv5, y1 = jm1 + u1 * jv5, y2 = jm2 + u2 * jv5;
-  const R yn = y0 * n0 + y1 * n1 + y2 * n2;
-  const R t0 = y0 - yn * n0, t1 = y1 - yn * n1, t2 = y2 - yn * n2;
+  const R y0 = fma(u0, jv5, jm0), y1 = fma(u1, jv5, jm1), y2 = fma(u2, jv5, jm2);
+  const R yn = fma(y2, n2, fma(y1, n1, y0 * n0));
+  const R t0 = fma(-yn, n0, y0), t1 = fma(-yn, n1, y1), t2 = fma(-yn, n2, y2);
   const R csum = c1 + c2 + c5, cdif = c5 - c1;
-  const R d0 = csum;
-  const R dm0 = csum * u0 + a * cdif * n0 + ls * t0;
-  const R dm1 = csum * u1 + a * cdif * n1 + ls * t1;
-  const R dm2 = csum * u2 + a * cdif * n2 + ls * t2;
-  const R dE = (c1 + c5) * H + a * un * cdif + c2 * k2 + ls * (u0 * t0 + u1 * t1 + u2 * t2);
-  F[0] -= half * d0;
-  F[1] -= half * dm0;
-  F[2] -= half * dm1;
-  F[3] -= half * dm2;
-  F[4] -= half * dE;
+  const R acd = a * cdif;
+  const R dm0 = fma(csum, u0, fma(acd, n0, ls * t0));
+  const R dm1 = fma(csum, u1, fma(acd, n1, ls * t1));
+  const R dm2 = fma(csum, u2, fma(acd, n2, ls * t2));
+  const R ut = fma(u2, t2, fma(u1, t1, u0 * t0));
+  const R dE = fma(c1 + c5, H, fma(aun, cdif, fma(c2, k2, ls * ut)));
+  F[0] = fma((R)-0.5, csum, F[0]);
+  F[1] = fma((R)-0.5, dm0, F[1]);
+  F[2] = fma((R)-0.5, dm1, F[2]);
+  F[3] = fma((R)-0.5, dm2, F[3]);
+  F[4] = fma((R)-0.5, dE, F[4]);
 }
 
 // Mixed precision relative to a hydrostatic background (u_bg = 0, continuous
@@ -354,7 +369,7 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
     const float dm0 = esdg_d2f(qp[1] - qm[1]), dm1 = esdg_d2f(qp[2] - qm[2]),
                 dm2 = esdg_d2f(qp[3] - qm[3]);
     const float dp = esdg_d2f(prp - prm);
-    const float pbar_p = esdg_d2f(esdg_ldexp_n(prp + prm, -1) - pbg);  // {{p}} - p_bg
+    const float pbar_p = esdg_d2f(esdg_ldexp(prp + prm, -1) - pbg);  // {{p}} - p_bg
     const float rbar = 0.5f * (Pp.rho + Mb.rho), pbar = 0.5f * (ppf + pmf);
     const float X = fmaf(dr, pbar, -rbar * dp);  // rho+ p- - rho- p+
     BgFace J;

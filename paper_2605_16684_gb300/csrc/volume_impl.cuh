@@ -381,21 +381,21 @@ template <int NP>
 __device__ __forceinline__ void prims64(double q0, double q1, double q2, double q3, double q4,
                                         double phi, double gm1, double* S, int n) {
   const double ir = esdg_rcp(q0);
-  const double hi = esdg_ldexp_n(ir, -1);  // 1/(2 rho)
+  const double hi = esdg_ldexp(ir, -1);  // 1/(2 rho)
   const double u0 = q1 * hi, u1 = q2 * hi, u2 = q3 * hi;
   double ei = fma(-q0, phi, q4);
   ei = fma(-q1, u0, ei);
   ei = fma(-q2, u1, ei);
   ei = fma(-q3, u2, ei);
   const double p = gm1 * ei;
-  const double ib = esdg_ldexp_n(p, 1) * ir;  // 1/b = 2p/rho
-  S[0 * NP + n] = esdg_ldexp_n(q0, -2);
-  S[1 * NP + n] = esdg_ldexp_n(esdg_rcp(ib), -1);
+  const double ib = esdg_ldexp(p, 1) * ir;  // 1/b = 2p/rho
+  S[0 * NP + n] = esdg_ldexp(q0, -2);
+  S[1 * NP + n] = esdg_ldexp(esdg_rcp(ib), -1);
   S[2 * NP + n] = ib;
   S[3 * NP + n] = u0;
   S[4 * NP + n] = u1;
   S[5 * NP + n] = u2;
-  S[6 * NP + n] = esdg_ldexp_z(phi, -1);
+  S[6 * NP + n] = esdg_ldexp(phi, -1);
 }
 
 // Does any pair of this element leave the FP64 series range?  All
