@@ -718,11 +718,26 @@ static_assert(sizeof(EsdgMember) % 16 == 0, "descriptors are bulk-copied");
 // dynamic shared memory a pipelined tile may use (227 KB less static use)
 #define ESDG_PIPE_SMEM_MAX (232448 - 1024)
 
-// the tile with index t: (member, first element)
+// The tile with index t: (member, first element, elements).  TABLE: from the
+// work table (EPB elements, fewer at a member's end).  SINGLE: EPB-element
+// tiles up to tile t1, then tiles of s1 elements, so that the last partial
+// round of the persistent grid is spread over all CTAs instead of a few.
 template <bool TABLE, int EPB>
-__device__ __forceinline__ int2 pipe_tile(const int2* tiles, int t) {
-  if constexpr (TABLE) return tiles[t];
-  else return make_int2(0, t * EPB);
+__device__ __forceinline__ int4 pipe_tile(const int2* tiles, int t, int t1, int s1, int E) {
+  int e0, ne;
+  if constexpr (TABLE) {
+    const int2 tr = tiles[t];
+    return make_int4(tr.x, tr.y, min(EPB, E - tr.y), 0);
+  } else {
+    if (t < t1) {
+      e0 = t * EPB;
+      ne = EPB;
+    } else {
+      e0 = t1 * EPB + (t - t1) * s1;
+      ne = s1;
+    }
+    return make_int4(0, e0, min(ne, E - e0), 0);
+  }
 }
 
 // Shared state of a pipelined CTA: mbarriers, the tile's (member, e0) in two
@@ -730,7 +745,7 @@ __device__ __forceinline__ int2 pipe_tile(const int2* tiles, int t) {
 template <bool TABLE>
 struct PipeCtl {
   unsigned long long bars[2];  // [0] RAW of the next tile, [1] CUR of this tile
-  int2 info[2];
+  int4 info[2];  // (member, first element, elements)
   EsdgMember desc[TABLE ? 2 : 1];
 };
 
@@ -849,7 +864,7 @@ template <int N, int MODE, bool TABLE>
 __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
     k_volume_pipe64(const EsdgMember one, const EsdgMember* __restrict__ members,
                     const int2* __restrict__ tiles, const int* __restrict__ ntiles_d, int ntiles_1,
-                    EsdgLGL L, double rkA, double rkB, unsigned phantom) {
+                    EsdgLGL L, double rkA, double rkB, unsigned phantom, int t1, int s1) {
   static_assert(!TABLE || MODE == 1, "the batched kernel applies an RK stage");
   using SH = Shape<N, false, false>;
   using PP = Pipe64<N, MODE>;
@@ -865,7 +880,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
   // the next tile as seen by the issuing lanes (fetched early: in TABLE mode
   // these are global loads whose latency the prologue hides)
   struct Next {
-    int2 tr;
+    int4 tr;  // (member, first element, elements)
     int E;
     const double* q;
     const double* vg;
@@ -873,9 +888,10 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
   };
   auto fetch = [&](int t) {
     Next x;
-    x.tr = pipe_tile<TABLE, EPB>(tiles, t);
-    x.Mg = TABLE ? members + x.tr.x : &ctl.desc[0];
+    const int m = TABLE ? tiles[t].x : 0;
+    x.Mg = TABLE ? members + m : &ctl.desc[0];
     x.E = x.Mg->g.E;
+    x.tr = pipe_tile<TABLE, EPB>(tiles, t, t1, s1, x.E);
     x.q = x.Mg->a.q_in;
     x.vg = reinterpret_cast<const double*>(x.Mg->a.vgeo);
     return x;
@@ -883,7 +899,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
   // issuing lanes: the next tile's (member, e0), descriptor and RAW blocks into slot s
   auto issue_next = [&](const Next& x, int s, unsigned ph = 0) {
     if (tid == ISS::FIRST) ctl.info[s] = x.tr;
-    const int e0 = x.tr.y, ne = min(EPB, x.E - e0);
+    const int e0 = x.tr.y, ne = x.tr.z;
     const BlockCopy bl[2] = {
         {sm + PP::RAW_Q, x.q + (size_t)e0 * 5 * NP, x.q + (size_t)x.E * 5 * NP, ne * 5 * NP, 8},
         {sm + PP::RAW_G, x.vg + (size_t)e0 * ESDG_NVGEO * NP, x.vg + (size_t)x.E * ESDG_NVGEO * NP,
@@ -916,7 +932,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
     const EsdgGrid& g = M.g;
     const EsdgPhys& P = M.P;
     const EsdgVolArgs& a = M.a;
-    const int E = g.E, e0 = ctl.info[slot].y;
+    const int E = g.E, e0 = ctl.info[slot].y, ne = ctl.info[slot].z;
     const int next = tile + (int)gridDim.x;
     // issuing lanes: this tile's dq (CUR) now, the next tile's location early
     Next nx;
@@ -924,7 +940,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
       if constexpr (MODE != 0) {
         const double* dqg = reinterpret_cast<const double*>(a.dq);
         const BlockCopy cb[1] = {{sm + PP::DQ, dqg + (size_t)e0 * 5 * NP, dqg + (size_t)E * 5 * NP,
-                                  min(EPB, E - e0) * 5 * NP, 8}};
+                                  ne * 5 * NP, 8}};
         pipe_issue<ISS>(tid, cb, 1, &ctl.bars[1]);
       }
       if (TABLE && next < ntiles) nx = fetch(next);  // global loads: early
@@ -938,7 +954,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
       for (int idx = tid; idx < EPB * NP; idx += T) {
         const int el2 = idx / NP, n = idx - el2 * NP;
         double* S = sm + PP::S0 + (size_t)el2 * NF * NP;
-        if (e0 + el2 < E) {
+        if (el2 < ne) {
           const double* qr = qr0 + (size_t)el2 * 5 * NP;
           const double* gr = gr0 + (size_t)el2 * ESDG_NVGEO * NP;
           double* X = sm + PP::EPI + (size_t)el2 * 6 * NP;
@@ -997,7 +1013,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
     for (int i = 0; i < Nq; i++)
 #pragma unroll
       for (int v = 0; v < 5; v++) acc[i][v] = 0.0;
-    if (active && e < E) {
+    if (active && el < ne) {
       face_lift<true, N, double>(g, a, e, d, ps + Nq * pt, acc);
       const double* S = sm + PP::S0 + (size_t)el * NF * NP;
       if (need_logs)
@@ -1006,7 +1022,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
         pencil_pass<N, false, false, false>(S, d, base, stride, L, ce_series(0.5 * P.igm1), acc);
     }
     __syncthreads();
-    if (active && e < E) {
+    if (active && el < ne) {
       double* S = sm + PP::S0 + (size_t)el * NF * NP;
 #pragma unroll
       for (int i = 0; i < Nq; i++)
@@ -1037,7 +1053,7 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
     double* const rhsp = a.rhs;
     for (int idx = tid; idx < EPB * NP; idx += T) {
       const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
-      if (e2 >= E) continue;
+      if (el2 >= ne) continue;
       const double* S = sm + PP::S0 + (size_t)el2 * NF * NP;
       const double* X = sm + PP::EPI + (size_t)el2 * 6 * NP;
       double iJ = X[5 * NP + n];
@@ -1095,7 +1111,7 @@ template <int N, int MODE, bool TABLE>
 __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     k_volume_pipe32(const EsdgMember one, const EsdgMember* __restrict__ members,
                     const int2* __restrict__ tiles, const int* __restrict__ ntiles_d, int ntiles_1,
-                    EsdgLGL L, double rkA, double rkB, unsigned phantom) {
+                    EsdgLGL L, double rkA, double rkB, unsigned phantom, int t1, int s1) {
   static_assert(!TABLE || MODE == 1, "the batched kernel applies an RK stage");
   using SH = Shape<N, true, true>;
   using PP = Pipe32<N, MODE>;
@@ -1121,7 +1137,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
   };
   using ISS = Issuers<T, SH::PENCILS>;
   struct Next {
-    int2 tr;
+    int4 tr;  // (member, first element, elements)
     int E;
     const double* q;
     const double* bg;
@@ -1131,9 +1147,10 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
   };
   auto fetch = [&](int t) {
     Next x;
-    x.tr = pipe_tile<TABLE, EPB>(tiles, t);
-    x.Mg = TABLE ? members + x.tr.x : &ctl.desc[0];
+    const int m = TABLE ? tiles[t].x : 0;
+    x.Mg = TABLE ? members + m : &ctl.desc[0];
     x.E = x.Mg->g.E;
+    x.tr = pipe_tile<TABLE, EPB>(tiles, t, t1, s1, x.E);
     x.q = x.Mg->a.q_in;
     x.bg = x.Mg->a.bg;
     x.vg = reinterpret_cast<const float*>(x.Mg->a.vgeo);
@@ -1143,7 +1160,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
   // issuing lanes: the next tile's (member, e0), descriptor and RAW blocks into slot s
   auto issue_next = [&](const Next& x, int s, unsigned ph = 0) {
     if (tid == ISS::FIRST) ctl.info[s] = x.tr;
-    const int e0 = x.tr.y, ne = min(EPB, x.E - e0);
+    const int e0 = x.tr.y, ne = x.tr.z;
     const double* v64end = x.v64 + (size_t)x.E * ESDG_NVGEO * NP;
     BlockCopy bl[3 + EPB];
     bl[0] = {rawq, x.q + (size_t)e0 * 5 * NP, x.q + (size_t)x.E * 5 * NP, ne * 5 * NP, 8};
@@ -1182,13 +1199,12 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     const EsdgGrid& g = M.g;
     const EsdgPhys& P = M.P;
     const EsdgVolArgs& a = M.a;
-    const int E = g.E, e0 = ctl.info[slot].y;
+    const int E = g.E, e0 = ctl.info[slot].y, ne = ctl.info[slot].z;
     const int next = tile + (int)gridDim.x;
     // issuing lanes: this tile's background rhs and dq (CUR) now, the next
     // tile's location early
     Next nx;
     if (ISS::is(tid)) {
-      const int ne = min(EPB, E - e0);
       const float* dqg = reinterpret_cast<const float*>(a.dq);
       const BlockCopy cb[2] = {
           {currb, a.rhs_bg + (size_t)e0 * 3 * NP, a.rhs_bg + (size_t)E * 3 * NP, ne * 3 * NP, 8},
@@ -1208,7 +1224,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
       for (int idx = tid; idx < EPB * NP; idx += T) {
         const int el2 = idx / NP, n = idx - el2 * NP;
         float* S = sm + (size_t)el2 * NF * NP;
-        if (e0 + el2 < E) {
+        if (el2 < ne) {
           const double* qr = qr0 + (size_t)el2 * 5 * NP;
           const double* br = br0 + (size_t)el2 * 3 * NP;
           const float* gr = gr0 + (size_t)el2 * ESDG_NVGEO * NP;
@@ -1265,7 +1281,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     for (int i = 0; i < Nq; i++)
 #pragma unroll
       for (int v = 0; v < 5; v++) acc[i][v] = 0.0f;
-    if (active && e < E) {
+    if (active && el < ne) {
       const float* S = sm + (size_t)el * NF * NP;
       const float ce = esdg_d2f(0.5 * P.igm1);
       if (need_logs)
@@ -1278,7 +1294,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
       face_lift<false, N, float>(g, a, e, d, ps + Nq * pt, acc);
     }
     __syncthreads();
-    if (active && e < E) {
+    if (active && el < ne) {
       float* S = sm + (size_t)el * NF * NP;
 #pragma unroll
       for (int i = 0; i < Nq; i++)
@@ -1305,7 +1321,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     const double dtv = a.dt;
     for (int idx = tid; idx < EPB * NP; idx += T) {
       const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
-      if (e2 >= E) continue;
+      if (el2 >= ne) continue;
       const float* S = sm + (size_t)el2 * NF * NP;
       const double* X = epq + (size_t)el2 * 5 * NP;
       const float iJ = epj[(size_t)el2 * NP + n];
@@ -1362,6 +1378,29 @@ int pipe_grid_cap(int threads, size_t smem) {
   return cap[dev];
 }
 
+// Tiles of a single mesh of E elements on a persistent grid of at most cap
+// CTAs: full rounds of EPB-element tiles, then the remaining elements as tiles
+// of s1 = ceil(rest / cap) elements, so the last round is spread over the grid.
+inline void pipe_split(int E, int EPB, int cap, int& ntiles, int& grid, int& t1, int& s1) {
+  const int nfull = (E + EPB - 1) / EPB;
+  grid = nfull < cap ? nfull : cap;
+  if (grid <= 0) {
+    ntiles = grid = t1 = 0;
+    s1 = 1;
+    return;
+  }
+  t1 = (nfull / grid) * grid;  // tiles of the full rounds
+  if (t1 * EPB >= E) {         // no partial round
+    t1 = nfull;
+    s1 = EPB;
+    ntiles = nfull;
+    return;
+  }
+  const int rest = E - t1 * EPB;
+  s1 = (rest + grid - 1) / grid;
+  ntiles = t1 + (rest + s1 - 1) / s1;
+}
+
 inline EsdgMember pipe_member(const EsdgGrid& g, const EsdgPhys& P, const EsdgVolArgs& a) {
   EsdgMember m;
   memset(&m, 0, sizeof(m));
@@ -1379,10 +1418,12 @@ cudaError_t launch_pipe64(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L
   constexpr auto k = k_volume_pipe64<N, MODE, false>;
   const int cap = pipe_grid_cap<k>(SH::THREADS, Pipe64<N, MODE>::SMEM);
   if (cap < 0) return cudaErrorInvalidConfiguration;
-  const int ntiles = (g.E + SH::EPB - 1) / SH::EPB;
+  int ntiles, grid, t1, s1;
+  pipe_split(g.E, SH::EPB, cap, ntiles, grid, t1, s1);
   if (ntiles == 0) return cudaSuccess;
-  k<<<ntiles < cap ? ntiles : cap, SH::THREADS, Pipe64<N, MODE>::SMEM, s>>>(
-      pipe_member(g, P, a), nullptr, nullptr, nullptr, ntiles, L, a.rkA, a.rkB, esdg_take_phantom());
+  k<<<grid, SH::THREADS, Pipe64<N, MODE>::SMEM, s>>>(pipe_member(g, P, a), nullptr, nullptr, nullptr,
+                                                     ntiles, L, a.rkA, a.rkB, esdg_take_phantom(),
+                                                     t1, s1);
   return cudaGetLastError();
 }
 
@@ -1393,10 +1434,12 @@ cudaError_t launch_pipe32(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L
   constexpr auto k = k_volume_pipe32<N, MODE, false>;
   const int cap = pipe_grid_cap<k>(SH::THREADS, Pipe32<N, MODE>::SMEM);
   if (cap < 0) return cudaErrorInvalidConfiguration;
-  const int ntiles = (g.E + SH::EPB - 1) / SH::EPB;
+  int ntiles, grid, t1, s1;
+  pipe_split(g.E, SH::EPB, cap, ntiles, grid, t1, s1);
   if (ntiles == 0) return cudaSuccess;
-  k<<<ntiles < cap ? ntiles : cap, SH::THREADS, Pipe32<N, MODE>::SMEM, s>>>(
-      pipe_member(g, P, a), nullptr, nullptr, nullptr, ntiles, L, a.rkA, a.rkB, esdg_take_phantom());
+  k<<<grid, SH::THREADS, Pipe32<N, MODE>::SMEM, s>>>(pipe_member(g, P, a), nullptr, nullptr, nullptr,
+                                                     ntiles, L, a.rkA, a.rkB, esdg_take_phantom(),
+                                                     t1, s1);
   return cudaGetLastError();
 }
 
@@ -1428,7 +1471,7 @@ int pipe_batch(int what, const EsdgMember* members, const int2* tiles, const int
   }
   EsdgMember none;
   memset(&none, 0, sizeof(none));
-  k<<<grid, SH::THREADS, SMEM, s>>>(none, members, tiles, ntiles, 0, L, A, B, 0u);
+  k<<<grid, SH::THREADS, SMEM, s>>>(none, members, tiles, ntiles, 0, L, A, B, 0u, 0, 0);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
