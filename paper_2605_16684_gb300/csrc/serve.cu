@@ -111,6 +111,7 @@ struct es_dg_server {
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
   int use_graph = 1;
+  int force_variant = -1;  // ES_DG_BATCH_VARIANT: skip the autotuner (tests)
   std::map<long long, std::pair<int, int>> tuned;  // (N, mixed) -> (variant, grid mult)
   // statistics
   es_dg_server_stats_t st{};
@@ -219,15 +220,31 @@ int upload(es_dg_server* s) {
 // Autotune one group: every tile shape x grid multiplier, timed on the current
 // members with zero RK weights (B = 0 leaves the state unchanged; dq is
 // rewritten at the next stage 0 anyway).
+// tuning results shared by the servers of this process: (device, N, mixed) -> (variant, grid multiplier)
+std::mutex g_tuned_mu;
+std::map<long long, std::pair<int, int>> g_tuned;
+
 int autotune(es_dg_server* s, Group& g) {
+  const int nvar = g.mixed ? esdg_volume_batch_variants_mixed(g.N) : esdg_volume_batch_variants_f64(g.N);
+  if (s->force_variant >= 0) {
+    g.variant = s->force_variant < nvar ? s->force_variant : nvar - 1;
+    g.grid_vol = s->sms * vol_occ(g, g.variant);
+    s->graph_valid = false;
+    return ES_DG_OK;
+  }
   const long long key = g.N * 2 + g.mixed;
+  const long long gkey = ((long long)s->device << 8) | key;
   auto it = s->tuned.find(key);
+  if (it == s->tuned.end()) {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto jt = g_tuned.find(gkey);
+    if (jt != g_tuned.end()) it = s->tuned.insert({key, jt->second}).first;
+  }
   if (it != s->tuned.end()) {
     g.variant = it->second.first;
     g.grid_vol = s->sms * it->second.second;
     return ES_DG_OK;
   }
-  const int nvar = g.mixed ? esdg_volume_batch_variants_mixed(g.N) : esdg_volume_batch_variants_f64(g.N);
   float best = 1e30f;
   int bv = 0, bm = 1;
   cudaEvent_t a, b;
@@ -263,6 +280,10 @@ int autotune(es_dg_server* s, Group& g) {
   g.variant = bv;
   g.grid_vol = s->sms * bm;
   s->tuned[key] = {bv, bm};
+  {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    g_tuned[gkey] = {bv, bm};
+  }
   s->graph_valid = false;
   return ES_DG_OK;
 }
@@ -541,6 +562,8 @@ int es_dg_server_create(size_t hbm_budget_bytes, int max_slots, void* cuda_strea
   }
   const char* g = std::getenv("ES_DG_NO_GRAPH");
   s->use_graph = !(g && g[0] == '1');
+  const char* v = std::getenv("ES_DG_BATCH_VARIANT");
+  if (v && v[0] >= '0' && v[0] <= '9') s->force_variant = v[0] - '0';
   s->t0 = now_s();
   s->worker = std::thread(worker, s);
   *out = s;

@@ -77,6 +77,25 @@ def test_result_same_alone_and_in_mix(lib):
     assert np.array_equal(qa, qm)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_every_batched_variant_equals_single_handle(lib, monkeypatch, variant):
+    # the autotuner's candidates (pipelined table-driven kernel, per-tile kernel at two
+    # tile shapes), each forced in turn: bitwise the single-handle result
+    monkeypatch.setenv("ES_DG_BATCH_VARIANT", str(variant))
+    reqs = [dict(K=(5, 4, 3), N=4, precision="fp64", nsteps=3, warp=0.05),
+            dict(K=(4, 4, 3), N=4, precision="mixed", nsteps=4, warp=0.05, amp=0.7),
+            dict(K=(3, 3, 3), N=3, precision="mixed", nsteps=3),
+            dict(K=(2, 2, 2), N=7, precision="mixed", nsteps=2),
+            dict(kind="channel", K=(6, 3, 2), N=4, precision="mixed", nsteps=2)]
+    srv = lib.Server()
+    tickets = [srv.submit(**r) for r in reqs]
+    for t, r in zip(tickets, reqs):
+        res = srv.wait(t)
+        assert res["status"] == 0, srv.stats()["error"]
+        assert np.array_equal(res["q"], single_handle(lib, r)[0]), r
+    srv.close()
+
+
 def test_twin_meshes_share_geometry_exactly(lib):
     # members with the same mesh and order copy the first one's geometry at
     # admission; every result still equals its own single-handle solve bit for bit
