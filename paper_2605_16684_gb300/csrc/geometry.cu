@@ -25,25 +25,29 @@ __global__ void k_geometry(EsdgGrid g, EsdgLGL L, EsdgPhys P, double* __restrict
   dd* X = sg;            // [3][np]
   dd* dX = X + 3 * np;   // [3 comp][3 dir][np]
   dd* V = dX + 9 * np;   // [3][np]
+  dd* R1 = V + 3 * np;   // [3][Nq] 1-D node offsets from lo along each direction
+  dd* S1 = R1 + 3 * Nq;  // [3][Nq] their warp sines sin(2 pi r / L)
   const int ex = e % g.K[0], ey = (e / g.K[0]) % g.K[1], ez = e / (g.K[0] * g.K[1]);
   const int eidx[3] = {ex, ey, ez};
+  // the unwarped coordinates and the warp sines are functions of one 1-D index
+  for (int it = threadIdx.x; it < 3 * Nq; it += blockDim.x) {
+    const int d = it / Nq, i = it - d * Nq;
+    const double Ld = g.hi[d] - g.lo[d];
+    // offset from lo: L (e + (1 + xi)/2) / K
+    const dd xi = dd{L.xi[i], L.xi_lo[i]};
+    dd t = dd_add(dd_make(1.0), xi);
+    t = dd{0.5 * t.hi, 0.5 * t.lo};
+    t = dd_add(dd_make((double)eidx[d]), t);
+    R1[it] = dd_div_d(dd_mul_d(t, Ld), (double)g.K[d]);
+    if (g.warp != 0.0) S1[it] = dd_sinpi(dd_div_d(dd_mul_d(R1[it], 2.0), Ld));
+  }
+  __syncthreads();
   for (int n = threadIdx.x; n < np; n += blockDim.x) {
     const int ijk[3] = {n % Nq, (n / Nq) % Nq, n / (Nq * Nq)};
-    dd r[3];
-    double Ld[3];
-    for (int d = 0; d < 3; d++) {
-      Ld[d] = g.hi[d] - g.lo[d];
-      // offset from lo: L (e + (1 + xi)/2) / K
-      const dd xi = dd{L.xi[ijk[d]], L.xi_lo[ijk[d]]};
-      dd t = dd_add(dd_make(1.0), xi);
-      t = dd{0.5 * t.hi, 0.5 * t.lo};
-      t = dd_add(dd_make((double)eidx[d]), t);
-      r[d] = dd_div_d(dd_mul_d(t, Ld[d]), (double)g.K[d]);
-    }
-    dd o[3] = {r[0], r[1], r[2]};
+    dd o[3] = {R1[ijk[0]], R1[Nq + ijk[1]], R1[2 * Nq + ijk[2]]};
     if (g.warp != 0.0) {
-      dd sv[3];
-      for (int d = 0; d < 3; d++) sv[d] = dd_sinpi(dd_div_d(dd_mul_d(r[d], 2.0), Ld[d]));
+      const dd sv[3] = {S1[ijk[0]], S1[Nq + ijk[1]], S1[2 * Nq + ijk[2]]};
+      const double Ld[3] = {g.hi[0] - g.lo[0], g.hi[1] - g.lo[1], g.hi[2] - g.lo[2]};
       o[0] = dd_add(o[0], dd_mul(dd_mul_d(sv[1], g.warp * Ld[0]), sv[2]));
       o[1] = dd_add(o[1], dd_mul(dd_mul_d(sv[2], g.warp * Ld[1]), sv[0]));
       o[2] = dd_add(o[2], dd_mul(dd_mul_d(sv[0], g.warp * Ld[2]), sv[1]));
@@ -259,7 +263,7 @@ cudaError_t esdg_launch_background(const EsdgGrid& g, const EsdgPhys& P, const d
 cudaError_t esdg_launch_geometry(const EsdgGrid& g, const EsdgLGL& L, double* x, double* J,
                                  double* Ja, double* vgeo, float* vgeo32, double* fgeo,
                                  const EsdgPhys& P, cudaStream_t s) {
-  const size_t smem = sizeof(dd) * 15 * g.np;
+  const size_t smem = sizeof(dd) * (15 * (size_t)g.np + 6 * (size_t)g.Nq);
   if (smem > 48 * 1024) {
     cudaError_t err = cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
