@@ -174,33 +174,13 @@ __device__ __forceinline__ bool esdg_mbar_wait(unsigned long long* bar, unsigned
   }
   return false;
 }
-// Copy n elements (double or float) from global src into shared memory at
-// region + sh, where sh = (src / sizeof(T)) mod (16 / sizeof(T)): the interior
-// then is 16-byte aligned on both sides and goes as one bulk copy on `bar`; the
-// few leading and trailing elements outside it are copied by the calling
-// thread.  region must be 16-byte aligned and hold n + 16/sizeof(T) - 1
-// elements.  esdg_block_bytes gives the bulk bytes of such a copy (the
-// barrier's expect_tx, registered before the copies are issued).
+// The shift of a block's data in its shared-memory copy target: the bulk copy
+// starts at the 16-byte boundary at or below src, so the block's first element
+// lands (src mod 16) / sizeof(T) elements into the target.
 template <typename T>
 __device__ __forceinline__ int esdg_block_shift(const T* src) {
   constexpr unsigned long long K = 16 / sizeof(T);
   return (int)((reinterpret_cast<unsigned long long>(src) / sizeof(T)) % K);
-}
-template <typename T>
-__device__ __forceinline__ void esdg_block_split(const T* src, int n, int& sh, int& head,
-                                                 int& body) {
-  constexpr int K = 16 / sizeof(T);
-  sh = esdg_block_shift(src);
-  head = (K - sh) % K;
-  if (head > n) head = n;
-  body = ((n - head) / K) * K;
-}
-template <typename T>
-__device__ __forceinline__ unsigned esdg_block_bytes(const T* src, int n) {
-  if (n <= 0) return 0;
-  int sh, head, body;
-  esdg_block_split(src, n, sh, head, body);
-  return (unsigned)body * (unsigned)sizeof(T);
 }
 template <typename T>
 __device__ __forceinline__ void esdg_cp_async(T* dst, const T* src) {  // sizeof(T) bytes
@@ -211,26 +191,6 @@ __device__ __forceinline__ void esdg_cp_async(T* dst, const T* src) {  // sizeof
 __device__ __forceinline__ void esdg_cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
-// the bulk interior of the block copy (one thread)
-template <typename T>
-__device__ __forceinline__ void esdg_block_bulk(T* region, const T* src, int n,
-                                                unsigned long long* bar) {
-  if (n <= 0) return;
-  int sh, head, body;
-  esdg_block_split(src, n, sh, head, body);
-  if (body > 0)
-    esdg_bulk_g2s(region + sh + head, src + head, (unsigned)body * (unsigned)sizeof(T), bar);
-}
-// all of the block's elements outside the bulk interior, by the calling thread
-template <typename T>
-__device__ __forceinline__ void esdg_block_edges(T* region, const T* src, int n) {
-  if (n <= 0) return;
-  int sh, head, body;
-  esdg_block_split(src, n, sh, head, body);
-  for (int i = 0; i < head; i++) esdg_cp_async(region + sh + i, src + i);
-  for (int i = head + body; i < n; i++) esdg_cp_async(region + sh + i, src + i);
-}
-
 // x < y for non-negative doubles, compared as integers (no FP64-pipe compare)
 __device__ __forceinline__ bool esdg_lt_pos(double x, double y) {
   return __double_as_longlong(x) < __double_as_longlong(y);
@@ -248,15 +208,6 @@ __device__ __forceinline__ float esdg_rcpf(float x) {
 // (coefficients of f/artanh f).  For u < 1e-4 four terms leave a truncation
 // error below 2e-17.
 #define ESDG_LOG_EPS 1.0e-4
-__device__ __forceinline__ double esdg_A(double u) {
-  return fma(u, fma(u, fma(u, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), 1.0);
-}
-__device__ __forceinline__ double esdg_Q(double u) {
-  return fma(u, fma(u, fma(u, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
-}
-__device__ __forceinline__ double esdg_Q2(double u) {  // 2 Q(u)
-  return fma(u, fma(u, fma(u, -88.0 / 945.0, -8.0 / 45.0), -2.0 / 3.0), 2.0);
-}
 // FP64 series with the tail in FP32: for u < 1e-4 the terms beyond u^1 are below
 // 2e-9 in size, so evaluating them in FP32 (relative error ~2^-22) perturbs the
 // result by < 1e-16 of its value; two DFMA instead of three.  Used on the

@@ -796,11 +796,6 @@ __device__ __forceinline__ BlockSpan bc_span(const BlockCopy& c) {
   s.tail0 = s.b >= end ? c.n : (s.b > src ? (int)((s.b - src) / (unsigned)c.esz) : 0);
   return s;
 }
-// the shift of a block's data in its shared-memory target
-template <typename T>
-__device__ __forceinline__ int bc_shift(const T* src) {
-  return (int)((reinterpret_cast<unsigned long long>(src) & 15ull) / sizeof(T));
-}
 
 // The copy issue of a pipelined CTA is spread over the lanes that own no pencil
 // (all in the last warp; thread 0 alone when every lane has a pencil): lane il
@@ -1558,7 +1553,5 @@ int batch_occupancy() {
   return nb > 0 ? nb : 1;
 }
 
-template <int N, bool MIXED, bool BG, int EPB_>
-constexpr int batch_epb() { return Shape<N, MIXED, BG, EPB_>::EPB; }
 
 }  // namespace esdg_vol
