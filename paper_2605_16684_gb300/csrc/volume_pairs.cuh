@@ -1,0 +1,457 @@
+// volume_pairs.cuh -- the arithmetic of the flux-differencing volume kernels
+// (Section 3, Eq. (nm:semi); Section 4.1): tile shapes, node data, the two-point
+// pair in FP64 and FP32 (with and without a hydrostatic background), the pencil
+// pass, the interface lifts, the node prologues and the mixed stage update.
+// Shared by the per-tile kernels (volume_tile.cuh) and the pipelined
+// persistent kernels (volume_pipe.cuh), so both give bitwise the same results.
+#pragma once
+#include <cstring>
+#include <type_traits>
+
+#include "esdg_internal.cuh"
+
+namespace esdg_vol {
+
+
+template <int N, bool MIXED>
+struct Cfg;
+// elements per CTA, chosen so that 3 Nq^2 EPB pencils fill whole warps
+template <> struct Cfg<1, false> { static constexpr int EPB = 8; };
+template <> struct Cfg<2, false> { static constexpr int EPB = 16; };
+template <> struct Cfg<3, false> { static constexpr int EPB = 8; };
+template <> struct Cfg<4, false> { static constexpr int EPB = 5; };
+template <> struct Cfg<5, false> { static constexpr int EPB = 2; };
+template <> struct Cfg<6, false> { static constexpr int EPB = 1; };
+template <> struct Cfg<7, false> { static constexpr int EPB = 1; };
+template <> struct Cfg<1, true> { static constexpr int EPB = 16; };
+template <> struct Cfg<2, true> { static constexpr int EPB = 16; };
+template <> struct Cfg<3, true> { static constexpr int EPB = 8; };
+template <> struct Cfg<4, true> { static constexpr int EPB = 5; };
+template <> struct Cfg<5, true> { static constexpr int EPB = 3; };
+template <> struct Cfg<6, true> { static constexpr int EPB = 2; };
+template <> struct Cfg<7, true> { static constexpr int EPB = 2; };
+
+template <int N, bool MIXED, bool BG = false, int EPB_ = 0>
+struct Shape {
+  static constexpr int Nq = N + 1, NP = Nq * Nq * Nq, NPEN = Nq * Nq;
+  static constexpr int EPB = EPB_ > 0 ? EPB_ : Cfg<N, MIXED>::EPB;  // elements per CTA (tile)
+  static constexpr int PENCILS = 3 * NPEN * EPB;
+  static constexpr int THREADS = ((PENCILS + 31) / 32) * 32;
+  // node fields: rq=rho/4, bh=b/2, ib=1/b, uh=u/2 (3), ph=phi/2, [lr, lb], nh=Ja/2 (9),
+  // [background: rq'=rho'/4, bh'=b'/2, rq_bg, bh_bg, 1/b_bg, p_bg, p'=p-p_bg]
+  static constexpr int F_LR = 7, F_LB = 8;
+  static constexpr int F_NH = MIXED ? 7 : 9;
+  static constexpr int F_BG = F_NH + 9;
+  static constexpr int NF = F_NH + 9 + (BG ? 7 : 0);
+  using R = typename std::conditional<MIXED, float, double>::type;
+  static constexpr size_t SMEM = sizeof(R) * (size_t)NF * NP * EPB;
+};
+
+template <typename R>
+struct Node {
+  R rq, bh, ib, u0, u1, u2, ph, n0, n1, n2, lr, lb;
+  R rqp, bhp, rqb, bhb, ibb, pb, pp;  // perturbation and background (mixed mode with a background)
+};
+
+template <typename R, bool LOGS, int F_NH, int NP, bool BG = false>
+__device__ __forceinline__ Node<R> load_node(const R* __restrict__ S, int n, int d) {
+  Node<R> a;
+  a.rq = S[0 * NP + n];
+  a.bh = S[1 * NP + n];
+  a.ib = S[2 * NP + n];
+  a.u0 = S[3 * NP + n];
+  a.u1 = S[4 * NP + n];
+  a.u2 = S[5 * NP + n];
+  a.ph = S[6 * NP + n];
+  const R* nh = S + (F_NH + 3 * d) * NP;
+  a.n0 = nh[0 * NP + n];
+  a.n1 = nh[1 * NP + n];
+  a.n2 = nh[2 * NP + n];
+  if (LOGS && F_NH == 9) {
+    a.lr = S[7 * NP + n];
+    a.lb = S[8 * NP + n];
+  } else {
+    a.lr = a.lb = (R)0;
+  }
+  if (BG) {
+    const R* b = S + (F_NH + 9) * NP;
+    a.rqp = b[0 * NP + n];
+    a.bhp = b[1 * NP + n];
+    a.rqb = b[2 * NP + n];
+    a.bhb = b[3 * NP + n];
+    a.ibb = b[4 * NP + n];
+    a.pb = b[5 * NP + n];
+    a.pp = b[6 * NP + n];
+  }
+  return a;
+}
+
+// The artanh series of 1/<b>_log scaled by ce = 1/(2(gamma - 1)): the energy
+// flux only needs ce/<b>_log, so ce goes into the coefficients (computed once
+// per thread) and one FMA per pair folds the term into the energy bracket.
+// Tail beyond u^1 in FP32 (see esdg_A_t).
+struct CeSeries {
+  double c0, c1;    // ce, ce/3
+  float c2f, c3f;   // ce/5, ce/7
+};
+__device__ __forceinline__ CeSeries ce_series(double ce) {
+  return CeSeries{ce, ce * (1.0 / 3.0), esdg_d2f(ce * 0.2), esdg_d2f(ce * (1.0 / 7.0))};
+}
+__device__ __forceinline__ double esdg_Ace_t(double u, const CeSeries& c) {
+  const float tail = fmaf(esdg_d2f_tail(u), c.c3f, c.c2f);
+  return fma(u, fma(u, esdg_f2d_pos(tail), c.c1), c.c0);
+}
+
+// One unordered pair (i = A, l = B) in FP64: 61 FP64 instructions on the
+// series path.  ai += Dt_il H(i,l), al += Dt_li H(l,i).  The momentum flux is
+// regrouped as Fr {{u}} + (p* + g_own) {{n}}, so the gravity coefficient of
+// each side folds into its pressure term with one FMA.
+template <bool LOGS>
+__device__ __forceinline__ void pair64(const Node<double>& A, const Node<double>& B, double dil,
+                                       double dli, const CeSeries& cs, double* ai, double* al) {
+  const double sr = A.rq + B.rq;  // {{rho}}/2
+  const double sb = A.bh + B.bh;  // {{b}}
+  const double rsb = esdg_rcp(sb);
+  const double pt = sr * rsb;     // p* = {{rho}}/(2{{b}})
+  const double dr = A.rq - B.rq, db = A.bh - B.bh;
+  const double fr = dr * esdg_rcp_lo(sr), ur = fr * fr;
+  const double fb = db * rsb, ub = fb * fb;
+  const double uu = fma(A.u2, B.u2, fma(A.u1, B.u1, A.u0 * B.u0));  // u_i . u_l / 4
+  const double t = fma(2.0, uu, A.ph + B.ph);                        // u_i.u_l/2 + {{phi}}
+  double rlog, bracket;  // <rho>_log and ce/<b>_log + t
+  if (!LOGS) {
+    rlog = sr * esdg_Q2_t(ur);
+    bracket = fma(rsb, esdg_Ace_t(ub, cs), t);
+  } else {
+    if (esdg_lt_pos(ur, ESDG_LOG_EPS)) rlog = sr * esdg_Q2_t(ur);
+    else rlog = (4.0 * dr) * esdg_rcp(A.lr - B.lr);
+    if (esdg_lt_pos(ub, ESDG_LOG_EPS)) bracket = fma(rsb, esdg_Ace_t(ub, cs), t);
+    else bracket = fma((A.lb - B.lb) * esdg_rcp(2.0 * db), cs.c0, t);
+  }
+  const double n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;  // {{Ja^d}}
+  const double u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;  // {{u}}
+  const double un = fma(u2, n2, fma(u1, n1, u0 * n0));
+  const double Fr = rlog * un;
+  const double f0 = Fr * u0, f1 = Fr * u1, f2 = Fr * u2;
+  const double FE = un * fma(rlog, bracket, pt);
+  // gravity: 1/2 rho_hat [[phi]] with rho_hat = {{b}} <rho>_log / b_(own node)
+  const double gq = sb * rlog * (B.ph - A.ph);
+  const double pi = fma(gq, A.ib, pt), pl = fma(-gq, B.ib, pt);
+  ai[0] = fma(dil, Fr, ai[0]);
+  ai[1] = fma(dil, fma(pi, n0, f0), ai[1]);
+  ai[2] = fma(dil, fma(pi, n1, f1), ai[2]);
+  ai[3] = fma(dil, fma(pi, n2, f2), ai[3]);
+  ai[4] = fma(dil, FE, ai[4]);
+  al[0] = fma(dli, Fr, al[0]);
+  al[1] = fma(dli, fma(pl, n0, f0), al[1]);
+  al[2] = fma(dli, fma(pl, n1, f1), al[2]);
+  al[3] = fma(dli, fma(pl, n2, f2), al[3]);
+  al[4] = fma(dli, FE, al[4]);
+}
+
+// The same pair in FP32 (mixed mode; geopotential relative to the element).
+template <bool LOGS>
+__device__ __forceinline__ void pair32(const Node<float>& A, const Node<float>& B, float dil,
+                                       float dli, float ce, float* ai, float* al) {
+  const float sr = A.rq + B.rq;
+  const float sb = A.bh + B.bh;
+  const float rsb = esdg_rcpf(sb);
+  const float pt = sr * rsb;
+  const float dr = A.rq - B.rq, db = A.bh - B.bh;
+  const float fr = dr * esdg_rcpf(sr), ur = fr * fr;
+  const float fb = db * rsb, ub = fb * fb;
+  float rlog, iblog;
+  if (!LOGS || (ur < ESDG_LOG_EPS32 && ub < ESDG_LOG_EPS32)) {
+    rlog = sr * esdg_Q2f(ur);
+    iblog = rsb * esdg_Af(ub);
+  } else {
+    rlog = (ur < ESDG_LOG_EPS32) ? sr * esdg_Q2f(ur)
+                                 : (4.0f * dr) / log1pf(dr * esdg_rcpf(B.rq));
+    iblog = (ub < ESDG_LOG_EPS32) ? rsb * esdg_Af(ub)
+                                  : log1pf(db * esdg_rcpf(B.bh)) / (2.0f * db);
+  }
+  const float n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;
+  const float u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;
+  const float un = fmaf(u2, n2, fmaf(u1, n1, u0 * n0));
+  const float Fr = rlog * un;
+  const float m0 = fmaf(Fr, u0, pt * n0);
+  const float m1 = fmaf(Fr, u1, pt * n1);
+  const float m2 = fmaf(Fr, u2, pt * n2);
+  const float uu = fmaf(A.u2, B.u2, fmaf(A.u1, B.u1, A.u0 * B.u0));
+  const float t = fmaf(2.0f, uu, A.ph + B.ph);
+  const float FE = fmaf(Fr, fmaf(iblog, ce, t), pt * un);
+  const float gq = sb * rlog * (B.ph - A.ph);
+  const float gi = gq * A.ib, gl = -gq * B.ib;
+  ai[0] = fmaf(dil, Fr, ai[0]);
+  ai[1] = fmaf(dil, fmaf(gi, n0, m0), ai[1]);
+  ai[2] = fmaf(dil, fmaf(gi, n1, m1), ai[2]);
+  ai[3] = fmaf(dil, fmaf(gi, n2, m2), ai[3]);
+  ai[4] = fmaf(dil, FE, ai[4]);
+  al[0] = fmaf(dli, Fr, al[0]);
+  al[1] = fmaf(dli, fmaf(gl, n0, m0), al[1]);
+  al[2] = fmaf(dli, fmaf(gl, n1, m1), al[2]);
+  al[3] = fmaf(dli, fmaf(gl, n2, m2), al[3]);
+  al[4] = fmaf(dli, FE, al[4]);
+}
+
+// The FP32 pair relative to a hydrostatic background (u_bg = 0): the
+// momentum flux's pressure and gravity parts are formed as exact differences
+// H - H_bg in perturbation variables rho' = rho - rho_bg, b' = b - b_bg, so
+// their FP32 rounding is relative to the perturbation, not to the hydrostatic
+// pressure (the background's own FP64 right-hand side is added in the
+// epilogue).  The pressure mean is rewritten exactly as
+//   p* = {{rho}}/(2{{b}}) = {{p}} + T,  T = (p_i - p_l)(rho_i p_l - rho_l p_i) / (2 D),
+//   D = rho_i p_l + rho_l p_i,
+// so p* - p*_bg = {{p'}} + T - T_bg with p' = p - p_bg exact from the FP64
+// prologue and T - T_bg expanded into terms that each carry a perturbation
+// factor.  With sums over the pair (sr = rq_i + rq_l etc.):
+//   <rho>_log - <rho_bg>_log = sr' Q2(u) + sr_bg (u - u_bg) S2(u, u_bg),
+//     u - u_bg = (f - f_bg)(f + f_bg), f - f_bg = 2 (rq'_i rq_bg,l - rq'_l rq_bg,i)/(sr sr_bg),
+//     S2 the divided difference of the Q2 polynomial,
+//   {{b}}/b_i - {{b_bg}}/b_bg,i = 2 (bh'_l bh_bg,i - bh_bg,l bh'_i) / (b_i b_bg,i),
+// and the gravity difference follows by the product rule.  Density and energy
+// fluxes carry no background part (u_bg = 0) and are unchanged.
+template <bool LOGS>
+__device__ __forceinline__ void pair32bg(const Node<float>& A, const Node<float>& B, float dil,
+                                         float dli, float ce, float* ai, float* al) {
+  const float sr = A.rq + B.rq;
+  const float sb = A.bh + B.bh;
+  const float rsb = esdg_rcpf(sb);
+  const float pt = sr * rsb;
+  const float dr = A.rq - B.rq, db = A.bh - B.bh;
+  const float rsr = esdg_rcpf(sr);
+  const float fr = dr * rsr, ur = fr * fr;
+  const float fb = db * rsb, ub = fb * fb;
+  // background sums and perturbation sums
+  const float srb = A.rqb + B.rqb, sbb = A.bhb + B.bhb;
+  const float srp = A.rqp + B.rqp;
+  float ptp;
+  {
+    const float ri = 4.0f * A.rqb, rl = 4.0f * B.rqb, rpi = 4.0f * A.rqp, rpl = 4.0f * B.rqp;
+    const float dpb = A.pb - B.pb, dpp = A.pp - B.pp;
+    const float Cb = ri * B.pb - rl * A.pb;
+    const float Db = fmaf(ri, B.pb, rl * A.pb);
+    const float x1 = fmaf(ri, B.pp, fmaf(rpi, B.pb, rpi * B.pp));
+    const float x2 = fmaf(rl, A.pp, fmaf(rpl, A.pb, rpl * A.pp));
+    const float Cp = x1 - x2, Dp = x1 + x2;
+    const float C = Cb + Cp, D = Db + Dp;
+    const float num = fmaf(dpp * C, Db, dpb * fmaf(Cp, Db, -Cb * Dp));
+    ptp = fmaf(0.5f, A.pp + B.pp, num * esdg_rcpf(2.0f * D * Db));
+  }
+  const float drb = A.rqb - B.rqb;
+  const float rsrb = esdg_rcpf(srb);
+  const float frb = drb * rsrb, urb = frb * frb;
+  float rlog, iblog, rlogp;
+  if (!LOGS || (ur < ESDG_LOG_EPS32 && ub < ESDG_LOG_EPS32 && urb < ESDG_LOG_EPS32)) {
+    const float q2 = esdg_Q2f(ur);
+    rlog = sr * q2;
+    iblog = rsb * esdg_Af(ub);
+    const float fdiff = 2.0f * (A.rqp * B.rqb - B.rqp * A.rqb) * rsr * rsrb;
+    const float udiff = fdiff * (fr + frb);
+    // divided difference of Q2(u) = 2 - 2u/3 - 8u^2/45 - 88u^3/945
+    const float s2 = fmaf(-88.0f / 945.0f, fmaf(ur, ur, fmaf(ur, urb, urb * urb)),
+                          fmaf(-8.0f / 45.0f, ur + urb, -2.0f / 3.0f));
+    rlogp = fmaf(srp, q2, srb * udiff * s2);
+  } else {
+    rlog = (ur < ESDG_LOG_EPS32) ? sr * esdg_Q2f(ur)
+                                 : (4.0f * dr) / log1pf(dr * esdg_rcpf(B.rq));
+    iblog = (ub < ESDG_LOG_EPS32) ? rsb * esdg_Af(ub)
+                                  : log1pf(db * esdg_rcpf(B.bh)) / (2.0f * db);
+    const float rlogb = (urb < ESDG_LOG_EPS32) ? srb * esdg_Q2f(urb)
+                                               : (4.0f * drb) / log1pf(drb * esdg_rcpf(B.rqb));
+    rlogp = rlog - rlogb;
+  }
+  const float n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;
+  const float u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;
+  const float un = fmaf(u2, n2, fmaf(u1, n1, u0 * n0));
+  const float Fr = rlog * un;
+  const float m0 = fmaf(Fr, u0, ptp * n0);
+  const float m1 = fmaf(Fr, u1, ptp * n1);
+  const float m2 = fmaf(Fr, u2, ptp * n2);
+  const float uu = fmaf(A.u2, B.u2, fmaf(A.u1, B.u1, A.u0 * B.u0));
+  const float t = fmaf(2.0f, uu, A.ph + B.ph);
+  const float FE = fmaf(Fr, fmaf(iblog, ce, t), pt * un);
+  // gravity perturbation
+  const float dph = B.ph - A.ph;
+  const float dYi = 2.0f * (B.bhp * A.bhb - B.bhb * A.bhp) * A.ib * A.ibb;
+  const float dYl = 2.0f * (A.bhp * B.bhb - A.bhb * B.bhp) * B.ib * B.ibb;
+  const float gi = dph * fmaf(dYi, rlog, sbb * A.ibb * rlogp);
+  const float gl = -dph * fmaf(dYl, rlog, sbb * B.ibb * rlogp);
+  ai[0] = fmaf(dil, Fr, ai[0]);
+  ai[1] = fmaf(dil, fmaf(gi, n0, m0), ai[1]);
+  ai[2] = fmaf(dil, fmaf(gi, n1, m1), ai[2]);
+  ai[3] = fmaf(dil, fmaf(gi, n2, m2), ai[3]);
+  ai[4] = fmaf(dil, FE, ai[4]);
+  al[0] = fmaf(dli, Fr, al[0]);
+  al[1] = fmaf(dli, fmaf(gl, n0, m0), al[1]);
+  al[2] = fmaf(dli, fmaf(gl, n1, m1), al[2]);
+  al[3] = fmaf(dli, fmaf(gl, n2, m2), al[3]);
+  al[4] = fmaf(dli, FE, al[4]);
+}
+
+// ce: 1/(2(gamma - 1)) as float (mixed) or as the scaled series (FP64)
+template <int N, bool MIXED, bool LOGS, bool BG, typename CE>
+__device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED, BG>::R* __restrict__ S,
+                                            int d, int base, int stride, const EsdgLGL& L,
+                                            const CE& ce,
+                                            typename Shape<N, MIXED, BG>::R (&acc)[N + 1][5]) {
+  using SH = Shape<N, MIXED, BG>;
+  using R = typename SH::R;
+  constexpr int Nq = N + 1;
+#pragma unroll
+  for (int i = 0; i < Nq; i++) {
+    const Node<R> A = load_node<R, LOGS, SH::F_NH, SH::NP, BG>(S, base + i * stride, d);
+#pragma unroll
+    for (int l = i + 1; l < Nq; l++) {
+      const Node<R> B = load_node<R, LOGS, SH::F_NH, SH::NP, BG>(S, base + l * stride, d);
+      if constexpr (MIXED && BG)
+        pair32bg<LOGS>(A, B, L.Dtf[i][l], L.Dtf[l][i], ce, acc[i], acc[l]);
+      else if constexpr (MIXED)
+        pair32<LOGS>(A, B, L.Dtf[i][l], L.Dtf[l][i], ce, acc[i], acc[l]);
+      else
+        pair64<LOGS>(A, B, L.Dt[i][l], L.Dt[l][i], ce, acc[i], acc[l]);
+    }
+  }
+}
+
+// Interface terms of one pencil: the element is the "+" side of plane e_d
+// (its first node receives -(s/w) F*) and the "-" side of plane e_d + 1 (its
+// last node receives +(s/w) F*); fn is the pencil's node index on those faces.
+// INIT: the terms are the accumulators' initial value (FP64: they are then
+// loaded long before their first use), else they are added at the end (mixed:
+// after the element's reference geopotential is restored in the pair sums).
+template <bool INIT, int N, typename R>
+__device__ __forceinline__ void face_lift(const EsdgGrid& g, const EsdgVolArgs& a, int e, int d,
+                                          int fn, R (&acc)[N + 1][5]) {
+  constexpr int NPEN = (N + 1) * (N + 1);
+  // element indices selected without dynamic array indexing (no local memory)
+  const int i0 = e % g.K[0], i1 = (e / g.K[0]) % g.K[1], i2 = e / (g.K[0] * g.K[1]);
+  const int Pm = (d == 0) ? i0 : ((d == 1) ? i1 : i2);
+  const int ia = (d == 0) ? i1 : i0;  // index along esdg_others(d).o1
+  const int ib = (d == 2) ? i1 : i2;  // index along esdg_others(d).o2
+  const int Kd = (d == 0) ? g.K[0] : ((d == 1) ? g.K[1] : g.K[2]);
+  const int per = (d == 0) ? g.periodic[0] : ((d == 1) ? g.periodic[1] : g.periodic[2]);
+  int Pp = Pm + 1;
+  if (Pp == Kd && per) Pp = 0;
+  const long long fm = esdg_face_id(g, d, Pm, ia, ib);
+  const long long fp = esdg_face_id(g, d, Pp, ia, ib);
+  const R* ff = reinterpret_cast<const R*>(a.fflux);
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const R m = ff[((size_t)fm * 5 + v) * NPEN + fn], p = ff[((size_t)fp * 5 + v) * NPEN + fn];
+    if (INIT) {
+      acc[0][v] = -m;
+      acc[N][v] = p;
+    } else {
+      acc[0][v] -= m;
+      acc[N][v] += p;
+    }
+  }
+}
+
+// FP64 node primitives from the conserved state: rho/4, b/2 = rho/(4p),
+// 1/b = 2p/rho, u/2 and phi/2, with p = (gamma - 1)(E - rho phi - |rho u|^2/(2 rho)).
+// Power-of-two factors are applied exactly on the exponent field and b/2 is
+// taken as 1/(2 (1/b)): 15 FP64-pipe instructions per node.
+template <int NP>
+__device__ __forceinline__ void prims64(double q0, double q1, double q2, double q3, double q4,
+                                        double phi, double gm1, double* S, int n) {
+  const double ir = esdg_rcp(q0);
+  const double hi = esdg_ldexp(ir, -1);  // 1/(2 rho)
+  const double u0 = q1 * hi, u1 = q2 * hi, u2 = q3 * hi;
+  double ei = fma(-q0, phi, q4);
+  ei = fma(-q1, u0, ei);
+  ei = fma(-q2, u1, ei);
+  ei = fma(-q3, u2, ei);
+  const double p = gm1 * ei;
+  const double ib = esdg_ldexp(p, 1) * ir;  // 1/b = 2p/rho
+  S[0 * NP + n] = esdg_ldexp(q0, -2);
+  S[1 * NP + n] = esdg_ldexp(esdg_rcp(ib), -1);
+  S[2 * NP + n] = ib;
+  S[3 * NP + n] = u0;
+  S[4 * NP + n] = u1;
+  S[5 * NP + n] = u2;
+  S[6 * NP + n] = esdg_ldexp(phi, -1);
+}
+
+// Does any pair of this element leave the FP64 series range?  All
+// |x_n/x_0 - 1| below 0.0095 (x = rho, b) bound |f| < 0.0096 for every pair,
+// i.e. u < 1e-4.  Integer-repacked FP32 comparisons keep the FP64 pipe free.
+template <int NP>
+__device__ __forceinline__ bool out_of_series64(const double* S, int n) {
+  const float r0 = esdg_d2f(S[0]), rn = esdg_d2f(S[n]);
+  const float b0 = esdg_d2f(S[NP]), bn = esdg_d2f(S[NP + n]);
+  return fabsf(rn - r0) > 0.0095f * r0 || fabsf(bn - b0) > 0.0095f * b0;
+}
+
+// Mixed-precision node prologue: FP32 primitives, the pressure recovered in
+// FP64 (E - rho phi cancels there) and, with a background, the FP64
+// perturbations rho' = rho - rho_bg and p' = p - p_bg rounded to FP32; the
+// perturbation of b = rho/(2p) follows exactly from them,
+//   b - b_bg = (rho' p_bg - rho_bg p') / (2 p p_bg),
+// evaluated in FP32 (its rounding is relative to the perturbations).  phh is
+// the geopotential relative to the element's first node, halved (FP32
+// geometry).  5 FP64 instructions per node with a background.
+template <int NP, bool BG>
+__device__ __forceinline__ void prims32(double q0, double q1, double q2, double q3, double q4,
+                                        double phi, float phh, double gm1, float* S, int n,
+                                        double rb = 0.0, double bb = 0.0, double pbg = 0.0,
+                                        float* Bf = nullptr) {
+  const float q0f = esdg_d2f(q0), q1f = esdg_d2f(q1), q2f = esdg_d2f(q2), q3f = esdg_d2f(q3);
+  const float irf = esdg_rcpf(q0f);
+  const float hf = 0.5f * irf;
+  const float u0 = q1f * hf, u1 = q2f * hf, u2 = q3f * hf;
+  const float ke = fmaf(q3f, u2, fmaf(q2f, u1, q1f * u0));
+  const double p = gm1 * (fma(-q0, phi, q4) - esdg_f2d(ke));
+  const float pf = esdg_d2f(p);
+  const float rq = 0.25f * q0f;
+  S[0 * NP + n] = rq;
+  S[1 * NP + n] = rq * esdg_rcpf(pf);
+  S[2 * NP + n] = 2.0f * pf * irf;
+  S[3 * NP + n] = u0;
+  S[4 * NP + n] = u1;
+  S[5 * NP + n] = u2;
+  S[6 * NP + n] = phh;
+  if constexpr (BG) {
+    const float rpf = esdg_d2f(q0 - rb), ppf = esdg_d2f(p - pbg);
+    const float rbf = esdg_d2f(rb), bbf = esdg_d2f(bb), pbf = esdg_d2f(pbg);
+    Bf[0 * NP + n] = 0.25f * rpf;
+    Bf[1 * NP + n] = 0.25f * fmaf(rpf, pbf, -rbf * ppf) * esdg_rcpf(pf * pbf);  // b'/2
+    Bf[2 * NP + n] = 0.25f * rbf;
+    Bf[3 * NP + n] = 0.5f * bbf;
+    Bf[4 * NP + n] = esdg_rcpf(bbf);
+    Bf[5 * NP + n] = pbf;
+    Bf[6 * NP + n] = ppf;
+  }
+}
+
+// Mixed-precision stage update of one node: r = -(1/J) (volume + lifts) in
+// FP32, plus the background's right-hand side and the Coriolis source, all in
+// FP32 (they join an FP32 increment); FP64 only in q += B dq.  Arrays are per
+// node with stride NP between variables: rbg (3, background rhs), qin (5),
+// dqold (5) may be in shared or global memory; dq and qio are the node's
+// global locations.
+template <int NP, bool BG>
+__device__ __forceinline__ void stage32(float (&r)[5], const double* rbg, const EsdgPhys& P,
+                                        double y, const double* qin, const float* dqold, float* dq,
+                                        double* qio, double rkA, double rkB, double dt) {
+  if constexpr (BG) {
+    r[1] += esdg_d2f(rbg[0]);
+    r[2] += esdg_d2f(rbg[NP]);
+    r[3] += esdg_d2f(rbg[2 * NP]);
+  }
+  if ((P.f0 != 0.0) || (P.beta != 0.0)) {
+    const float f = esdg_d2f(P.f0 + P.beta * (y - P.y0));
+    r[1] = fmaf(f, esdg_d2f(qin[2 * NP]), r[1]);
+    r[2] = fmaf(-f, esdg_d2f(qin[NP]), r[2]);
+  }
+  const float A = esdg_d2f(rkA), B = esdg_d2f(rkB), dtf = esdg_d2f(dt);
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const float dv = fmaf(A, dqold[(size_t)v * NP], dtf * r[v]);
+    dq[(size_t)v * NP] = dv;
+    qio[(size_t)v * NP] = qin[(size_t)v * NP] + esdg_f2d(B * dv);
+  }
+}
+
+}  // namespace esdg_vol
