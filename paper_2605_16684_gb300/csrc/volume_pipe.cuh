@@ -272,7 +272,8 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
           X[2 * NP + n] = q2;
           X[3 * NP + n] = q3;
           X[4 * NP + n] = q4;
-          X[5 * NP + n] = gr[9 * NP + n];
+          // 1/J, times dt for a stage update (the epilogue's scale)
+          X[5 * NP + n] = MODE != 0 ? gr[9 * NP + n] * a.dt : gr[9 * NP + n];
         } else {  // padding element: any valid state, results are discarded
           S[0 * NP + n] = 0.25;
           S[1 * NP + n] = 0.5;
@@ -345,7 +346,8 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
       __syncthreads();
     }
 
-    // ---- epilogue: one thread per node --------------------------------------
+    // ---- epilogue: one thread per (node, variable) (eight full rounds instead
+    // of one and a partial one per node) ---------------------------------------
     const double* D0 = sm + PP::DQ + esdg_block_shift(reinterpret_cast<const double*>(a.dq) + (size_t)e0 * 5 * NP);
     // descriptor fields in registers (the stores below would force reloads)
     const double dt = a.dt;
@@ -355,35 +357,26 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
     double* const dqp = reinterpret_cast<double*>(a.dq);
     double* const qio = a.q_io;
     double* const rhsp = a.rhs;
-    for (int idx = tid; idx < EPB * NP; idx += T) {
-      const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
+    for (int idx = tid; idx < 5 * EPB * NP; idx += T) {
+      const int v = idx / (EPB * NP), rem = idx - v * (EPB * NP);
+      const int el2 = rem / NP, n = rem - el2 * NP, e2 = e0 + el2;
       if (el2 >= ne) continue;
       const double* S = sm + PP::S0 + (size_t)el2 * NF * NP;
       const double* X = sm + PP::EPI + (size_t)el2 * 6 * NP;
-      double iJ = X[5 * NP + n];
-      if constexpr (MODE != 0) iJ *= dt;
-      double r[5];
-#pragma unroll
-      for (int v = 0; v < 5; v++) r[v] = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
-      if (rot) {
+      double r = -X[5 * NP + n] * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
+      if (rot && (v == 1 || v == 2)) {
         const double y = xg[((size_t)e2 * 3 + 1) * NP + n];
         double f = Pl.f0 + Pl.beta * (y - Pl.y0);
         if constexpr (MODE != 0) f *= dt;
-        r[1] = fma(f, X[2 * NP + n], r[1]);
-        r[2] = fma(-f, X[NP + n], r[2]);
+        r = v == 1 ? fma(f, X[2 * NP + n], r) : fma(-f, X[NP + n], r);
       }
-      const size_t qb = (size_t)e2 * 5 * NP + n;
+      const size_t qv = ((size_t)e2 * 5 + v) * NP + n;
       if constexpr (MODE == 0) {
-#pragma unroll
-        for (int v = 0; v < 5; v++) rhsp[qb + (size_t)v * NP] = r[v];
+        rhsp[qv] = r;
       } else {
-        const double* D = D0 + (size_t)el2 * 5 * NP;
-#pragma unroll
-        for (int v = 0; v < 5; v++) {
-          const double dv = fma(rkA, D[v * NP + n], r[v]);
-          dqp[qb + (size_t)v * NP] = dv;
-          qio[qb + (size_t)v * NP] = fma(rkB, dv, X[v * NP + n]);
-        }
+        const double dv = fma(rkA, D0[((size_t)el2 * 5 + v) * NP + n], r);
+        dqp[qv] = dv;
+        qio[qv] = fma(rkB, dv, X[v * NP + n]);
       }
     }
   }
