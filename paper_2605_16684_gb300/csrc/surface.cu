@@ -75,24 +75,26 @@ __device__ __forceinline__ Side<R> side_from(const double* q, double phi, double
   const double rho = q[0];
   const double ir = esdg_rcp(rho);
   const double u0 = q[1] * ir, u1 = q[2] * ir, u2 = q[3] * ir;
+  // halvings on the exponent field (esdg_ldexp): no FP64-pipe instruction
   double e = fma(-rho, phi, q[4]);
-  e = fma(-0.5 * q[1], u0, e);
-  e = fma(-0.5 * q[2], u1, e);
-  e = fma(-0.5 * q[3], u2, e);
+  e = fma(-esdg_ldexp(q[1], -1), u0, e);
+  e = fma(-esdg_ldexp(q[2], -1), u1, e);
+  e = fma(-esdg_ldexp(q[3], -1), u2, e);
   const double p = gm1 * e;
+  const double b = esdg_ldexp(rho, -1) * esdg_rcp(p);  // rho/(2p)
   Side<R> s;
   if constexpr (sizeof(R) == sizeof(float)) {
     s.rho = esdg_d2f(rho);
     s.u0 = esdg_d2f(u0);
     s.u1 = esdg_d2f(u1);
     s.u2 = esdg_d2f(u2);
-    s.b = esdg_d2f(0.5 * rho * esdg_rcp(p));
+    s.b = esdg_d2f(b);
   } else {
     s.rho = rho;
     s.u0 = u0;
     s.u1 = u1;
     s.u2 = u2;
-    s.b = 0.5 * rho * esdg_rcp(p);
+    s.b = b;
   }
   return s;
 }
