@@ -51,10 +51,10 @@ FLOPS_PER_NODE = 45
 FACE_BYTES_PER_NODE = {"fp64": 160, "mixed": 140}
 
 # DRAM traffic of one FP64 volume launch (k_volume_pipe64<4, 1, 0>): ncu capture of the same
-# kernel on the 24^3 case (dram__bytes_read.sum + dram__bytes_write.sum = 332.77 MB +
-# 99.34 MB for 13 824 elements), scaled to the 32^3 launch by the element count
+# kernel on the 24^3 case (dram__bytes_read.sum + dram__bytes_write.sum = 332.80 MB +
+# 99.38 MB for 13 824 elements), scaled to the 32^3 launch by the element count
 # (profiles/volume_fp64_N4_24cubed.md).
-VOLUME_FP64_TRAFFIC_BYTES = (332.77e6 + 99.34e6) * 32768 / 13824
+VOLUME_FP64_TRAFFIC_BYTES = (332.80e6 + 99.38e6) * 32768 / 13824
 
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2     # 2 DFMA / clk / SM -> 1.258 TFLOP/s
