@@ -1,8 +1,8 @@
 // volume_impl.cuh -- flux-differencing volume kernel (Section 3, the volume term
+// of Eq. (nm:semi), with the optimisations of Section 4.1).
 // The arithmetic lives in volume_pairs.cuh, the per-tile kernels in
 // volume_tile.cuh, the pipelined persistent kernels in volume_pipe.cuh; this
 // file dispatches the single-mesh launches.
-// of Eq. (nm:semi), with the optimisations of Section 4.1).
 //
 //   rhs_i = -(1/J_i) [ sum_d sum_l Dt^{(d)}_{il} H^d(q_i, q_l) + face lifts ] + h_i
 //
