@@ -52,6 +52,8 @@ def _lib(precision: str = "double"):
             lib.or_lsrk_coeffs.argtypes = [_D, _D, _D]
             lib.or_lsrk_steps.argtypes = [C.c_void_p, _D, C.c_double, C.c_int]
             lib.or_init_bubble.argtypes = [C.c_void_p, C.c_double, C.c_double, _D, C.c_double, _D]
+            lib.or_init_bubble_profile.argtypes = [C.c_void_p, C.c_double, C.c_double, _D,
+                                                   C.c_double, C.c_int, _D]
             lib.or_init_isothermal.argtypes = [C.c_void_p, C.c_double, C.c_double, _D]
             lib.or_init_channel.argtypes = [C.c_void_p, _D]
             lib.or_integrals.argtypes = [C.c_void_p, _D, _D]
@@ -202,9 +204,14 @@ class Oracle:
         self.lib.or_lsrk_steps(self._h, _p(q), float(dt), int(nsteps))
         return q
 
-    def bubble(self, theta0=300.0, amp=0.5, centre=(500.0, 500.0, 350.0), radius=250.0):
+    def bubble(self, theta0=300.0, amp=0.5, centre=(500.0, 500.0, 350.0), radius=250.0,
+               profile="smooth"):
+        """Rising-bubble state: profile "smooth" is Eq. (smooth-rb-ic), "sharp" Eq. (sharp-rb-ic)."""
         q = np.zeros(self.shape())
-        self.lib.or_init_bubble(self._h, theta0, amp, _p(_vec(centre, 3)), radius, _p(q))
+        k = {"smooth": 0, "sharp": 1}[profile]
+        st = self.lib.or_init_bubble_profile(self._h, theta0, amp, _p(_vec(centre, 3)), radius,
+                                             k, _p(q))
+        assert st == 0
         return q
 
     def isothermal(self, T=280.0, rho_surface=1.2):

@@ -25,7 +25,8 @@
  *       efficient formulation the paper adopts.
  *   Section 3 (last paragraph): Carpenter-Kennedy five-stage fourth-order
  *       low-storage Runge-Kutta.
- *   Section 5.1, Eq. (smooth-rb-ic): cosine potential-temperature bubble.
+ *   Section 5.1, Eqs. (smooth-rb-ic) and (sharp-rb-ic): cosine and step
+ *       potential-temperature bubbles.
  *
  * Readings where the paper points elsewhere (its Eq. 76 and Eq. A.1 citations,
  * the RK coefficients, the bubble background) are stated next to the code.
@@ -756,13 +757,17 @@ int or_lsrk_steps(const or_ctx* c, double* qd, double dt, int nsteps) {
 
 static real cp_of(const or_phys* p) { return (real)p->gamma * (real)p->R / ((real)p->gamma - 1); }
 
-/* Section 5.1, Eq. (smooth-rb-ic): theta = theta0 + amp (1 + cos(pi r/rc))/2 for
- * r <= rc, over an isentropic (constant theta0) hydrostatic background:
+/* Section 5.1: a potential-temperature bubble over an isentropic (constant theta0)
+ * hydrostatic background,
+ *   Eq. (smooth-rb-ic), profile 0: theta = theta0 + amp (1 + cos(pi r/rc))/2 for r <= rc,
+ *   Eq. (sharp-rb-ic),  profile 1: theta = theta0 + amp for r <= rc,
+ * theta = theta0 outside; then
  *   Exner pi = 1 - g z/(cp theta0), p = p0 pi^(cp/R), T = theta pi, rho = p/(R T),
  *   u = 0, E = p/(gamma-1) + rho g z.
  * The pressure is left unperturbed (the background reading of the bubble). */
-int or_init_bubble(const or_ctx* c, double theta0, double amp, const double* centre,
-                   double radius, double* q) {
+int or_init_bubble_profile(const or_ctx* c, double theta0, double amp, const double* centre,
+                           double radius, int profile, double* q) {
+  if (profile != 0 && profile != 1) return -1;
   const or_phys* ph = &c->phys;
   real cp = cp_of(ph), R = (real)ph->R, g = (real)ph->g, gamma = (real)ph->gamma;
   const real pi = (real)3.141592653589793238462643383279502884L;
@@ -774,7 +779,8 @@ int or_init_bubble(const or_ctx* c, double theta0, double amp, const double* cen
       real r2 = 0;
       for (int d = 0; d < 3; d++) r2 += (X[d] - (real)centre[d]) * (X[d] - (real)centre[d]);
       real r = sqrt(r2);
-      real dth = (r <= (real)radius) ? (real)amp * (1 + cos(pi * r / (real)radius)) / 2 : 0;
+      real dth = 0;
+      if (r <= (real)radius) dth = profile ? (real)amp : (real)amp * (1 + cos(pi * r / (real)radius)) / 2;
       real ex = 1 - g * X[2] / (cp * (real)theta0);
       real p = (real)ph->p0 * pow(ex, cp / R);
       real T = ((real)theta0 + dth) * ex;
@@ -786,6 +792,11 @@ int or_init_bubble(const or_ctx* c, double theta0, double amp, const double* cen
       q[((size_t)e * NV + 4) * np + n] = (double)(p / (gamma - 1) + rho * g * X[2]);
     }
   return 0;
+}
+
+int or_init_bubble(const or_ctx* c, double theta0, double amp, const double* centre,
+                   double radius, double* q) {
+  return or_init_bubble_profile(c, theta0, amp, centre, radius, 0, q);
 }
 
 /* Isothermal rest state: rho = rho_s exp(-g z/(R T)), p = rho R T, u = 0. */

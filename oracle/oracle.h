@@ -65,6 +65,9 @@ int  or_lsrk_steps(const or_ctx* c, double* q, double dt, int nsteps);
 /* Initial states. */
 int or_init_bubble(const or_ctx* c, double theta0, double amp, const double* centre,
                    double radius, double* q);
+/* profile 0 = cosine bubble, Eq. (smooth-rb-ic); 1 = step bubble, Eq. (sharp-rb-ic) */
+int or_init_bubble_profile(const or_ctx* c, double theta0, double amp, const double* centre,
+                           double radius, int profile, double* q);
 int or_init_isothermal(const or_ctx* c, double T, double rho_surface, double* q);
 int or_init_channel(const or_ctx* c, double* q);
 
