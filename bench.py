@@ -498,6 +498,86 @@ def run_channel(args):
     print(json.dumps(out))
 
 
+SHARP = dict(K=(64, 64, 64), N=4, lo=(-1000.0, -1000.0, 0.0), hi=(1000.0, 1000.0, 2000.0),
+             periodic=(1, 1, 0), centre=(0.0, 0.0, 260.0), radius=250.0, amp=0.5, cfl=0.5)
+# Section 5.1, Table rb-timing: 8 A100s, N = 4, 64^3 elements, sharp bubble:
+# 6622.03 s (64-bit) and 3070.25 s (32-bit) for the whole run
+PAPER_SHARP_SPEEDUP_32_OVER_64 = 6622.03 / 3070.25
+
+
+def _mirror_x(q, K, N):
+    """State under x -> -x on a uniform box mesh (x-momentum negated)."""
+    Nq = N + 1
+    a = q.reshape(K[2], K[1], K[0], 5, Nq, Nq, Nq).flip(2).flip(6).clone()
+    a[:, :, :, 1] *= -1
+    return a.reshape(q.shape)
+
+
+def run_sharp(args):
+    """The paper's rising-bubble run with the sharp initial perturbation (Section 5.1,
+    Eq. (sharp-rb-ic)): 2000 m box, periodic x and y, walls z, 64^3 elements at N = 4
+    (32,768,000 nodes, the paper's L = 6 mesh), on one GPU in FP64 and in mixed precision.
+    Reports DOF-updates/s per RK stage of both and their ratio (the paper's 32-bit run was
+    2.16x its 64-bit run on 8 A100s), the entropy change and the mass / total-energy drift
+    over the run, and the mirror asymmetry of the flow under x -> -x, which the exact
+    solution does not have (the paper's figures show FP32 losing the symmetry)."""
+    import torch
+    from paper_2605_16684_gb300 import _build, _lib
+    _build.build()
+    c = SHARP
+    K = (args.K,) * 3 if args.K else c["K"]
+    res = {}
+    for prec in ("fp64", "mixed"):
+        s = _lib.Solver(*K, c["N"], lo=c["lo"], hi=c["hi"], periodic=c["periodic"],
+                        precision=prec)
+        s.init_bubble(amp=c["amp"], centre=c["centre"], radius=c["radius"], profile="sharp")
+        q0 = torch.empty(s.shape(), dtype=torch.float64, device="cuda")
+        s.get_state(q0)
+        dt = s.cfl_dt(c["cfl"])
+        s.step(dt, 2)  # warm-up, then back to the initial state
+        s.set_state(q0)
+        i0 = s.integrals()
+        s.sync()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s.step(dt, args.steps)
+        s.sync()
+        el = time.perf_counter() - t
+        i1 = s.integrals()
+        q = torch.empty_like(q0)
+        s.get_state(q)
+        s.sync()
+        torch.cuda.synchronize()
+        f = q - q0
+        asym = float(torch.linalg.vector_norm(q - _mirror_x(q, K, c["N"])) /
+                     torch.linalg.vector_norm(f))
+        res[prec] = dict(value=s.E * s.np * 5 * args.steps / el, seconds=el, dt=dt,
+                         drift=[float((i1[k] - i0[k]) / abs(i0[k])) for k in (0, 1)],
+                         entropy_change_rel=float((i1[2] - i0[2]) / abs(i0[2])),
+                         mirror_asymmetry=asym, q=q, q0=q0)
+        s.close()
+    d = res["mixed"]["q"] - res["fp64"]["q"]
+    f = res["fp64"]["q"] - res["fp64"]["q0"]
+    mom = torch.linalg.vector_norm(f[:, 1:4])
+    flow_err = [float(torch.linalg.vector_norm(d[:, v]) /
+                      (mom if v in (1, 2, 3) else torch.linalg.vector_norm(f[:, v])))
+                for v in range(5)]
+    out = {"metric": "sharp rising bubble: DOF-updates/s per RK stage (FP64, mixed), "
+                     "entropy and conservation monitors, mirror asymmetry",
+           "unit": "DOF-updates/s", "n_gpus": 1, "steps": args.steps,
+           "config": {"workload": "sharp_rising_bubble_%dx%dx%d_N4" % K,
+                      "box_m": [2000, 2000, 2000], "boundaries": "periodic x/y, walls z",
+                      "perturbation": "theta + 0.5 K for r <= 250 m about (0, 0, 260) m",
+                      "cfl": c["cfl"], "data": "synthetic"},
+           "dt_s": res["fp64"]["dt"],
+           "fp64": {k: v for k, v in res["fp64"].items() if k not in ("q", "q0")},
+           "mixed": {k: v for k, v in res["mixed"].items() if k not in ("q", "q0")},
+           "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
+           "paper_fp32_over_fp64_8xA100": PAPER_SHARP_SPEEDUP_32_OVER_64,
+           "flow_rel_err_mixed_vs_fp64_rho_rhou_rhov_rhow_E": flow_err}
+    print(json.dumps(out))
+
+
 def run_serving(args):
     import threading
     import numpy as np
@@ -565,7 +645,7 @@ def main():
     ap.add_argument("--K", type=int, default=0, help="elements per direction (small profiling cases)")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--workload", default="bubble32",
-                    choices=["bubble32", "ensemble", "serving", "channel"])
+                    choices=["bubble32", "ensemble", "serving", "channel", "sharp"])
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--check", type=int, default=4, help="ensemble members compared with FP64")
     ap.add_argument("--requests", type=int, default=60)
@@ -582,6 +662,9 @@ def main():
         return
     if args.workload == "channel":
         run_channel(args)
+        return
+    if args.workload == "sharp":
+        run_sharp(args)
         return
     if args.warmup < 3:
         args.warmup = 3

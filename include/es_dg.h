@@ -111,6 +111,13 @@ int es_dg_get_state(es_dg_t* h, double* q, int on_device);
  * (K) and radius `radius` about `centre`; pressure unperturbed; u = 0. */
 int es_dg_init_bubble(es_dg_t* h, double theta0, double amp, const double centre[3],
                       double radius);
+/* The same with the profile chosen: ES_DG_BUBBLE_SMOOTH is es_dg_init_bubble;
+ * ES_DG_BUBBLE_SHARP is the step of Section 5.1, Eq. (sharp-rb-ic): theta0 + amp
+ * for r <= radius, theta0 outside (a discontinuity the entropy-stable flux must
+ * carry without a limiter).  Any other profile: ES_DG_EINVAL. */
+enum { ES_DG_BUBBLE_SMOOTH = 0, ES_DG_BUBBLE_SHARP = 1 };
+int es_dg_init_bubble_profile(es_dg_t* h, double theta0, double amp, const double centre[3],
+                              double radius, int profile);
 /* Synthetic baroclinic-channel state (balanced zonal jet of isothermal columns
  * plus a 1 m/s Gaussian wind perturbation; see the oracle for the formulas). */
 int es_dg_init_channel(es_dg_t* h);
@@ -195,7 +202,8 @@ typedef struct es_dg_server es_dg_server;
 typedef struct {
   int kind;                  /* 0 = rising bubble (1000 m cube, periodic x/y, walls z),
                                 1 = baroclinic channel stand-in (40000 x 6000 x 30 km,
-                                    periodic x, walls y/z, f0 = 1e-4) */
+                                    periodic x, walls y/z, f0 = 1e-4),
+                                2 = sharp rising bubble (as 0, Eq. (sharp-rb-ic)) */
   int kx, ky, kz, N;         /* elements per direction, order (1..7) */
   es_dg_precision precision;
   int nsteps;                /* LSRK steps to run */

@@ -80,6 +80,8 @@ SIGNATURES = {
     "es_dg_set_state": (C.c_int, [_VP, _VP, C.c_int]),
     "es_dg_get_state": (C.c_int, [_VP, _VP, C.c_int]),
     "es_dg_init_bubble": (C.c_int, [_VP, C.c_double, C.c_double, _DP, C.c_double]),
+    "es_dg_init_bubble_profile": (C.c_int, [_VP, C.c_double, C.c_double, _DP, C.c_double,
+                                            C.c_int]),
     "es_dg_init_channel": (C.c_int, [_VP]),
     "es_dg_rhs": (C.c_int, [_VP, _VP, _VP, C.c_int]),
     "es_dg_set_background": (C.c_int, [_VP, _VP, C.c_int]),
@@ -235,9 +237,13 @@ class Solver:
         check(self.lib.es_dg_get_state(self.h, C.c_void_p(_ptr(out)), _on_device(out)), "es_dg_get_state")
         return out
 
-    def init_bubble(self, theta0=300.0, amp=0.5, centre=(500.0, 500.0, 350.0), radius=250.0):
+    def init_bubble(self, theta0=300.0, amp=0.5, centre=(500.0, 500.0, 350.0), radius=250.0,
+                    profile="smooth"):
+        """Rising-bubble state: "smooth" (Eq. smooth-rb-ic) or "sharp" (Eq. sharp-rb-ic)."""
         c = (C.c_double * 3)(*centre)
-        check(self.lib.es_dg_init_bubble(self.h, theta0, amp, c, radius), "es_dg_init_bubble")
+        k = {"smooth": 0, "sharp": 1}[profile]
+        check(self.lib.es_dg_init_bubble_profile(self.h, theta0, amp, c, radius, k),
+              "es_dg_init_bubble_profile")
 
     def init_channel(self):
         check(self.lib.es_dg_init_channel(self.h), "es_dg_init_channel")
@@ -302,7 +308,7 @@ class Server:
     @staticmethod
     def request(kind="bubble", K=(4, 4, 4), N=3, precision="fp64", nsteps=10, cfl=0.5, amp=0.5,
                 centre=(500.0, 500.0, 350.0), radius=250.0, theta0=300.0, warp=0.0):
-        return es_dg_request({"bubble": 0, "channel": 1}[kind], *K, N,
+        return es_dg_request({"bubble": 0, "channel": 1, "sharp_bubble": 2}[kind], *K, N,
                              {"fp64": ES_DG_FP64, "mixed": ES_DG_FP32_MIXED}[precision], nsteps,
                              cfl, amp, (C.c_double * 3)(*centre), radius, theta0, warp)
 

@@ -376,13 +376,21 @@ int es_dg_get_state(es_dg_t* h, double* q, int on_device) {
 
 int es_dg_init_bubble(es_dg_t* h, double theta0, double amp, const double centre[3],
                       double radius) {
+  return es_dg_init_bubble_profile(h, theta0, amp, centre, radius, ES_DG_BUBBLE_SMOOTH);
+}
+
+int es_dg_init_bubble_profile(es_dg_t* h, double theta0, double amp, const double centre[3],
+                              double radius, int profile) {
   if (!h || !centre || !(theta0 > 0.0) || !(radius > 0.0)) return ES_DG_EINVAL;
+  if (profile != ES_DG_BUBBLE_SMOOTH && profile != ES_DG_BUBBLE_SHARP) return ES_DG_EINVAL;
+  const int sharp = profile == ES_DG_BUBBLE_SHARP;
   cudaError_t e;
   if (h->mixed) {
     // the unperturbed isentropic atmosphere is the mixed path's background
     int st = ensure_rhs_buffers(h);
     if (st) return st;
-    e = esdg_launch_bubble(h->g, h->P, h->x, theta0, 0.0, centre, radius, h->q, h->stream);
+    e = esdg_launch_bubble(h->g, h->P, h->x, theta0, 0.0, centre, radius, sharp, h->q,
+                           h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaMemcpyAsync(h->rhs, h->q, (size_t)h->g.E * 5 * h->g.np * sizeof(double),
                         cudaMemcpyDeviceToDevice, h->stream);
@@ -390,7 +398,7 @@ int es_dg_init_bubble(es_dg_t* h, double theta0, double amp, const double centre
     st = set_background_dev(h, h->rhs);
     if (st) return st;
   }
-  e = esdg_launch_bubble(h->g, h->P, h->x, theta0, amp, centre, radius, h->q, h->stream);
+  e = esdg_launch_bubble(h->g, h->P, h->x, theta0, amp, centre, radius, sharp, h->q, h->stream);
   return cuda_status(e);
 }
 

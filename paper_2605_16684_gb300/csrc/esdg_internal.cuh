@@ -252,8 +252,8 @@ cudaError_t esdg_launch_geometry(const EsdgGrid& g, const EsdgLGL& L, double* x,
                                  double* Ja, double* vgeo, float* vgeo32, double* fgeo,
                                  const EsdgPhys& P, cudaStream_t s);
 cudaError_t esdg_launch_bubble(const EsdgGrid& g, const EsdgPhys& P, const double* x, double theta0,
-                               double amp, const double* centre, double radius, double* q,
-                               cudaStream_t s);
+                               double amp, const double* centre, double radius, int sharp,
+                               double* q, cudaStream_t s);
 cudaError_t esdg_launch_channel(const EsdgGrid& g, const EsdgPhys& P, const double* x, double* q,
                                 cudaStream_t s);
 cudaError_t esdg_launch_background(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,

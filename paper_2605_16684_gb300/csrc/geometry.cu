@@ -171,10 +171,11 @@ __global__ void k_face_geometry(EsdgGrid g, EsdgLGL L, EsdgPhys P, const double*
   o[4 * nf2 + fn] = P.g * x[((size_t)e * 3 + 2) * g.np + n];
 }
 
-// Section 5.1, Eq. (smooth-rb-ic) over an isentropic hydrostatic background:
+// Section 5.1 over an isentropic hydrostatic background: the cosine bubble of
+// Eq. (smooth-rb-ic) (sharp = 0) or the step of Eq. (sharp-rb-ic) (sharp = 1) in theta;
 // Exner = 1 - g z/(cp theta0), p = p0 Exner^(cp/R), T = theta Exner, rho = p/(R T).
 __global__ void k_bubble(EsdgGrid g, EsdgPhys P, const double* __restrict__ x, double theta0,
-                         double amp, double cx, double cy, double cz, double radius,
+                         double amp, double cx, double cy, double cz, double radius, int sharp,
                          double* __restrict__ q) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int np = g.np;
@@ -184,7 +185,7 @@ __global__ void k_bubble(EsdgGrid g, EsdgPhys P, const double* __restrict__ x, d
   const double X = x[(e * 3 + 0) * np + n], Y = x[(e * 3 + 1) * np + n], Z = x[(e * 3 + 2) * np + n];
   const double cp = P.gamma * P.R / (P.gamma - 1.0);
   const double r = sqrt((X - cx) * (X - cx) + (Y - cy) * (Y - cy) + (Z - cz) * (Z - cz));
-  const double dth = (r <= radius) ? amp * 0.5 * (1.0 + cospi(r / radius)) : 0.0;
+  const double dth = (r <= radius) ? (sharp ? amp : amp * 0.5 * (1.0 + cospi(r / radius))) : 0.0;
   const double ex = 1.0 - P.g * Z / (cp * theta0);
   const double p = P.p0 * pow(ex, cp / P.R);
   const double rho = p / (P.R * (theta0 + dth) * ex);
@@ -282,11 +283,11 @@ cudaError_t esdg_launch_geometry(const EsdgGrid& g, const EsdgLGL& L, double* x,
 }
 
 cudaError_t esdg_launch_bubble(const EsdgGrid& g, const EsdgPhys& P, const double* x, double theta0,
-                               double amp, const double* c, double radius, double* q,
+                               double amp, const double* c, double radius, int sharp, double* q,
                                cudaStream_t s) {
   const long long nt = (long long)g.E * g.np;
   k_bubble<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, P, x, theta0, amp, c[0], c[1], c[2],
-                                                         radius, q);
+                                                         radius, sharp, q);
   return cudaGetLastError();
 }
 

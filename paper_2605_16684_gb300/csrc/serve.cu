@@ -369,7 +369,8 @@ int admit_one(es_dg_server* s, Member& m) {
   mesh.ky = q.ky;
   mesh.kz = q.kz;
   es_dg_physics ph{1.4, 9.81, 287.0, 1.0e5, 0.0, 0.0, 0.0, 1};
-  if (q.kind == 0) {  // rising bubble in the 1000 m cube
+  const bool bubble = q.kind != 1;  // kinds 0 and 2: rising bubbles in the 1000 m cube
+  if (bubble) {
     for (int d = 0; d < 3; d++) {
       mesh.lo[d] = 0.0;
       mesh.hi[d] = 1000.0;
@@ -388,8 +389,8 @@ int admit_one(es_dg_server* s, Member& m) {
   // copy instead of the double-double metric computation)
   const es_dg_t* twin = nullptr;
   for (const auto& a : s->active)
-    if (a->h && a->req.kind == q.kind && a->req.kx == q.kx && a->req.ky == q.ky &&
-        a->req.kz == q.kz && a->req.N == q.N && (q.kind != 0 || a->req.warp == q.warp)) {
+    if (a->h && (a->req.kind != 1) == bubble && a->req.kx == q.kx && a->req.ky == q.ky &&
+        a->req.kz == q.kz && a->req.N == q.N && (!bubble || a->req.warp == q.warp)) {
       twin = a->h;
       break;
     }
@@ -398,10 +399,11 @@ int admit_one(es_dg_server* s, Member& m) {
     std::snprintf(s->msg, sizeof(s->msg), "es_dg_create: %s", es_dg_strerror(st));
     return st;
   }
-  if (q.kind == 0) {
+  if (bubble) {
     const double c[3] = {q.centre[0], q.centre[1], q.centre[2]};
-    st = es_dg_init_bubble(m.h, q.theta0 > 0 ? q.theta0 : 300.0, q.amp, c,
-                           q.radius > 0 ? q.radius : 250.0);
+    st = es_dg_init_bubble_profile(m.h, q.theta0 > 0 ? q.theta0 : 300.0, q.amp, c,
+                                   q.radius > 0 ? q.radius : 250.0,
+                                   q.kind == 2 ? ES_DG_BUBBLE_SHARP : ES_DG_BUBBLE_SMOOTH);
   } else {
     st = es_dg_init_channel(m.h);
   }
@@ -573,7 +575,7 @@ int es_dg_server_create(size_t hbm_budget_bytes, int max_slots, void* cuda_strea
 int es_dg_batch_submit(es_dg_server* s, const es_dg_request* req, uint64_t* ticket) {
   if (!s || !req || !ticket) return ES_DG_EINVAL;
   if (req->N < 1 || req->N > 7 || req->kx < 1 || req->ky < 1 || req->kz < 1 || req->nsteps < 0 ||
-      (req->kind != 0 && req->kind != 1) ||
+      req->kind < 0 || req->kind > 2 ||
       (req->precision != ES_DG_FP64 && req->precision != ES_DG_FP32_MIXED))
     return ES_DG_EINVAL;
   auto m = std::make_unique<Member>();

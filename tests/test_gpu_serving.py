@@ -22,9 +22,10 @@ def lib():
 def single_handle(lib, req):
     kind = req.get("kind", "bubble")
     K, N = req["K"], req["N"]
-    if kind == "bubble":
+    if kind in ("bubble", "sharp_bubble"):
         s = lib.Solver(*K, N, precision=req.get("precision", "fp64"), warp=req.get("warp", 0.0))
-        s.init_bubble(300.0, req.get("amp", 0.5), req.get("centre", (500.0, 500.0, 350.0)), 250.0)
+        s.init_bubble(300.0, req.get("amp", 0.5), req.get("centre", (500.0, 500.0, 350.0)), 250.0,
+                      profile="sharp" if kind == "sharp_bubble" else "smooth")
     else:
         s = lib.Solver(*K, N, lo=(0, 0, 0), hi=(40000e3, 6000e3, 30e3), periodic=(1, 0, 0),
                        precision=req.get("precision", "fp64"), f0=1e-4)
@@ -43,6 +44,7 @@ MIX = [
     dict(kind="channel", K=(6, 3, 2), N=3, precision="fp64", nsteps=2),
     dict(K=(5, 4, 3), N=4, precision="fp64", nsteps=6, centre=(450.0, 520.0, 300.0)),
     dict(K=(3, 2, 2), N=3, precision="mixed", nsteps=7),
+    dict(kind="sharp_bubble", K=(3, 3, 3), N=4, precision="mixed", nsteps=4),
 ]
 
 
