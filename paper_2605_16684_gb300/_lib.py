@@ -278,12 +278,17 @@ class Solver:
         check(self.lib.es_dg_integrals(self.h, out), "es_dg_integrals")
         return np.array(out[:])
 
-    def geometry(self):
-        x = np.empty((self.E, 3, self.np))
-        J = np.empty((self.E, self.np))
-        Ja = np.empty((self.E, 3, 3, self.np))
-        check(self.lib.es_dg_geometry(self.h, C.c_void_p(x.ctypes.data), C.c_void_p(J.ctypes.data),
-                                      C.c_void_p(Ja.ctypes.data), 0), "es_dg_geometry")
+    def geometry(self, device=False):
+        """Node positions x [E][3][np], J [E][np] and Ja [E][3][3][np]: numpy arrays, or
+        CUDA torch tensors with device=True."""
+        shapes = ((self.E, 3, self.np), (self.E, self.np), (self.E, 3, 3, self.np))
+        if device:
+            import torch
+            x, J, Ja = (torch.empty(sh, dtype=torch.float64, device="cuda") for sh in shapes)
+        else:
+            x, J, Ja = (np.empty(sh) for sh in shapes)
+        check(self.lib.es_dg_geometry(self.h, C.c_void_p(_ptr(x)), C.c_void_p(_ptr(J)),
+                                      C.c_void_p(_ptr(Ja)), int(device)), "es_dg_geometry")
         return x, J, Ja
 
     def launch(self, which: int, stage: int = 0, dt: float = 0.0):
