@@ -182,6 +182,59 @@ int es_dg_geometry(es_dg_t* h, double* x, double* J, double* Ja, int on_device);
  * with the fused RK update at stage `stage` (0..4) and step dt. */
 int es_dg_launch(es_dg_t* h, int which, int stage, double dt);
 
+/* ---- Domain decomposition (Section 4.3: elements split among processes, face
+ * traces exchanged every stage).  A mesh is cut into slabs of whole x element
+ * layers; each slab is a handle of its own whose cut x planes are "remote":
+ * their outside state is a trace, 5 x (N+1)^2 values per face of the plane,
+ * received from the neighbouring slab before every stage.  Node positions,
+ * metric terms, face geometry and arithmetic are those of the whole mesh, so
+ * partitioned stepping reproduces the whole-mesh result bit for bit.  Traces
+ * live in caller-owned device buffers, which lets the caller move them with
+ * device copies (es_dg_partitions_*: all slabs on one GPU and one stream) or
+ * with any transport between processes (pack, send / receive, then es_dg_launch
+ * for the stage).  A periodic x wraps from the last slab to the first. */
+
+/* Handle of x element layers [x_begin, x_end) of `mesh` (0 <= x_begin < x_end <=
+ * kx).  Its low plane is remote if x_begin > 0 or x is periodic, its high plane
+ * if x_end < kx or x is periodic (a slab holding every layer is a whole mesh).
+ * Other arguments as es_dg_create.  es_dg_step on a handle with a remote plane
+ * returns ES_DG_EINVAL; es_dg_rhs and es_dg_launch use the received traces as
+ * they stand and return ES_DG_EINVAL until es_dg_set_traces gave them. */
+int es_dg_create_partition(const es_dg_mesh* mesh, int N, es_dg_precision precision,
+                           const es_dg_physics* physics, int x_begin, int x_end,
+                           const es_dg_allocator* allocator, void* cuda_stream, es_dg_t** out);
+/* The slab's layer range, remote flags (low, high) and the length in doubles of
+ * one plane's trace: ky * kz * 5 * (N+1)^2, laid out [face a + ky b][variable][face
+ * node i_y + (N+1) i_z].  Any output pointer may be NULL. */
+int es_dg_partition_info(const es_dg_t* h, int* x_begin, int* x_end, int remote[2],
+                         long long* trace_len);
+/* Register the trace buffers (device, trace_len doubles each, 8-byte aligned,
+ * owned by the caller and alive while the handle uses them).  send_* are written
+ * by es_dg_pack_traces, recv_* are read by the interface kernel; the pair of a
+ * plane that is not remote may be NULL.  ES_DG_EINVAL if a remote plane lacks one. */
+int es_dg_set_traces(es_dg_t* h, double* send_lo, double* send_hi, double* recv_lo,
+                     double* recv_hi);
+/* Stream-ordered: ES_DG_TRACE_STATE writes the state of the slab's first layer
+ * at its low face nodes into send_lo and of its last layer at its high face nodes
+ * into send_hi (remote planes only).  ES_DG_TRACE_GEOMETRY writes the high plane's
+ * face geometry (normals, scalings, geopotential: the same length) into send_hi;
+ * the neighbour hands it to es_dg_accept_geometry_trace, once, before stepping. */
+enum { ES_DG_TRACE_STATE = 0, ES_DG_TRACE_GEOMETRY = 1 };
+int es_dg_pack_traces(es_dg_t* h, int what);
+/* Take recv_lo as the low plane's face geometry (the whole mesh evaluates a face
+ * from the element below it, here the neighbour's).  No-op without a remote low
+ * plane. */
+int es_dg_accept_geometry_trace(es_dg_t* h);
+/* All slabs of one mesh on one GPU: parts[0..P-1] in x order, created on one
+ * stream, traces set.  connect exchanges the face geometry (once, synchronous);
+ * exchange packs every state trace and copies each into its neighbour's receive
+ * buffer (device-to-device, stream-ordered); step advances all slabs by nsteps
+ * LSRK steps with an exchange before every stage.  ES_DG_EINVAL if the slabs do
+ * not cover the mesh in order or a trace buffer is missing. */
+int es_dg_partitions_connect(es_dg_t* const* parts, int P);
+int es_dg_partitions_exchange(es_dg_t* const* parts, int P);
+int es_dg_partitions_step(es_dg_t* const* parts, int P, double dt, int nsteps);
+
 const char* es_dg_strerror(int status);
 
 /* ---- batched ensembles and the continuous-batching server -------------------

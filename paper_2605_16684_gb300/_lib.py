@@ -93,6 +93,17 @@ SIGNATURES = {
     "es_dg_integrals": (C.c_int, [_VP, _DP]),
     "es_dg_geometry": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int]),
     "es_dg_launch": (C.c_int, [_VP, C.c_int, C.c_int, C.c_double]),
+    "es_dg_create_partition": (C.c_int, [C.POINTER(es_dg_mesh), C.c_int, C.c_int,
+                                         C.POINTER(es_dg_physics), C.c_int, C.c_int,
+                                         C.POINTER(es_dg_allocator), _VP, C.POINTER(_VP)]),
+    "es_dg_partition_info": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    "es_dg_set_traces": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "es_dg_pack_traces": (C.c_int, [_VP, C.c_int]),
+    "es_dg_accept_geometry_trace": (C.c_int, [_VP]),
+    "es_dg_partitions_connect": (C.c_int, [C.POINTER(_VP), C.c_int]),
+    "es_dg_partitions_exchange": (C.c_int, [C.POINTER(_VP), C.c_int]),
+    "es_dg_partitions_step": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_double, C.c_int]),
     "es_dg_strerror": (C.c_char_p, [C.c_int]),
     "es_dg_integrals_noalloc": (C.c_int, [C.POINTER(es_dg_mesh), C.c_int, C.POINTER(es_dg_physics),
                                           _VP, _VP, _VP, _VP, _VP]),
@@ -183,12 +194,15 @@ class Solver:
 
     def __init__(self, kx, ky, kz, N, lo=(0.0, 0.0, 0.0), hi=(1000.0, 1000.0, 1000.0),
                  periodic=(1, 1, 0), warp=0.0, precision="fp64", stream=None,
-                 torch_allocator=True, **phys):
+                 torch_allocator=True, part=None, **phys):
+        """part=(x_begin, x_end): the slab of x element layers [x_begin, x_end) of this
+        mesh (es_dg_create_partition); K and E are then the slab's."""
         import torch
         self.lib = load()
         self.N, self.Nq, self.np = N, N + 1, (N + 1) ** 3
-        self.K = (kx, ky, kz)
-        self.E = kx * ky * kz
+        self.part = tuple(part) if part is not None else None
+        self.K = (kx if part is None else part[1] - part[0], ky, kz)
+        self.E = self.K[0] * ky * kz
         self.precision = precision
         p = dict(gamma=1.4, g=9.81, R=287.0, p0=1.0e5, f0=0.0, beta=0.0, y0=0.0, dissipation=1)
         p.update(phys)
@@ -204,10 +218,38 @@ class Solver:
         self._alloc = _TorchAllocator(sp) if torch_allocator else None
         h = C.c_void_p()
         prec = {"fp64": ES_DG_FP64, "mixed": ES_DG_FP32_MIXED}[precision]
-        check(self.lib.es_dg_create(C.byref(self._mesh), N, prec, C.byref(self._phys),
-                                    C.byref(self._alloc.struct) if self._alloc else None,
-                                    C.c_void_p(sp), C.byref(h)), "es_dg_create")
+        alloc = C.byref(self._alloc.struct) if self._alloc else None
+        if part is None:
+            check(self.lib.es_dg_create(C.byref(self._mesh), N, prec, C.byref(self._phys), alloc,
+                                        C.c_void_p(sp), C.byref(h)), "es_dg_create")
+        else:
+            check(self.lib.es_dg_create_partition(C.byref(self._mesh), N, prec, C.byref(self._phys),
+                                                  int(part[0]), int(part[1]), alloc,
+                                                  C.c_void_p(sp), C.byref(h)),
+                  "es_dg_create_partition")
         self.h = h
+
+    def partition_info(self):
+        """(x_begin, x_end, (remote_lo, remote_hi), trace length in doubles)."""
+        b, e, n = C.c_int(), C.c_int(), C.c_longlong()
+        r = (C.c_int * 2)()
+        check(self.lib.es_dg_partition_info(self.h, C.byref(b), C.byref(e), r, C.byref(n)),
+              "es_dg_partition_info")
+        return b.value, e.value, (r[0], r[1]), n.value
+
+    def set_traces(self, send_lo, send_hi, recv_lo, recv_hi):
+        """Register caller-owned CUDA float64 tensors (None for a plane that is not remote);
+        keep them alive while the handle steps."""
+        ptr = lambda t: C.c_void_p(None if t is None else _ptr(t))
+        self._traces = (send_lo, send_hi, recv_lo, recv_hi)
+        check(self.lib.es_dg_set_traces(self.h, ptr(send_lo), ptr(send_hi), ptr(recv_lo),
+                                        ptr(recv_hi)), "es_dg_set_traces")
+
+    def pack_traces(self, geometry=False):
+        check(self.lib.es_dg_pack_traces(self.h, 1 if geometry else 0), "es_dg_pack_traces")
+
+    def accept_geometry_trace(self):
+        check(self.lib.es_dg_accept_geometry_trace(self.h), "es_dg_accept_geometry_trace")
 
     def close(self):
         if getattr(self, "h", None):
@@ -293,6 +335,88 @@ class Solver:
 
     def launch(self, which: int, stage: int = 0, dt: float = 0.0):
         check(self.lib.es_dg_launch(self.h, int(which), int(stage), float(dt)), "es_dg_launch")
+
+
+class PartitionedSolver:
+    """A mesh cut into P slabs of x element layers, each its own handle, all on one
+    GPU and one stream; traces move by device copies (es_dg_partitions_*).  The
+    state, RHS and time step are those of the whole mesh, bit for bit."""
+
+    def __init__(self, kx, ky, kz, N, P=2, bounds=None, precision="fp64", stream=None, **kw):
+        import torch
+        from .decomp import split_layers
+        self.lib = load()
+        self.N, self.np, self.K = N, (N + 1) ** 3, (kx, ky, kz)
+        self.E = kx * ky * kz
+        self.bounds = list(bounds) if bounds is not None else split_layers(kx, P)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.parts = [Solver(kx, ky, kz, N, precision=precision, stream=stream, part=b, **kw)
+                      for b in self.bounds]
+        self.traces = []
+        for s in self.parts:
+            _, _, remote, n = s.partition_info()
+            t = [torch.zeros(n, dtype=torch.float64, device="cuda") if remote[k % 2] else None
+                 for k in range(4)]  # send_lo, send_hi, recv_lo, recv_hi
+            s.set_traces(*t)
+            self.traces.append(t)
+        self._arr = (C.c_void_p * len(self.parts))(*[s.h.value for s in self.parts])
+        check(self.lib.es_dg_partitions_connect(self._arr, len(self.parts)),
+              "es_dg_partitions_connect")
+
+    def shape(self):
+        return (self.E, 5, self.np)
+
+    def _split(self, q):
+        kx, ky, kz = self.K
+        g = q.reshape(kz, ky, kx, 5, self.np)
+        return [np.ascontiguousarray(g[:, :, b:e]).reshape(-1, 5, self.np) for b, e in self.bounds]
+
+    def _join(self, parts):
+        kx, ky, kz = self.K
+        g = [p.reshape(kz, ky, e - b, 5, self.np) for p, (b, e) in zip(parts, self.bounds)]
+        return np.concatenate(g, axis=2).reshape(self.E, 5, self.np)
+
+    def set_state(self, q):
+        for s, qp in zip(self.parts, self._split(np.asarray(q, dtype=np.float64))):
+            s.set_state(qp)
+
+    def get_state(self):
+        return self._join([s.get_state() for s in self.parts])
+
+    def init_bubble(self, **kw):
+        for s in self.parts:
+            s.init_bubble(**kw)
+
+    def init_channel(self):
+        for s in self.parts:
+            s.init_channel()
+
+    def exchange(self):
+        check(self.lib.es_dg_partitions_exchange(self._arr, len(self.parts)),
+              "es_dg_partitions_exchange")
+
+    def rhs(self, q):
+        """Right-hand side of the whole-mesh state q (host arrays): slab states set,
+        traces exchanged, one RHS per slab."""
+        self.set_state(q)
+        self.exchange()
+        return self._join([s.rhs(qp) for s, qp in zip(self.parts, self._split(np.asarray(q)))])
+
+    def cfl_dt(self, C_=0.5):
+        return min(s.cfl_dt(C_) for s in self.parts)
+
+    def step(self, dt, nsteps=1):
+        check(self.lib.es_dg_partitions_step(self._arr, len(self.parts), float(dt), int(nsteps)),
+              "es_dg_partitions_step")
+
+    def sync(self):
+        for s in self.parts:
+            s.sync()
+
+    def close(self):
+        for s in self.parts:
+            s.close()
 
 
 class Server:

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/es_dg.h: handle management, buffers and launch
 // sequences.  All arithmetic happens in the kernels; this file only validates
 // arguments, owns device memory and orders launches on the handle's stream.
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <atomic>
@@ -46,6 +47,9 @@ struct es_dg {
   double* bg;       // [E][3][np] rho_bg, b_bg, p_bg
   double* rhs_bg;   // [E][3][np] FP64 momentum right-hand side of the background at rest
   double* fflux64;  // FP64 face fluxes for evaluating that right-hand side
+  // a partition's trace buffers (caller-owned device memory; [0] low x plane, [1] high)
+  double* tr_send[2];
+  double* tr_recv[2];
 };
 
 namespace {
@@ -75,19 +79,34 @@ int cuda_status(cudaError_t e) {
   return ES_DG_ECUDA;
 }
 
-int build_grid(const es_dg_mesh* m, int N, EsdgGrid* g) {
+// The grid of a whole mesh (x_end < 0) or of its partition of x element
+// layers [x_begin, x_end): the partition keeps the parent's box and element
+// counts for its node positions; a cut x plane becomes remote, and a periodic
+// x wraps through the traces (unless one partition holds the whole mesh).
+int build_grid(const es_dg_mesh* m, int N, EsdgGrid* g, int x_begin = 0, int x_end = -1) {
   if (!m || N < 1 || N > 7) return ES_DG_EINVAL;
-  const int K[3] = {m->kx, m->ky, m->kz};
-  long long E = 1;
-  for (int d = 0; d < 3; d++) {
+  int K[3] = {m->kx, m->ky, m->kz};
+  int per[3] = {m->periodic[0] ? 1 : 0, m->periodic[1] ? 1 : 0, m->periodic[2] ? 1 : 0};
+  for (int d = 0; d < 3; d++)
     if (K[d] < 1 || !(m->hi[d] > m->lo[d])) return ES_DG_EINVAL;
-    E *= K[d];
-  }
-  if (E > (1LL << 30) || !(m->warp >= 0.0 && m->warp < 0.15)) return ES_DG_EINVAL;
   std::memset(g, 0, sizeof(*g));
+  for (int d = 0; d < 3; d++) g->Kg[d] = K[d];
+  if (x_end >= 0) {
+    if (x_begin < 0 || x_end > K[0] || x_begin >= x_end) return ES_DG_EINVAL;
+    if (x_begin > 0 || x_end < K[0]) {
+      g->remote[0] = (x_begin > 0 || per[0]) ? 1 : 0;
+      g->remote[1] = (x_end < K[0] || per[0]) ? 1 : 0;
+      per[0] = 0;
+      g->eoff[0] = x_begin;
+      K[0] = x_end - x_begin;
+    }
+  }
+  long long E = 1;
+  for (int d = 0; d < 3; d++) E *= K[d];
+  if (E > (1LL << 30) || !(m->warp >= 0.0 && m->warp < 0.15)) return ES_DG_EINVAL;
   for (int d = 0; d < 3; d++) {
     g->K[d] = K[d];
-    g->periodic[d] = m->periodic[d] ? 1 : 0;
+    g->periodic[d] = per[d];
     g->lo[d] = m->lo[d];
     g->hi[d] = m->hi[d];
     g->nplanes[d] = g->periodic[d] ? K[d] : K[d] + 1;
@@ -134,11 +153,23 @@ EsdgVolArgs vol_args(es_dg_t* h, const double* q_in, double* rhs_out) {
   return a;
 }
 
+bool is_partition(const es_dg_t* h) { return h->g.remote[0] || h->g.remote[1]; }
+
+// every remote plane of a partition has its received trace
+bool traces_ready(const es_dg_t* h) {
+  for (int s = 0; s < 2; s++)
+    if (h->g.remote[s] && !h->tr_recv[s]) return false;
+  return true;
+}
+
+EsdgTraces traces_of(const es_dg_t* h) { return EsdgTraces{h->tr_recv[0], h->tr_recv[1]}; }
+
 // face fluxes then volume (+ lift, source, optional RK update) for state q_in
 int launch_stage(es_dg_t* h, const double* q_in, int mode, double* rhs_out, double A, double B,
                  double dt) {
+  if (!traces_ready(h)) return ES_DG_EINVAL;
   cudaError_t e = esdg_launch_face(h->g, h->P, h->mixed, q_in, h->fgeo, h->fflux, h->stream,
-                                   (h->mixed && h->has_bg) ? h->bg : nullptr);
+                                   (h->mixed && h->has_bg) ? h->bg : nullptr, traces_of(h));
   if (e != cudaSuccess) return cuda_status(e);
   EsdgVolArgs a = vol_args(h, q_in, rhs_out);
   a.rkA = A;
@@ -162,7 +193,11 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
   double* q0 = h->qtmp;
   if (q_dev == q0) return ES_DG_EINVAL;
   cudaError_t e = esdg_launch_background(h->g, h->P, h->vgeo, q_dev, h->bg, q0, h->stream);
-  if (e == cudaSuccess) e = esdg_launch_face(h->g, h->P, 0, q0, h->fgeo, h->fflux64, h->stream);
+  // a partition's cut planes take the inside background as the outside one (the
+  // background is a function of position, equal at coincident face nodes)
+  if (e == cudaSuccess)
+    e = esdg_launch_face(h->g, h->P, 0, q0, h->fgeo, h->fflux64, h->stream, nullptr,
+                         EsdgTraces{nullptr, nullptr});
   if (e == cudaSuccess) {
     EsdgVolArgs a = vol_args(h, q0, h->rhs);
     a.vgeo = h->vgeo;
@@ -186,6 +221,7 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
 int esdg_member_descriptor(es_dg_t* h, double dt, EsdgMember* out, EsdgLGL* L, int* mixed) {
   if (!h || !out) return ES_DG_EINVAL;
   if (h->mixed && !h->has_bg) return ES_DG_EINVAL;
+  if (is_partition(h)) return ES_DG_EINVAL;  // batched members are whole meshes
   std::memset(out, 0, sizeof(*out));
   out->g = h->g;
   out->P = h->P;
@@ -206,20 +242,20 @@ bool same_geometry(const es_dg_t* a, const EsdgGrid& g, double gravity) {
   if (!a || a->g.N != g.N || a->g.warp != g.warp || a->P.g != gravity) return false;
   for (int d = 0; d < 3; d++)
     if (a->g.K[d] != g.K[d] || a->g.periodic[d] != g.periodic[d] || a->g.lo[d] != g.lo[d] ||
-        a->g.hi[d] != g.hi[d])
+        a->g.hi[d] != g.hi[d] || a->g.eoff[d] != g.eoff[d] || a->g.Kg[d] != g.Kg[d])
       return false;
-  return true;
+  return a->g.remote[0] == g.remote[0] && a->g.remote[1] == g.remote[1];
 }
 
 int create_impl(const es_dg_mesh* mesh, int N, es_dg_precision precision,
                 const es_dg_physics* physics, const es_dg_allocator* allocator, void* cuda_stream,
-                const es_dg_t* geometry_of, es_dg_t** out) {
+                const es_dg_t* geometry_of, es_dg_t** out, int x_begin = 0, int x_end = -1) {
   if (!out) return ES_DG_EINVAL;
   *out = nullptr;
   if (precision != ES_DG_FP64 && precision != ES_DG_FP32_MIXED) return ES_DG_EINVAL;
   if (allocator && (!allocator->alloc || !allocator->free)) return ES_DG_EINVAL;
   EsdgGrid g;
-  int st = build_grid(mesh, N, &g);
+  int st = build_grid(mesh, N, &g, x_begin, x_end);
   if (st) return st;
   es_dg_t* h = new (std::nothrow) es_dg();
   if (!h) return ES_DG_ENOMEM;
@@ -470,6 +506,7 @@ int es_dg_cfl_dt(es_dg_t* h, double C, double* dt) {
 
 int es_dg_step(es_dg_t* h, double dt, int nsteps) {
   if (!h || nsteps < 0 || !(dt > 0.0)) return ES_DG_EINVAL;
+  if (is_partition(h)) return ES_DG_EINVAL;  // stages need the trace exchange
   for (int n = 0; n < nsteps; n++)
     for (int s = 0; s < 5; s++) {
       int st = launch_stage(h, h->q, 1, nullptr, kRkA[s], kRkB[s], dt);
@@ -512,9 +549,11 @@ int es_dg_geometry(es_dg_t* h, double* x, double* J, double* Ja, int on_device) 
 
 int es_dg_launch(es_dg_t* h, int which, int stage, double dt) {
   if (!h || stage < 0 || stage > 4) return ES_DG_EINVAL;
+  if (!traces_ready(h)) return ES_DG_EINVAL;
   if (which == 0)
     return cuda_status(esdg_launch_face(h->g, h->P, h->mixed, h->q, h->fgeo, h->fflux, h->stream,
-                                        (h->mixed && h->has_bg) ? h->bg : nullptr));
+                                        (h->mixed && h->has_bg) ? h->bg : nullptr,
+                                        traces_of(h)));
   if (which == 1) {
     int st = ensure_rhs_buffers(h);
     if (st) return st;
@@ -529,6 +568,160 @@ int es_dg_launch(es_dg_t* h, int which, int stage, double dt) {
     return cuda_status(esdg_launch_volume(h->g, h->L, h->P, h->mixed, 1, a, h->stream));
   }
   return ES_DG_EINVAL;
+}
+
+// ---- domain decomposition along x -----------------------------------------
+
+int es_dg_create_partition(const es_dg_mesh* mesh, int N, es_dg_precision precision,
+                           const es_dg_physics* physics, int x_begin, int x_end,
+                           const es_dg_allocator* allocator, void* cuda_stream, es_dg_t** out) {
+  if (x_end < 0) return ES_DG_EINVAL;
+  return create_impl(mesh, N, precision, physics, allocator, cuda_stream, nullptr, out, x_begin,
+                     x_end);
+}
+
+int es_dg_partition_info(const es_dg_t* h, int* x_begin, int* x_end, int remote[2],
+                         long long* trace_len) {
+  if (!h) return ES_DG_EINVAL;
+  if (x_begin) *x_begin = h->g.eoff[0];
+  if (x_end) *x_end = h->g.eoff[0] + h->g.K[0];
+  if (remote) {
+    remote[0] = h->g.remote[0];
+    remote[1] = h->g.remote[1];
+  }
+  if (trace_len) *trace_len = (long long)h->g.K[1] * h->g.K[2] * 5 * h->g.Nq * h->g.Nq;
+  return ES_DG_OK;
+}
+
+int es_dg_set_traces(es_dg_t* h, double* send_lo, double* send_hi, double* recv_lo,
+                     double* recv_hi) {
+  if (!h) return ES_DG_EINVAL;
+  if (h->g.remote[0] && (!send_lo || !recv_lo)) return ES_DG_EINVAL;
+  if (h->g.remote[1] && (!send_hi || !recv_hi)) return ES_DG_EINVAL;
+  for (const void* p : {(const void*)send_lo, (const void*)send_hi, (const void*)recv_lo,
+                        (const void*)recv_hi})
+    if (reinterpret_cast<uintptr_t>(p) % sizeof(double)) return ES_DG_EINVAL;
+  h->tr_send[0] = h->g.remote[0] ? send_lo : nullptr;
+  h->tr_send[1] = h->g.remote[1] ? send_hi : nullptr;
+  h->tr_recv[0] = h->g.remote[0] ? recv_lo : nullptr;
+  h->tr_recv[1] = h->g.remote[1] ? recv_hi : nullptr;
+  return ES_DG_OK;
+}
+
+int es_dg_pack_traces(es_dg_t* h, int what) {
+  if (!h) return ES_DG_EINVAL;
+  for (int s = 0; s < 2; s++)
+    if (h->g.remote[s] && !h->tr_send[s]) return ES_DG_EINVAL;
+  if (what == ES_DG_TRACE_STATE)
+    return cuda_status(esdg_launch_trace_pack(h->g, h->q, h->tr_send[0], h->tr_send[1], h->stream));
+  if (what == ES_DG_TRACE_GEOMETRY) {
+    // the high plane's face geometry (its "-" element is this partition's)
+    if (!h->g.remote[1]) return ES_DG_OK;
+    const size_t nf2 = (size_t)h->g.Nq * h->g.Nq, plane = (size_t)h->g.K[1] * h->g.K[2];
+    const double* src = h->fgeo + ((size_t)h->g.face_off[0] + (size_t)h->g.K[0] * plane) * 5 * nf2;
+    return cuda_status(cudaMemcpyAsync(h->tr_send[1], src, plane * 5 * nf2 * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return ES_DG_EINVAL;
+}
+
+int es_dg_accept_geometry_trace(es_dg_t* h) {
+  if (!h) return ES_DG_EINVAL;
+  if (!h->g.remote[0]) return ES_DG_OK;
+  if (!h->tr_recv[0]) return ES_DG_EINVAL;
+  const size_t nf2 = (size_t)h->g.Nq * h->g.Nq, plane = (size_t)h->g.K[1] * h->g.K[2];
+  double* dst = h->fgeo + (size_t)h->g.face_off[0] * 5 * nf2;  // plane 0 of direction x
+  return cuda_status(cudaMemcpyAsync(dst, h->tr_recv[0], plane * 5 * nf2 * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, h->stream));
+}
+
+namespace {
+
+// Partitions in x order on one stream with their traces set; returns the
+// neighbour across each remote plane through lo_of / hi_of.
+int check_partitions(es_dg_t* const* parts, int P, std::vector<int>& lo_of, std::vector<int>& hi_of) {
+  if (!parts || P < 1) return ES_DG_EINVAL;
+  lo_of.assign(P, -1);
+  hi_of.assign(P, -1);
+  for (int p = 0; p < P; p++) {
+    const es_dg_t* h = parts[p];
+    if (!h || h->stream != parts[0]->stream || h->mixed != parts[0]->mixed ||
+        h->g.N != parts[0]->g.N)
+      return ES_DG_EINVAL;
+    for (int d = 0; d < 3; d++)
+      if (h->g.Kg[d] != parts[0]->g.Kg[d]) return ES_DG_EINVAL;
+    for (int d = 1; d < 3; d++)
+      if (h->g.K[d] != parts[0]->g.K[d]) return ES_DG_EINVAL;
+    const int next = (p + 1 < P) ? p + 1 : 0;
+    const bool last = (p + 1 == P);
+    // contiguous cover of the parent's x layers, in order
+    if (!last && h->g.eoff[0] + h->g.K[0] != parts[next]->g.eoff[0]) return ES_DG_EINVAL;
+    if (p == 0 && h->g.eoff[0] != 0) return ES_DG_EINVAL;
+    if (last && h->g.eoff[0] + h->g.K[0] != h->g.Kg[0]) return ES_DG_EINVAL;
+    if (h->g.remote[1]) {
+      if (!parts[next]->g.remote[0] || (last && P < 2)) return ES_DG_EINVAL;
+      hi_of[p] = next;
+      lo_of[next] = p;
+    }
+    if (!traces_ready(h)) return ES_DG_EINVAL;
+    for (int s = 0; s < 2; s++)
+      if (h->g.remote[s] && !h->tr_send[s]) return ES_DG_EINVAL;
+  }
+  for (int p = 0; p < P; p++)
+    if (parts[p]->g.remote[0] && lo_of[p] < 0) return ES_DG_EINVAL;
+  return ES_DG_OK;
+}
+
+// copy every partition's outgoing trace into its neighbour's receive buffer
+int exchange_traces(es_dg_t* const* parts, int P, const std::vector<int>& hi_of, bool geometry_only) {
+  for (int p = 0; p < P; p++) {
+    const es_dg_t* h = parts[p];
+    const size_t bytes = (size_t)h->g.K[1] * h->g.K[2] * 5 * h->g.Nq * h->g.Nq * sizeof(double);
+    const int q = hi_of[p];
+    if (q < 0) continue;
+    // p's high plane is q's low plane
+    cudaError_t e = cudaMemcpyAsync(parts[q]->tr_recv[0], h->tr_send[1], bytes,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && !geometry_only)
+      e = cudaMemcpyAsync(h->tr_recv[1], parts[q]->tr_send[0], bytes, cudaMemcpyDeviceToDevice,
+                          h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return ES_DG_OK;
+}
+
+}  // namespace
+
+int es_dg_partitions_connect(es_dg_t* const* parts, int P) {
+  std::vector<int> lo_of, hi_of;
+  int st = check_partitions(parts, P, lo_of, hi_of);
+  for (int p = 0; p < P && !st; p++) st = es_dg_pack_traces(parts[p], ES_DG_TRACE_GEOMETRY);
+  if (!st) st = exchange_traces(parts, P, hi_of, true);
+  for (int p = 0; p < P && !st; p++) st = es_dg_accept_geometry_trace(parts[p]);
+  if (!st) st = cuda_status(cudaStreamSynchronize(parts[0]->stream));
+  return st;
+}
+
+int es_dg_partitions_exchange(es_dg_t* const* parts, int P) {
+  std::vector<int> lo_of, hi_of;
+  int st = check_partitions(parts, P, lo_of, hi_of);
+  for (int p = 0; p < P && !st; p++) st = es_dg_pack_traces(parts[p], ES_DG_TRACE_STATE);
+  if (!st) st = exchange_traces(parts, P, hi_of, false);
+  return st;
+}
+
+int es_dg_partitions_step(es_dg_t* const* parts, int P, double dt, int nsteps) {
+  if (nsteps < 0 || !(dt > 0.0)) return ES_DG_EINVAL;
+  std::vector<int> lo_of, hi_of;
+  int st = check_partitions(parts, P, lo_of, hi_of);
+  for (int n = 0; n < nsteps && !st; n++)
+    for (int s = 0; s < 5 && !st; s++) {
+      for (int p = 0; p < P && !st; p++) st = es_dg_pack_traces(parts[p], ES_DG_TRACE_STATE);
+      if (!st) st = exchange_traces(parts, P, hi_of, false);
+      for (int p = 0; p < P && !st; p++)
+        st = launch_stage(parts[p], parts[p]->q, 1, nullptr, kRkA[s], kRkB[s], dt);
+    }
+  return st;
 }
 
 const char* es_dg_strerror(int status) {

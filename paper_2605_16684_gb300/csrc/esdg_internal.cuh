@@ -42,12 +42,28 @@ inline void esdg_phys_derive(EsdgPhys* P) {
 struct EsdgGrid {  // structured box and derived face numbering
   int K[3];
   int periodic[3];
-  double lo[3], hi[3];
+  double lo[3], hi[3];  // the whole box (a partition keeps its parent's)
   double warp;
   int N, Nq, np, E;
   int nplanes[3];
   long long face_off[3];
   long long nfaces;
+  // A partition of a larger box: its elements are the parent's elements
+  // eoff + (0..K-1) of Kg per direction (node positions follow from the parent
+  // mesh), and remote[0] / remote[1] mark its low / high x plane as a cut whose
+  // outside state arrives as a trace from the neighbouring partition.  A whole
+  // mesh has eoff = 0, Kg = K, remote = 0.
+  int eoff[3], Kg[3];
+  int remote[2];
+};
+
+// Outside states of a partition's remote x planes, [face in plane][5][Nq^2] with
+// the plane's faces in face-id order.  A null pointer on a remote plane means
+// "the outside equals the inside" (the background's own right-hand side, whose
+// state is a function of position and so agrees at coincident face nodes).
+struct EsdgTraces {
+  const double* lo;
+  const double* hi;
 };
 
 // the two directions other than d, in increasing order
@@ -260,7 +276,12 @@ cudaError_t esdg_launch_background(const EsdgGrid& g, const EsdgPhys& P, const d
                                    const double* q, double* bg, double* q0, cudaStream_t s);
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
                              const double* fgeo, void* fflux, cudaStream_t s,
-                             const double* bg = nullptr);
+                             const double* bg = nullptr, EsdgTraces tr = EsdgTraces{nullptr, nullptr});
+// Pack a partition's own traces for its neighbours: the state of the first
+// element layer's i = 0 nodes into send_lo (if remote[0]) and of the last
+// layer's i = N nodes into send_hi (if remote[1]), layout of EsdgTraces.
+cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, double* send_lo,
+                                   double* send_hi, cudaStream_t s);
 // mode 0: write rhs; mode 1: fused LSRK stage (dq, q updated in place)
 struct EsdgVolArgs {
   const double* q_in;    // state read by the prologue and the source term

@@ -33,12 +33,13 @@ __global__ void k_geometry(EsdgGrid g, EsdgLGL L, EsdgPhys P, double* __restrict
   for (int it = threadIdx.x; it < 3 * Nq; it += blockDim.x) {
     const int d = it / Nq, i = it - d * Nq;
     const double Ld = g.hi[d] - g.lo[d];
-    // offset from lo: L (e + (1 + xi)/2) / K
+    // offset from lo: L (e + (1 + xi)/2) / K of the whole box
     const dd xi = dd{L.xi[i], L.xi_lo[i]};
     dd t = dd_add(dd_make(1.0), xi);
     t = dd{0.5 * t.hi, 0.5 * t.lo};
-    t = dd_add(dd_make((double)eidx[d]), t);
-    R1[it] = dd_div_d(dd_mul_d(t, Ld), (double)g.K[d]);
+    // the parent mesh's element index (a partition's elements are offset by eoff)
+    t = dd_add(dd_make((double)(eidx[d] + g.eoff[d])), t);
+    R1[it] = dd_div_d(dd_mul_d(t, Ld), (double)g.Kg[d]);
     if (g.warp != 0.0) S1[it] = dd_sinpi(dd_div_d(dd_mul_d(R1[it], 2.0), Ld));
   }
   __syncthreads();

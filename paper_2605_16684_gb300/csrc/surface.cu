@@ -281,43 +281,35 @@ template <typename R, int N, bool BG>
 __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
                                           const double* __restrict__ q,
                                           const double* __restrict__ fgeo, R* __restrict__ fflux,
-                                          const double* __restrict__ bg, long long tid) {
+                                          const double* __restrict__ bg, const double* tr_lo, const double* tr_hi,
+                                          long long tid) {
   constexpr int Nq = N + 1, NF2 = Nq * Nq, NP = Nq * Nq * Nq;
   if (tid >= g.nfaces * NF2) return;
   const long long f = tid / NF2;
   const int fn = (int)(tid - f * NF2);
   int d = 0;
   while (d < 2 && f >= g.face_off[d + 1]) d++;
-  int o1, o2;
-  esdg_others(d, o1, o2);
+  // direction d and the two others o1 < o2 (esdg_others) as strides: elements
+  // x 1, y K0, z K0 K1; nodes x 1, y Nq, z Nq^2
+  const int K0 = g.K[0], K1 = g.K[1], K2 = g.K[2];
+  const int Ko1 = (d == 0) ? K1 : K0, Ko2 = (d == 2) ? K1 : K2;
+  const int Kd = (d == 0) ? K0 : ((d == 1) ? K1 : K2);
+  const int per = (d == 0) ? g.periodic[0] : ((d == 1) ? g.periodic[1] : g.periodic[2]);
+  const int sd = (d == 0) ? 1 : ((d == 1) ? K0 : K0 * K1);
+  const int so1 = (d == 0) ? K0 : 1, so2 = (d == 2) ? K0 : K0 * K1;
+  const int nd = (d == 0) ? 1 : ((d == 1) ? Nq : NF2);
+  const int no1 = (d == 0) ? Nq : 1, no2 = (d == 2) ? Nq : NF2;
   long long r = f - g.face_off[d];
-  const int a = (int)(r % g.K[o1]);
-  r /= g.K[o1];
-  const int b = (int)(r % g.K[o2]);
-  const int Pl = (int)(r / g.K[o2]);
-  const int Kd = g.K[d];
-  // elements below and above the plane (-1 at a wall)
-  int em = -1, ep = -1;
-  {
-    int idx[3];
-    idx[o1] = a;
-    idx[o2] = b;
-    if (Pl > 0 || g.periodic[d]) {
-      idx[d] = (Pl - 1 + Kd) % Kd;
-      em = idx[0] + g.K[0] * (idx[1] + g.K[1] * idx[2]);
-    }
-    if (Pl < Kd) {
-      idx[d] = Pl;
-      ep = idx[0] + g.K[0] * (idx[1] + g.K[1] * idx[2]);
-    }
-  }
-  int ijk[3];
-  ijk[o1] = fn % Nq;
-  ijk[o2] = fn / Nq;
-  ijk[d] = N;
-  const int nm = esdg_node(Nq, ijk[0], ijk[1], ijk[2]);
-  ijk[d] = 0;
-  const int npn = esdg_node(Nq, ijk[0], ijk[1], ijk[2]);
+  const int a = (int)(r % Ko1);
+  r /= Ko1;
+  const int b = (int)(r % Ko2);
+  const int Pl = (int)(r / Ko2);
+  // elements below and above the plane (-1 at a wall or a partition's cut)
+  const int et = a * so1 + b * so2;
+  const int em = (Pl > 0 || per) ? et + ((Pl - 1 + Kd) % Kd) * sd : -1;
+  const int ep = (Pl < Kd) ? et + Pl * sd : -1;
+  const int nt = (fn % Nq) * no1 + (fn / Nq) * no2;
+  const int nm = nt + N * nd, npn = nt;
   const double* G = fgeo + (size_t)f * 5 * NF2;
   const double n0 = G[0 * NF2 + fn], n1 = G[1 * NF2 + fn], n2 = G[2 * NF2 + fn];
   const double scale = G[3 * NF2 + fn], phi = G[4 * NF2 + fn];
@@ -326,7 +318,18 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
     for (int v = 0; v < 5; v++) qm[v] = q[((size_t)em * 5 + v) * NP + nm];
   if (ep >= 0)
     for (int v = 0; v < 5; v++) qp[v] = q[((size_t)ep * 5 + v) * NP + npn];
-  if (em < 0 || ep < 0) {  // reflecting wall: mirror the existing side
+  // a partition's cut x plane: the outside state is the neighbour's trace
+  const bool cut = d == 0 && ((em < 0 && g.remote[0]) || (ep < 0 && g.remote[1]));
+  if (cut) {
+    const size_t toff = ((size_t)b * K1 + a) * 5 * NF2 + fn;  // d = 0: a along y, b along z
+    if (em < 0) {
+#pragma unroll
+      for (int v = 0; v < 5; v++) qm[v] = tr_lo ? tr_lo[toff + (size_t)v * NF2] : qp[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; v++) qp[v] = tr_hi ? tr_hi[toff + (size_t)v * NF2] : qm[v];
+    }
+  } else if (em < 0 || ep < 0) {  // reflecting wall: mirror the existing side
     const double* src = (em < 0) ? qp : qm;
     double* dst = (em < 0) ? qm : qp;
     const double Un = src[1] * n0 + src[2] * n1 + src[3] * n2;
@@ -409,8 +412,30 @@ template <typename R, int N, bool BG>
 __global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const double* __restrict__ q,
                                               const double* __restrict__ fgeo,
                                               R* __restrict__ fflux,
-                                              const double* __restrict__ bg) {
-  face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+                                              const double* __restrict__ bg, EsdgTraces tr) {
+  face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, tr.lo, tr.hi,
+                      (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// A partition's traces: one thread per (side, face of the plane, face node).
+__global__ void k_trace_pack(EsdgGrid g, const double* __restrict__ q, double* __restrict__ lo,
+                             double* __restrict__ hi) {
+  const int Nq = g.Nq, NF2 = Nq * Nq, np = g.np;
+  const long long per_side = (long long)g.K[1] * g.K[2] * NF2;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= 2 * per_side) return;
+  const int side = (int)(tid / per_side);
+  const long long r = tid - side * per_side;
+  double* out = side ? hi : lo;
+  if (!out) return;
+  const long long j = r / NF2;  // face of the plane: a + K[1] b
+  const int fn = (int)(r - j * NF2);
+  const int a = (int)(j % g.K[1]), b = (int)(j / g.K[1]);
+  const int ex = side ? g.K[0] - 1 : 0;
+  const long long e = ex + (long long)g.K[0] * (a + (long long)g.K[1] * b);
+  const int n = esdg_node(Nq, side ? g.N : 0, fn % Nq, fn / Nq);
+  for (int v = 0; v < 5; v++)
+    out[(j * 5 + v) * NF2 + fn] = q[((size_t)e * 5 + v) * np + n];
 }
 
 // Persistent batched face kernel: CTAs of 256 threads stride over a work table
@@ -431,25 +456,25 @@ __global__ void __launch_bounds__(256) k_face_batch(const EsdgMember* __restrict
     }
     __syncthreads();
     face_node<R, N, BG>(mb.g, mb.P, mb.a.q_in, mb.fgeo, (R*)mb.a.fflux, mb.bg,
-                        (long long)tile.y + threadIdx.x);
+                        nullptr, nullptr, (long long)tile.y + threadIdx.x);
     __syncthreads();
   }
 }
 
 template <typename R, bool BG>
 cudaError_t launch_face_t(const EsdgGrid& g, const EsdgPhys& P, const double* q, const double* fgeo,
-                          R* fflux, const double* bg, cudaStream_t s) {
+                          R* fflux, const double* bg, EsdgTraces tr, cudaStream_t s) {
   const long long nt = g.nfaces * g.Nq * g.Nq;
   if (nt == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((nt + 255) / 256);
   switch (g.N) {
-    case 1: k_face<R, 1, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
-    case 2: k_face<R, 2, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
-    case 3: k_face<R, 3, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
-    case 4: k_face<R, 4, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
-    case 5: k_face<R, 5, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
-    case 6: k_face<R, 6, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
-    case 7: k_face<R, 7, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg); break;
+    case 1: k_face<R, 1, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
+    case 2: k_face<R, 2, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
+    case 3: k_face<R, 3, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
+    case 4: k_face<R, 4, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
+    case 5: k_face<R, 5, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
+    case 6: k_face<R, 6, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
+    case 7: k_face<R, 7, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -474,8 +499,17 @@ cudaError_t esdg_launch_face_batch(int N, int mixed, int bg, const EsdgMember* m
 }
 
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
-                             const double* fgeo, void* fflux, cudaStream_t s, const double* bg) {
-  if (mixed && bg) return launch_face_t<float, true>(g, P, q, fgeo, (float*)fflux, bg, s);
-  if (mixed) return launch_face_t<float, false>(g, P, q, fgeo, (float*)fflux, nullptr, s);
-  return launch_face_t<double, false>(g, P, q, fgeo, (double*)fflux, nullptr, s);
+                             const double* fgeo, void* fflux, cudaStream_t s, const double* bg,
+                             EsdgTraces tr) {
+  if (mixed && bg) return launch_face_t<float, true>(g, P, q, fgeo, (float*)fflux, bg, tr, s);
+  if (mixed) return launch_face_t<float, false>(g, P, q, fgeo, (float*)fflux, nullptr, tr, s);
+  return launch_face_t<double, false>(g, P, q, fgeo, (double*)fflux, nullptr, tr, s);
+}
+
+cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, double* send_lo,
+                                   double* send_hi, cudaStream_t s) {
+  const long long nt = 2LL * g.K[1] * g.K[2] * g.Nq * g.Nq;
+  if ((!send_lo && !send_hi) || nt == 0) return cudaSuccess;
+  k_trace_pack<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, q, send_lo, send_hi);
+  return cudaGetLastError();
 }

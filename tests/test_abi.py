@@ -75,3 +75,22 @@ def test_server_rejects_bad_arguments_before_touching_cuda(lib):
     assert lib.es_dg_server_create(0, 4, None, C.byref(h)) == -1
     assert lib.es_dg_server_create(1 << 30, 0, None, C.byref(h)) == -1
     assert lib.es_dg_batch_submit(None, None, None) == -1
+
+
+@pytest.mark.parametrize("xb,xe", [(0, 0), (2, 1), (-1, 2), (0, 5), (3, 3)])
+def test_create_partition_rejects_bad_ranges_before_touching_cuda(lib, xb, xe):
+    m = _lib.es_dg_mesh(4, 2, 2, (C.c_double * 3)(0, 0, 0), (C.c_double * 3)(1, 1, 1),
+                        (C.c_int * 3)(1, 1, 0), 0.0)
+    h = C.c_void_p()
+    assert lib.es_dg_create_partition(C.byref(m), 3, 0, None, xb, xe, None, None, C.byref(h)) == -1
+    assert not h.value
+
+
+def test_partition_calls_reject_null_arguments(lib):
+    assert lib.es_dg_partition_info(None, None, None, None, None) == -1
+    assert lib.es_dg_set_traces(None, None, None, None, None) == -1
+    assert lib.es_dg_pack_traces(None, 0) == -1
+    assert lib.es_dg_accept_geometry_trace(None) == -1
+    assert lib.es_dg_partitions_connect(None, 2) == -1
+    assert lib.es_dg_partitions_exchange(None, 0) == -1
+    assert lib.es_dg_partitions_step(None, 2, 1.0, 1) == -1

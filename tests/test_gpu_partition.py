@@ -1,0 +1,105 @@
+"""Domain decomposition on one GPU: a mesh cut into slabs of x element layers,
+each slab its own handle, traces exchanged before every stage.
+
+The slabs' geometry, right-hand sides and LSRK steps equal the whole mesh's bit
+for bit (the same node positions, face geometry and per-face arithmetic; only
+the source of the outside state at a cut changes), in FP64 and in mixed
+precision, with periodic and walled x, ragged and single-layer slabs, a warped
+mesh, and the channel with its Coriolis term.  The whole mesh's own parity with
+the oracle is covered by the other GPU tests.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_16684_gb300 import inputs
+from paper_2605_16684_gb300._lib import EsDgError
+
+pytestmark = pytest.mark.gpu
+
+CUBE = dict(lo=(0.0, 0.0, 0.0), hi=(1000.0, 1000.0, 1000.0))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_16684_gb300 import _build, _lib
+    _build.build()
+    return _lib
+
+
+CASES = [
+    # K, N, bounds or P, periodic, warp
+    ((4, 3, 2), 3, 2, (1, 1, 0), 0.0),
+    ((5, 2, 3), 4, [(0, 1), (1, 3), (3, 5)], (1, 1, 0), 0.05),
+    ((5, 2, 3), 4, [(0, 2), (2, 5)], (0, 1, 0), 0.05),
+    ((3, 2, 2), 2, 3, (1, 0, 0), 0.0),
+    ((4, 2, 2), 7, 2, (1, 1, 0), 0.05),
+]
+
+
+def pair(lib, K, N, parts, periodic, warp, precision="fp64", **kw):
+    mesh = dict(CUBE, periodic=periodic, warp=warp)
+    mesh.update(kw.pop("mesh", {}))
+    whole = lib.Solver(*K, N, precision=precision, **mesh, **kw)
+    split = lib.PartitionedSolver(*K, N, P=parts if isinstance(parts, int) else 2,
+                                  bounds=None if isinstance(parts, int) else parts,
+                                  precision=precision, **mesh, **kw)
+    return whole, split, mesh
+
+
+@pytest.mark.parametrize("K,N,parts,periodic,warp", CASES)
+def test_slab_geometry_equals_whole(lib, K, N, parts, periodic, warp):
+    whole, split, _ = pair(lib, K, N, parts, periodic, warp)
+    xw, Jw, Jaw = whole.geometry()
+    g = lambda a: a.reshape(K[2], K[1], K[0], *a.shape[1:])
+    for s, (b, e) in zip(split.parts, split.bounds):
+        xs, Js, Jas = s.geometry()
+        for w, p in ((xw, xs), (Jw, Js), (Jaw, Jas)):
+            assert np.array_equal(g(w)[:, :, b:e].reshape(p.shape), p)
+
+
+@pytest.mark.parametrize("K,N,parts,periodic,warp", CASES)
+def test_slab_rhs_equals_whole(lib, K, N, parts, periodic, warp):
+    whole, split, mesh = pair(lib, K, N, parts, periodic, warp)
+    o = O.Oracle(*K, N, **mesh)
+    x, _, _ = o.geometry()
+    q = inputs.perturb_state(o.bubble(), x, mesh["lo"], mesh["hi"], seed=7)
+    assert np.array_equal(split.rhs(q), whole.rhs(q))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("K,N,parts,periodic,warp", CASES[:3])
+def test_slab_steps_equal_whole(lib, K, N, parts, periodic, warp, precision):
+    whole, split, _ = pair(lib, K, N, parts, periodic, warp, precision=precision)
+    whole.init_bubble(amp=0.8, profile="sharp")
+    split.init_bubble(amp=0.8, profile="sharp")
+    assert np.array_equal(split.get_state(), whole.get_state())
+    dt = whole.cfl_dt(0.5)
+    assert split.cfl_dt(0.5) == dt
+    whole.step(dt, 4)
+    split.step(dt, 4)
+    assert np.array_equal(split.get_state(), whole.get_state())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_slab_channel_with_coriolis(lib, precision):
+    kw = dict(mesh=dict(lo=(0.0, 0.0, 0.0), hi=(40000e3, 6000e3, 30e3)), f0=1e-4)
+    whole, split, _ = pair(lib, (6, 3, 2), 4, 3, (1, 0, 0), 0.0, precision=precision, **kw)
+    whole.init_channel()
+    split.init_channel()
+    dt = whole.cfl_dt(0.5)
+    whole.step(dt, 3)
+    split.step(dt, 3)
+    assert np.array_equal(split.get_state(), whole.get_state())
+
+
+def test_slab_calls_need_traces(lib):
+    m = dict(CUBE, periodic=(1, 1, 0))
+    s = lib.Solver(4, 2, 2, 3, part=(1, 3), **m)
+    b, e, remote, n = s.partition_info()
+    assert (b, e, remote, n) == (1, 3, (1, 1), 2 * 2 * 5 * 16)
+    with pytest.raises(EsDgError):
+        s.step(1e-3, 1)  # a slab steps only with its neighbours
+    with pytest.raises(EsDgError):
+        s.rhs(np.zeros(s.shape()))  # no traces registered yet
+    s.close()
