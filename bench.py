@@ -520,7 +520,7 @@ def lgl_weights(N):
     from numpy.polynomial import legendre as Lg
     cN = np.zeros(N + 1)
     cN[N] = 1.0
-    x = np.concatenate([[-1.0], np.sort(Lg.legroots(Lg.legder(cN))), [1.0]])
+    x = np.concatenate([[-1.0], np.sort(np.real(Lg.legroots(Lg.legder(cN)))), [1.0]])
     return 2.0 / (N * (N + 1) * Lg.legval(x, cN) ** 2)
 
 
@@ -609,6 +609,48 @@ def run_sharp(args):
     print(json.dumps(out))
 
 
+def run_slabs(args):
+    """The 32^3 N = 4 bubble cut into P slabs of x layers on one GPU (domain
+    decomposition: trace pack, device copies and the two launches per slab and stage)
+    against the whole mesh: DOF-updates/s per RK stage per P and precision, and a check
+    that the slabs' final state equals the whole mesh's bit for bit."""
+    import numpy as np
+    import torch
+    from paper_2605_16684_gb300 import _build, _lib
+    _build.build()
+    w = WORKLOAD
+    K = (args.K,) * 3 if args.K else w["K"]
+    res = {}
+    for prec in ("fp64", "mixed"):
+        ref = None
+        for P in (1, 2, 4, 8):
+            s = _lib.PartitionedSolver(*K, w["N"], P=P, precision=prec, lo=w["lo"], hi=w["hi"],
+                                       periodic=w["periodic"], warp=w["warp"])
+            s.init_bubble(theta0=w["theta0"], amp=w["amp"], centre=w["centre"],
+                          radius=w["radius"])
+            dt = s.cfl_dt(w["cfl"])
+            s.step(dt, args.warmup)
+            s.sync()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            s.step(dt, args.steps)
+            s.sync()
+            el = time.perf_counter() - t
+            q = s.get_state()
+            if ref is None:
+                ref = q
+            res.setdefault(prec, []).append(
+                {"slabs": P, "value": s.E * s.np * 5 * args.steps / el,
+                 "ms_per_step": 1e3 * el / args.steps, "equal_to_whole": bool(np.array_equal(q, ref))})
+            s.close()
+    out = {"metric": "domain decomposition on one GPU: DOF-updates/s per RK stage by slab count",
+           "unit": "DOF-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "config": {"workload": WORKLOAD_NAME + "_x_slabs", "slabs": "x element layers",
+                      "exchange": "pack kernel + one device copy per cut plane and stage"},
+           "fp64": res["fp64"], "mixed": res["mixed"]}
+    print(json.dumps(out))
+
+
 def run_serving(args):
     import threading
     import numpy as np
@@ -676,7 +718,7 @@ def main():
     ap.add_argument("--K", type=int, default=0, help="elements per direction (small profiling cases)")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--workload", default="bubble32",
-                    choices=["bubble32", "ensemble", "serving", "channel", "sharp"])
+                    choices=["bubble32", "ensemble", "serving", "channel", "sharp", "slabs"])
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--check", type=int, default=4, help="ensemble members compared with FP64")
     ap.add_argument("--requests", type=int, default=60)
@@ -696,6 +738,9 @@ def main():
         return
     if args.workload == "sharp":
         run_sharp(args)
+        return
+    if args.workload == "slabs":
+        run_slabs(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -204,8 +204,12 @@ int es_dg_create_partition(const es_dg_mesh* mesh, int N, es_dg_precision precis
                            const es_dg_physics* physics, int x_begin, int x_end,
                            const es_dg_allocator* allocator, void* cuda_stream, es_dg_t** out);
 /* The slab's layer range, remote flags (low, high) and the length in doubles of
- * one plane's trace: ky * kz * 5 * (N+1)^2, laid out [face a + ky b][variable][face
- * node i_y + (N+1) i_z].  Any output pointer may be NULL. */
+ * one plane's trace: ky * kz * nv * (N+1)^2, laid out [face a + ky b][slot][face
+ * node i_y + (N+1) i_z]; slots 0-4 the conserved state, and for FP32-mixed
+ * handles (nv = 7) slots 5-6 the background rho_bg and p_bg of the node, which a
+ * mixed slab needs for the faces of its cut planes (its background's own
+ * right-hand side is evaluated at the first stage after they arrived).  Any
+ * output pointer may be NULL. */
 int es_dg_partition_info(const es_dg_t* h, int* x_begin, int* x_end, int remote[2],
                          long long* trace_len);
 /* Register the trace buffers (device, trace_len doubles each, 8-byte aligned,

@@ -50,6 +50,9 @@ struct es_dg {
   // a partition's trace buffers (caller-owned device memory; [0] low x plane, [1] high)
   double* tr_send[2];
   double* tr_recv[2];
+  // a mixed partition evaluates its background's right-hand side at its first stage,
+  // once its neighbours' background values have arrived with the traces
+  int bg_pending;
 };
 
 namespace {
@@ -162,12 +165,27 @@ bool traces_ready(const es_dg_t* h) {
   return true;
 }
 
-EsdgTraces traces_of(const es_dg_t* h) { return EsdgTraces{h->tr_recv[0], h->tr_recv[1]}; }
+// doubles per face node in a trace: the state, and for mixed handles rho_bg and p_bg
+int trace_nv(const es_dg_t* h) { return h->mixed ? 7 : 5; }
+
+size_t trace_doubles(const es_dg_t* h) {
+  return (size_t)h->g.K[1] * h->g.K[2] * trace_nv(h) * h->g.Nq * h->g.Nq;
+}
+
+EsdgTraces traces_of(const es_dg_t* h) {
+  return EsdgTraces{h->tr_recv[0], h->tr_recv[1], trace_nv(h), 0};
+}
+
+int resolve_background(es_dg_t* h);
 
 // face fluxes then volume (+ lift, source, optional RK update) for state q_in
 int launch_stage(es_dg_t* h, const double* q_in, int mode, double* rhs_out, double A, double B,
                  double dt) {
   if (!traces_ready(h)) return ES_DG_EINVAL;
+  if (h->bg_pending) {
+    const int st = resolve_background(h);
+    if (st) return st;
+  }
   cudaError_t e = esdg_launch_face(h->g, h->P, h->mixed, q_in, h->fgeo, h->fflux, h->stream,
                                    (h->mixed && h->has_bg) ? h->bg : nullptr, traces_of(h));
   if (e != cudaSuccess) return cuda_status(e);
@@ -193,11 +211,15 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
   double* q0 = h->qtmp;
   if (q_dev == q0) return ES_DG_EINVAL;
   cudaError_t e = esdg_launch_background(h->g, h->P, h->vgeo, q_dev, h->bg, q0, h->stream);
-  // a partition's cut planes take the inside background as the outside one (the
-  // background is a function of position, equal at coincident face nodes)
-  if (e == cudaSuccess)
-    e = esdg_launch_face(h->g, h->P, 0, q0, h->fgeo, h->fflux64, h->stream, nullptr,
-                         EsdgTraces{nullptr, nullptr});
+  if (e != cudaSuccess) return cuda_status(e);
+  if (is_partition(h)) {
+    // the faces of the cut planes need the neighbours' background: evaluated at the
+    // first stage, after a trace exchange has brought it (resolve_background)
+    h->has_bg = 1;
+    h->bg_pending = 1;
+    return ES_DG_OK;
+  }
+  e = esdg_launch_face(h->g, h->P, 0, q0, h->fgeo, h->fflux64, h->stream);
   if (e == cudaSuccess) {
     EsdgVolArgs a = vol_args(h, q0, h->rhs);
     a.vgeo = h->vgeo;
@@ -211,6 +233,34 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
                           3 * np * sizeof(double), E, cudaMemcpyDeviceToDevice, h->stream);
   if (e != cudaSuccess) return cuda_status(e);
   h->has_bg = 1;
+  return ES_DG_OK;
+}
+
+// A mixed partition's background right-hand side, as the whole mesh evaluates it:
+// the at-rest state rebuilt from the stored background, the neighbours' at-rest
+// states at the cut planes from the received traces (slots 5-6).
+int resolve_background(es_dg_t* h) {
+  if (trace_nv(h) != 7) return ES_DG_EINVAL;  // only mixed handles carry a background
+  const size_t E = h->g.E, np = h->g.np;
+  double* q0 = h->qtmp;
+  cudaError_t e = esdg_launch_background_state(h->g, h->P, h->vgeo, h->bg, q0, h->stream);
+  if (e == cudaSuccess) {
+    EsdgTraces t = traces_of(h);
+    t.bgmode = 1;
+    e = esdg_launch_face(h->g, h->P, 0, q0, h->fgeo, h->fflux64, h->stream, nullptr, t);
+  }
+  if (e == cudaSuccess) {
+    EsdgVolArgs a = vol_args(h, q0, h->rhs);
+    a.vgeo = h->vgeo;
+    a.fflux = h->fflux64;
+    a.bg = nullptr;
+    e = esdg_launch_volume(h->g, h->L, h->P, 0, 0, a, h->stream);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(h->rhs_bg, 3 * np * sizeof(double), h->rhs + np, 5 * np * sizeof(double),
+                          3 * np * sizeof(double), E, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  h->bg_pending = 0;
   return ES_DG_OK;
 }
 
@@ -465,6 +515,7 @@ int es_dg_set_background(es_dg_t* h, const double* q_bg, int on_device) {
 int es_dg_clear_background(es_dg_t* h) {
   if (!h) return ES_DG_EINVAL;
   h->has_bg = 0;
+  h->bg_pending = 0;
   return ES_DG_OK;
 }
 
@@ -550,6 +601,10 @@ int es_dg_geometry(es_dg_t* h, double* x, double* J, double* Ja, int on_device) 
 int es_dg_launch(es_dg_t* h, int which, int stage, double dt) {
   if (!h || stage < 0 || stage > 4) return ES_DG_EINVAL;
   if (!traces_ready(h)) return ES_DG_EINVAL;
+  if (h->bg_pending) {
+    const int st = resolve_background(h);
+    if (st) return st;
+  }
   if (which == 0)
     return cuda_status(esdg_launch_face(h->g, h->P, h->mixed, h->q, h->fgeo, h->fflux, h->stream,
                                         (h->mixed && h->has_bg) ? h->bg : nullptr,
@@ -589,7 +644,7 @@ int es_dg_partition_info(const es_dg_t* h, int* x_begin, int* x_end, int remote[
     remote[0] = h->g.remote[0];
     remote[1] = h->g.remote[1];
   }
-  if (trace_len) *trace_len = (long long)h->g.K[1] * h->g.K[2] * 5 * h->g.Nq * h->g.Nq;
+  if (trace_len) *trace_len = (long long)trace_doubles(h);
   return ES_DG_OK;
 }
 
@@ -613,7 +668,9 @@ int es_dg_pack_traces(es_dg_t* h, int what) {
   for (int s = 0; s < 2; s++)
     if (h->g.remote[s] && !h->tr_send[s]) return ES_DG_EINVAL;
   if (what == ES_DG_TRACE_STATE)
-    return cuda_status(esdg_launch_trace_pack(h->g, h->q, h->tr_send[0], h->tr_send[1], h->stream));
+    return cuda_status(esdg_launch_trace_pack(h->g, h->q, (h->mixed && h->has_bg) ? h->bg : nullptr,
+                                              trace_nv(h), h->tr_send[0], h->tr_send[1],
+                                              h->stream));
   if (what == ES_DG_TRACE_GEOMETRY) {
     // the high plane's face geometry (its "-" element is this partition's)
     if (!h->g.remote[1]) return ES_DG_OK;
@@ -676,7 +733,7 @@ int check_partitions(es_dg_t* const* parts, int P, std::vector<int>& lo_of, std:
 int exchange_traces(es_dg_t* const* parts, int P, const std::vector<int>& hi_of, bool geometry_only) {
   for (int p = 0; p < P; p++) {
     const es_dg_t* h = parts[p];
-    const size_t bytes = (size_t)h->g.K[1] * h->g.K[2] * 5 * h->g.Nq * h->g.Nq * sizeof(double);
+    const size_t bytes = trace_doubles(h) * sizeof(double);
     const int q = hi_of[p];
     if (q < 0) continue;
     // p's high plane is q's low plane

@@ -57,13 +57,17 @@ struct EsdgGrid {  // structured box and derived face numbering
   int remote[2];
 };
 
-// Outside states of a partition's remote x planes, [face in plane][5][Nq^2] with
-// the plane's faces in face-id order.  A null pointer on a remote plane means
-// "the outside equals the inside" (the background's own right-hand side, whose
-// state is a function of position and so agrees at coincident face nodes).
+// Outside states of a partition's remote x planes, [face in plane][nv][Nq^2]
+// with the plane's faces in face-id order: slots 0-4 the conserved state, and
+// for mixed-precision handles slots 5-6 the background rho_bg and p_bg of the
+// same node (nv = 7).  bgmode = 1 makes the outside state the background at
+// rest (rho_bg, 0, 0, 0, p_bg/(gamma-1) + rho_bg phi), for the background's own
+// right-hand side.  Null pointers: no remote plane is read.
 struct EsdgTraces {
   const double* lo;
   const double* hi;
+  int nv;
+  int bgmode;
 };
 
 // the two directions other than d, in increasing order
@@ -276,12 +280,18 @@ cudaError_t esdg_launch_background(const EsdgGrid& g, const EsdgPhys& P, const d
                                    const double* q, double* bg, double* q0, cudaStream_t s);
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
                              const double* fgeo, void* fflux, cudaStream_t s,
-                             const double* bg = nullptr, EsdgTraces tr = EsdgTraces{nullptr, nullptr});
+                             const double* bg = nullptr,
+                             EsdgTraces tr = EsdgTraces{nullptr, nullptr, 5, 0});
 // Pack a partition's own traces for its neighbours: the state of the first
 // element layer's i = 0 nodes into send_lo (if remote[0]) and of the last
 // layer's i = N nodes into send_hi (if remote[1]), layout of EsdgTraces.
-cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, double* send_lo,
-                                   double* send_hi, cudaStream_t s);
+cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, const double* bg, int nv,
+                                   double* send_lo, double* send_hi, cudaStream_t s);
+// The background state at rest from the stored background, per node:
+// (rho_bg, 0, 0, 0, p_bg/(gamma-1) + rho_bg phi) -- the expression the
+// background kernel uses, so the result equals its own at-rest state.
+cudaError_t esdg_launch_background_state(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
+                                         const double* bg, double* q0, cudaStream_t s);
 // mode 0: write rhs; mode 1: fused LSRK stage (dq, q updated in place)
 struct EsdgVolArgs {
   const double* q_in;    // state read by the prologue and the source term

@@ -250,10 +250,34 @@ __global__ void k_background(EsdgGrid g, EsdgPhys P, const double* __restrict__ 
   o[np + n] = 0.0;
   o[2 * np + n] = 0.0;
   o[3 * np + n] = 0.0;
-  o[4 * np + n] = p / (P.gamma - 1.0) + rho * phi;
+  o[4 * np + n] = fma(rho, phi, p / (P.gamma - 1.0));
+}
+
+__global__ void k_background_state(EsdgGrid g, EsdgPhys P, const double* __restrict__ vgeo,
+                                   const double* __restrict__ bg, double* __restrict__ q0) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int np = g.np;
+  if (tid >= (long long)g.E * np) return;
+  const long long e = tid / np;
+  const int n = (int)(tid - e * np);
+  const double phi = vgeo[(e * ESDG_NVGEO + 10) * np + n];
+  const double rho = bg[(e * 3 + 0) * np + n], p = bg[(e * 3 + 2) * np + n];
+  double* o = q0 + e * 5 * np;
+  o[n] = rho;
+  o[np + n] = 0.0;
+  o[2 * np + n] = 0.0;
+  o[3 * np + n] = 0.0;
+  o[4 * np + n] = fma(rho, phi, p / (P.gamma - 1.0));
 }
 
 }  // namespace
+
+cudaError_t esdg_launch_background_state(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
+                                         const double* bg, double* q0, cudaStream_t s) {
+  const long long nt = (long long)g.E * g.np;
+  k_background_state<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, P, vgeo, bg, q0);
+  return cudaGetLastError();
+}
 
 cudaError_t esdg_launch_background(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
                                    const double* q, double* bg, double* q0, cudaStream_t s) {

@@ -281,7 +281,8 @@ template <typename R, int N, bool BG>
 __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
                                           const double* __restrict__ q,
                                           const double* __restrict__ fgeo, R* __restrict__ fflux,
-                                          const double* __restrict__ bg, const double* tr_lo, const double* tr_hi,
+                                          const double* __restrict__ bg, const double* tr_lo,
+                                          const double* tr_hi, int tr_nv, int tr_bg,
                                           long long tid) {
   constexpr int Nq = N + 1, NF2 = Nq * Nq, NP = Nq * Nq * Nq;
   if (tid >= g.nfaces * NF2) return;
@@ -320,14 +321,35 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
     for (int v = 0; v < 5; v++) qp[v] = q[((size_t)ep * 5 + v) * NP + npn];
   // a partition's cut x plane: the outside state is the neighbour's trace
   const bool cut = d == 0 && ((em < 0 && g.remote[0]) || (ep < 0 && g.remote[1]));
+  // mixed path: the background pressure of the element below the face (at a
+  // partition's low cut the neighbour's, carried in its trace)
+  double pbg = 0.0;
+  const size_t toff = ((size_t)b * K1 + a) * tr_nv * NF2 + fn;  // d = 0: a along y, b along z
+  if constexpr (BG) {
+    if (cut && em < 0 && tr_lo && tr_nv == 7) pbg = tr_lo[toff + 6 * (size_t)NF2];
+    else pbg = (em >= 0) ? bg[((size_t)em * 3 + 2) * NP + nm] : bg[((size_t)ep * 3 + 2) * NP + npn];
+  }
   if (cut) {
-    const size_t toff = ((size_t)b * K1 + a) * 5 * NF2 + fn;  // d = 0: a along y, b along z
-    if (em < 0) {
+    const double* t = (em < 0) ? tr_lo : tr_hi;
+    double o[5];
+    if (!t) {  // no trace given: the inside state
 #pragma unroll
-      for (int v = 0; v < 5; v++) qm[v] = tr_lo ? tr_lo[toff + (size_t)v * NF2] : qp[v];
+      for (int v = 0; v < 5; v++) o[v] = (em < 0) ? qp[v] : qm[v];
+    } else if (tr_bg) {  // the neighbour's background at rest (as esdg_launch_background)
+      const double rb = t[toff + 5 * (size_t)NF2], pb = t[toff + 6 * (size_t)NF2];
+      o[0] = rb;
+      o[1] = o[2] = o[3] = 0.0;
+      o[4] = fma(rb, phi, pb / (P.gamma - 1.0));
     } else {
 #pragma unroll
-      for (int v = 0; v < 5; v++) qp[v] = tr_hi ? tr_hi[toff + (size_t)v * NF2] : qm[v];
+      for (int v = 0; v < 5; v++) o[v] = t[toff + (size_t)v * NF2];
+    }
+    if (em < 0) {
+#pragma unroll
+      for (int v = 0; v < 5; v++) qm[v] = o[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; v++) qp[v] = o[v];
     }
   } else if (em < 0 || ep < 0) {  // reflecting wall: mirror the existing side
     const double* src = (em < 0) ? qp : qm;
@@ -351,8 +373,6 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
     //   [[x y]] = [[x]] {{y}} + {{x}} [[y]]  (for b u and (b u) . u),
     //   p* - p_bg = {{p}} - p_bg + [[p]] (rho+ p- - rho- p+)/(2 D),
     //   D = rho+ p- + rho- p+ = 2 {{rho}} {{p}} - [[rho]] [[p]]/2.
-    const int eb = (em >= 0) ? em : ep, nb = (em >= 0) ? nm : npn;
-    const double pbg = bg[((size_t)eb * 3 + 2) * NP + nb];
     float mf[5], pf5[5];
 #pragma unroll
     for (int v = 0; v < 4; v++) {
@@ -413,12 +433,14 @@ __global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const doub
                                               const double* __restrict__ fgeo,
                                               R* __restrict__ fflux,
                                               const double* __restrict__ bg, EsdgTraces tr) {
-  face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, tr.lo, tr.hi,
+  face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, tr.lo, tr.hi, tr.nv, tr.bgmode,
                       (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// A partition's traces: one thread per (side, face of the plane, face node).
-__global__ void k_trace_pack(EsdgGrid g, const double* __restrict__ q, double* __restrict__ lo,
+// A partition's traces: one thread per (side, face of the plane, face node);
+// with a background (nv = 7) also its rho_bg and p_bg.
+__global__ void k_trace_pack(EsdgGrid g, const double* __restrict__ q,
+                             const double* __restrict__ bg, int nv, double* __restrict__ lo,
                              double* __restrict__ hi) {
   const int Nq = g.Nq, NF2 = Nq * Nq, np = g.np;
   const long long per_side = (long long)g.K[1] * g.K[2] * NF2;
@@ -435,7 +457,11 @@ __global__ void k_trace_pack(EsdgGrid g, const double* __restrict__ q, double* _
   const long long e = ex + (long long)g.K[0] * (a + (long long)g.K[1] * b);
   const int n = esdg_node(Nq, side ? g.N : 0, fn % Nq, fn / Nq);
   for (int v = 0; v < 5; v++)
-    out[(j * 5 + v) * NF2 + fn] = q[((size_t)e * 5 + v) * np + n];
+    out[(j * nv + v) * NF2 + fn] = q[((size_t)e * 5 + v) * np + n];
+  if (bg && nv == 7) {
+    out[(j * nv + 5) * NF2 + fn] = bg[((size_t)e * 3 + 0) * np + n];
+    out[(j * nv + 6) * NF2 + fn] = bg[((size_t)e * 3 + 2) * np + n];
+  }
 }
 
 // Persistent batched face kernel: CTAs of 256 threads stride over a work table
@@ -456,7 +482,7 @@ __global__ void __launch_bounds__(256) k_face_batch(const EsdgMember* __restrict
     }
     __syncthreads();
     face_node<R, N, BG>(mb.g, mb.P, mb.a.q_in, mb.fgeo, (R*)mb.a.fflux, mb.bg,
-                        nullptr, nullptr, (long long)tile.y + threadIdx.x);
+                        nullptr, nullptr, 5, 0, (long long)tile.y + threadIdx.x);
     __syncthreads();
   }
 }
@@ -506,10 +532,11 @@ cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, co
   return launch_face_t<double, false>(g, P, q, fgeo, (double*)fflux, nullptr, tr, s);
 }
 
-cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, double* send_lo,
-                                   double* send_hi, cudaStream_t s) {
+cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, const double* bg, int nv,
+                                   double* send_lo, double* send_hi, cudaStream_t s) {
   const long long nt = 2LL * g.K[1] * g.K[2] * g.Nq * g.Nq;
   if ((!send_lo && !send_hi) || nt == 0) return cudaSuccess;
-  k_trace_pack<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, q, send_lo, send_hi);
+  if (nv != 5 && nv != 7) return cudaErrorInvalidValue;
+  k_trace_pack<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, q, bg, nv, send_lo, send_hi);
   return cudaGetLastError();
 }
