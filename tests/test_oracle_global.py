@@ -12,7 +12,9 @@ Fixed outside the oracle by the mathematics of the method:
   hydrostatic isentropic background; the channel state is in geostrophic balance;
 * on the discontinuous sharp bubble the EC scheme still conserves entropy and the
   ES scheme dissipates it while conserving mass and energy;
-* the double build sits within the long-double build's floor.
+* the double build sits within the long-double build's floor;
+* the Coriolis source turns a uniform flow on an f-plane at the rate f (inertial
+  oscillation), and LSRK(5,4) converges to that closed form at fourth order.
 """
 import numpy as np
 import pytest
@@ -353,3 +355,49 @@ def test_sharp_bubble_steps_dissipate_entropy():
     assert np.allclose(dS[1:], trap, rtol=0.05, atol=0)
     assert np.abs(I[:, 0] / I[0, 0] - 1).max() < 5e-14
     assert np.abs(I[:, 1] / I[0, 1] - 1).max() < 5e-14
+
+
+def test_inertial_oscillation_closed_form():
+    # Uniform flow on an f-plane with g = 0 on a periodic box: the fluxes of a constant
+    # state cancel, so the only right-hand side is the Coriolis source -f zhat x (rho U)
+    # (Eq. (Eq:euler)) and the horizontal velocity turns clockwise at the rate f:
+    #   u(t) = u0 cos(f t) + v0 sin(f t),  v(t) = -u0 sin(f t) + v0 cos(f t).
+    f = 1e-4
+    # elements of h = 5e7 m, so that steps of up to 0.1 / f lie far inside the acoustic CFL limit
+    h = 5e7
+    o = O.Oracle(2, 1, 1, 2, lo=(0, 0, 0), hi=(2 * h, h, h), periodic=(1, 1, 1), warp=0.0,
+                 g=0.0, f0=f)
+    rho, u0, v0, w0, p = 1.1, 7.0, -3.0, 0.5, 9e4
+    q = np.zeros(o.shape())
+    q[:, 0], q[:, 1], q[:, 2], q[:, 3] = rho, rho * u0, rho * v0, rho * w0
+    q[:, 4] = p / (GAMMA - 1) + 0.5 * rho * (u0 ** 2 + v0 ** 2 + w0 ** 2)
+    r = o.rhs(q)
+    # the cancelling flux terms are of size flux / h: a 1e-13 relative floor
+    speed = np.sqrt(u0 ** 2 + v0 ** 2 + w0 ** 2)
+    flux = [rho * speed, p + rho * speed ** 2, p + rho * speed ** 2, p + rho * speed ** 2,
+            (q[0, 4, 0] + p) * speed]
+    tol = [1e-13 * fl / h for fl in flux]
+    assert np.abs(r[:, 1] - f * rho * v0).max() < tol[1]
+    assert np.abs(r[:, 2] + f * rho * u0).max() < tol[2]
+    for v in (0, 3, 4):
+        assert np.abs(r[:, v]).max() < tol[v]
+    # LSRK(5,4) on the rotation: fourth-order convergence to the closed form at t = 1.6
+    # inertial periods (a wrong sign in either Coriolis component turns the flow the
+    # other way and leaves an O(1) error)
+    t = 10.0 / f
+    errs = []
+    for n in (100, 200, 400):
+        dt = t / n
+        assert dt < 0.1 * o.cfl_dt(q, 0.5)
+        qn = o.steps(q, dt, n)
+        u_ex = u0 * np.cos(f * t) + v0 * np.sin(f * t)
+        v_ex = -u0 * np.sin(f * t) + v0 * np.cos(f * t)
+        errs.append(max(np.abs(qn[:, 1] / qn[:, 0] - u_ex).max(),
+                        np.abs(qn[:, 2] / qn[:, 0] - v_ex).max()))
+    assert errs[0] < 1e-4 * speed
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 3.8) and np.all(rates < 4.3), (errs, rates)
+    # the source does no work: density, vertical momentum and total energy stay put
+    assert np.abs(qn[:, 0] - rho).max() < 1e-13
+    assert np.abs(qn[:, 3] - rho * w0).max() < 1e-13
+    assert np.abs(qn[:, 4] - q[:, 4]).max() < 1e-13 * q[0, 4, 0]
