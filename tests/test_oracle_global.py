@@ -401,3 +401,21 @@ def test_inertial_oscillation_closed_form():
     assert np.abs(qn[:, 0] - rho).max() < 1e-13
     assert np.abs(qn[:, 3] - rho * w0).max() < 1e-13
     assert np.abs(qn[:, 4] - q[:, 4]).max() < 1e-13 * q[0, 4, 0]
+
+
+def test_beta_plane_source_is_linear_in_y():
+    # f = f0 + beta (y - y0): on a uniform flow the source-only right-hand side follows
+    # the node's y coordinate (a beta-plane channel as in Section 5.2's benchmark family)
+    f0, beta, y0, h = 1e-4, 1.6e-11, 3e6, 5e7
+    o = O.Oracle(1, 2, 1, 3, lo=(0, 0, 0), hi=(h, 2 * h, h), periodic=(1, 1, 1), warp=0.0,
+                 g=0.0, f0=f0, beta=beta, y0=y0)
+    x, _, _ = o.geometry()
+    rho, u0, v0, p = 1.0, 5.0, 2.0, 1e5
+    q = np.zeros(o.shape())
+    q[:, 0], q[:, 1], q[:, 2] = rho, rho * u0, rho * v0
+    q[:, 4] = p / (GAMMA - 1) + 0.5 * rho * (u0 ** 2 + v0 ** 2)
+    r = o.rhs(q)
+    f = f0 + beta * (x[:, 1] - y0)
+    assert np.abs(f).max() > 10 * f0  # the beta term dominates somewhere
+    assert np.abs(r[:, 1] - f * rho * v0).max() < 1e-12 * np.abs(f * rho * v0).max()
+    assert np.abs(r[:, 2] + f * rho * u0).max() < 1e-12 * np.abs(f * rho * u0).max()
