@@ -30,6 +30,16 @@
  *
  * Readings where the paper points elsewhere (its Eq. 76 and Eq. A.1 citations,
  * the RK coefficients, the bubble background) are stated next to the code.
+ *
+ * Parity unpinned: two choices have no value in the paper to pin them to.
+ *   - The averaged state of the matrix dissipation (rho_hat = <rho>_log,
+ *     u = {{u}}, p_hat = {{rho}}/(2{{b}})).  What is pinned is that the
+ *     resulting D is symmetric positive semi-definite, that R, Lambda and T
+ *     match the flux Jacobian at equal states, and the exact entropy-dissipation
+ *     identity; which average the paper's Eq. A.1 citation uses is not.
+ *   - The switch point u < 1e-4 between the log-mean series and the logarithms.
+ *     Both branches are pinned against 50-digit arithmetic; the threshold
+ *     itself is a choice that changes results only at the rounding level.
  */
 #include <tgmath.h>
 #include <stdlib.h>
