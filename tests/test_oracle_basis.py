@@ -4,6 +4,8 @@ Each check compares the oracle with something fixed outside it: closed-form LGL
 nodes and weights, exactness of D and of the quadrature on polynomials, the SBP
 property, and the Runge-Kutta order conditions.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -58,44 +60,57 @@ def test_lgl_long_double_agrees():
 
 def _butcher_from_2n(A, B):
     """Butcher tableau of the 2N-storage scheme dq_s = A_s dq_{s-1} + dt f(Y_s),
-    q_s = q_{s-1} + B_s dq_s, Y_{s+1} = q_s."""
+    q_s = q_{s-1} + B_s dq_s, Y_{s+1} = q_s, in exact rational arithmetic."""
     s = len(A)
-    a = np.zeros((s, s))
-    b = np.zeros(s)
+    a = [[Fraction(0)] * s for _ in range(s)]
+    b = [Fraction(0)] * s
 
     def coef(j, r):  # coefficient of k_j in dq_r
-        c = 1.0
+        c = Fraction(1)
         for m in range(j + 1, r + 1):
             c *= A[m]
         return c
 
     for i in range(1, s):          # stage i uses q_{i-1}
         for j in range(i):
-            a[i, j] = sum(B[r] * coef(j, r) for r in range(j, i))
+            a[i][j] = sum(B[r] * coef(j, r) for r in range(j, i))
     for j in range(s):
         b[j] = sum(B[r] * coef(j, r) for r in range(j, s))
     return a, b
 
 
 def test_lsrk_order_conditions():
-    A, B, c = O.lsrk_coeffs()
+    # The oracle's coefficients (doubles) are converted exactly to rationals and the
+    # eight conditions of order <= 4 evaluated without rounding: the published rationals
+    # meet them to ~1e-26 and their doubles to ~1e-17, while a one-digit typo in any
+    # 13-digit numerator or denominator leaves residuals of ~1e-14 to 1e-13.
+    A, B, c = (list(map(Fraction, v)) for v in O.lsrk_coeffs())
     a, b = _butcher_from_2n(A, B)
-    cc = a.sum(axis=1)
-    assert np.allclose(cc, c, atol=1e-12, rtol=0)
+    s = len(A)
+    cc = [sum(row) for row in a]
+    assert max(abs(float(x - y)) for x, y in zip(cc, c)) < 1e-15
+
+    def dot(x, y):
+        return sum(p * q for p, q in zip(x, y))
+
+    def amul(v):
+        return [dot(a[i], v) for i in range(s)]
+
+    ac = amul(cc)
     conds = [
-        (b.sum(), 1.0),
-        (b @ cc, 1 / 2),
-        (b @ cc ** 2, 1 / 3),
-        (b @ (a @ cc), 1 / 6),
-        (b @ cc ** 3, 1 / 4),
-        (b @ (cc * (a @ cc)), 1 / 8),
-        (b @ (a @ cc ** 2), 1 / 12),
-        (b @ (a @ (a @ cc)), 1 / 24),
+        (sum(b), Fraction(1)),
+        (dot(b, cc), Fraction(1, 2)),
+        (dot(b, [x ** 2 for x in cc]), Fraction(1, 3)),
+        (dot(b, ac), Fraction(1, 6)),
+        (dot(b, [x ** 3 for x in cc]), Fraction(1, 4)),
+        (dot(b, [x * y for x, y in zip(cc, ac)]), Fraction(1, 8)),
+        (dot(b, amul([x ** 2 for x in cc])), Fraction(1, 12)),
+        (dot(b, amul(ac)), Fraction(1, 24)),
     ]
     for got, want in conds:
-        assert abs(got - want) < 1e-12
+        assert abs(float(got - want)) < 1e-15, float(got - want)
     # a fifth-order condition is not met: the scheme is exactly fourth order
-    assert abs(b @ cc ** 4 - 1 / 5) > 1e-6
+    assert abs(float(dot(b, [x ** 4 for x in cc]) - Fraction(1, 5))) > 1e-6
 
 
 def test_lsrk_fourth_order_on_linear_ode():
