@@ -1,0 +1,156 @@
+"""Planted mistakes in the oracle are caught by its pins (CPU only).
+
+Each entry below changes one expression of a scratch copy of oracle/oracle.c (a
+dropped term, a wrong sign, factor or index, a transposed operand, a mistyped
+constant), rebuilds that copy and runs the oracle's pin tests against it; the pins
+must fail.  The mutations run in parallel subprocesses, one scratch directory each;
+the oracle in the repository is never modified.
+
+One entry is expected to pass the pins: the averaged state of the matrix dissipation
+is a reading (the paper's Eq. A.1 citation is not in the paper), and any average that
+keeps the matrix symmetric positive semi-definite and exact at equal states satisfies
+every pin.  It is listed so that the gap stays visible.
+"""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PIN_TESTS = ["test_oracle_basis.py", "test_oracle_flux.py", "test_oracle_global.py",
+             "test_oracle_matrix_form.py", "test_golden_paper.py"]
+
+# (what, original expression, planted mistake)
+MUTATIONS = [
+    ("EC energy flux drops {{phi}}",
+     "F[0] * (1 / (2 * (gamma - 1) * b_log) + uu / 2 + phi_avg)",
+     "F[0] * (1 / (2 * (gamma - 1) * b_log) + uu / 2)"),
+    ("p* missing its factor 2", "real pstar = rho_avg / (2 * b_avg);",
+     "real pstar = rho_avg / (b_avg);"),
+    ("gravity rho_hat divides by the partner's b", "real rho_hat = b_avg * rho_log / A->b;",
+     "real rho_hat = b_avg * rho_log / Bp->b;"),
+    ("gravity sign", "real g = rho_hat * (Bp->phi - A->phi) / 2;",
+     "real g = rho_hat * (A->phi - Bp->phi) / 2;"),
+    ("gravity factor 1/2 dropped", "real g = rho_hat * (Bp->phi - A->phi) / 2;",
+     "real g = rho_hat * (Bp->phi - A->phi);"),
+    ("mean velocity from the partner only", "ubar[k] = (A->u[k] + Bp->u[k]) / 2;",
+     "ubar[k] = Bp->u[k];"),
+    ("u- . u+ replaced by |u-|^2", "uu += A->u[k] * Bp->u[k];", "uu += A->u[k] * A->u[k];"),
+    ("pressure drops the geopotential", "s.p = (gamma - 1) * (q[4] - ke - q[0] * phi);",
+     "s.p = (gamma - 1) * (q[4] - ke);"),
+    ("entropy variable drops 2 b phi",
+     "v[0] = (gamma - ent) / (gamma - 1) - s.b * u2 + 2 * s.b * phi;",
+     "v[0] = (gamma - ent) / (gamma - 1) - s.b * u2;"),
+    ("log-mean series coefficient", "s = s * u + (real)2 / (real)(2 * k + 1);",
+     "s = s * u + (real)2 / (real)(2 * k + 3);"),
+    ("volume metric not averaged",
+     "n[k] = (Ja[(d * 3 + k) * np + i] + Ja[(d * 3 + k) * np + l]) / 2;",
+     "n[k] = Ja[(d * 3 + k) * np + i];"),
+    ("Dt = D instead of 2D", "B->Dt[i][l] = (i == l) ? (real)0 : 2 * B->D[i][l];",
+     "B->Dt[i][l] = (i == l) ? (real)0 : B->D[i][l];"),
+    ("surface lift weight of an interior node",
+     "surf[((size_t)e * NV + v) * np + i] -= s / (J[i] * B->w[own_end]) * Fs[v];",
+     "surf[((size_t)e * NV + v) * np + i] -= s / (J[i] * B->w[1]) * Fs[v];"),
+    ("wall mirror without the factor 2", "qp[1 + k] = qm[1 + k] - 2 * Un * nh[k];",
+     "qp[1 + k] = qm[1 + k] - Un * nh[k];"),
+    ("periodic neighbour off by one", "idx[d] = (idx[d] + K[d]) % K[d];",
+     "idx[d] = (idx[d] + K[d] + 1) % K[d];"),
+    ("metric curl sign", "Ja[(d * 3 + comp) * np + n] = -(t1[n] - t2[n]);",
+     "Ja[(d * 3 + comp) * np + n] = (t1[n] - t2[n]);"),
+    ("warp displacement index", "out[1] += a * L[1] * s2 * s0;", "out[1] += a * L[1] * s2 * s1;"),
+    ("dissipation T[1]", "T[1] = rho_hat * (gamma - 1) / gamma;", "T[1] = rho_hat / gamma;"),
+    ("dissipation acoustic T", "T[0] = T[4] = rho_hat / (2 * gamma);",
+     "T[0] = T[4] = rho_hat / gamma;"),
+    ("enthalpy drops phi", "real H = a * a / (gamma - 1) + u2 / 2 + phi;",
+     "real H = a * a / (gamma - 1) + u2 / 2;"),
+    ("entropy-wave eigenvector drops phi", "{1, u[0], u[1], u[2], u2 / 2 + phi},",
+     "{1, u[0], u[1], u[2], u2 / 2},"),
+    ("dissipation sign", "Fs[r] -= s / 2;", "Fs[r] += s / 2;"),
+    ("dissipation halved", "Fs[r] -= s / 2;", "Fs[r] -= s / 4;"),
+    ("Coriolis sign in x-momentum",
+     "src[((size_t)e * NV + 1) * np + i] = f * q[((size_t)e * NV + 2) * np + i];",
+     "src[((size_t)e * NV + 1) * np + i] = -f * q[((size_t)e * NV + 2) * np + i];"),
+    ("Coriolis sign in y-momentum",
+     "src[((size_t)e * NV + 2) * np + i] = -f * q[((size_t)e * NV + 1) * np + i];",
+     "src[((size_t)e * NV + 2) * np + i] = f * q[((size_t)e * NV + 1) * np + i];"),
+    ("LSRK A_2 denominator typo", "-567301805773.0L / 1357537059087.0L",
+     "-567301805773.0L / 1357537059088.0L"),
+    ("LSRK B_2 denominator typo", "5161836677717.0L / 13612068292357.0L",
+     "5161836677717.0L / 13612068292347.0L"),
+    ("LSRK c_3 denominator typo", "2526269341429.0L / 6820363962896.0L",
+     "2526269341429.0L / 6820363962886.0L"),
+    ("CFL without the square root", "real lam = (fabs(un) + cs * sqrt(a2)) / J;",
+     "real lam = (fabs(un) + cs * a2) / J;"),
+    ("smooth bubble profile", "(real)amp * (1 + cos(pi * r / (real)radius)) / 2",
+     "(real)amp * cos(pi * r / (real)radius / 2)"),
+    ("sharp bubble amplitude", "dth = profile ? (real)amp :", "dth = profile ? (real)amp / 2 :"),
+    ("Exner exponent inverted", "real p = (real)ph->p0 * pow(ex, cp / R);",
+     "real p = (real)ph->p0 * pow(ex, R / cp);"),
+    ("bubble temperature", "real T = ((real)theta0 + dth) * ex;",
+     "real T = ((real)theta0) * ex + dth;"),
+    ("isothermal scale height",
+     "real rho = (real)rho_surface * exp(-g * z / (R * (real)T));",
+     "real rho = (real)rho_surface * exp(-g * z / (R * (real)T * 1.01));"),
+    ("channel density off hydrostatic balance", "real rho = p / (g * H);",
+     "real rho = p / (g * H * 1.001);"),
+    ("channel wind sign", "real u = -g * Z * dHdy / (f * H);", "real u = g * Z * dHdy / (f * H);"),
+    ("entropy integral sign",
+     "ent += wJ * (-qn[0] * (log(s.p) - gamma * log(s.rho)) / (gamma - 1));",
+     "ent += wJ * (qn[0] * (log(s.p) - gamma * log(s.rho)) / (gamma - 1));"),
+    ("mass integral without the weight", "m += wJ * qn[0];",
+     "m += c->J[(size_t)e * np + n] * qn[0];"),
+]
+
+# readings the paper does not fix: the pins cannot tell these apart (parity unpinned)
+UNPINNED = [
+    ("dissipation p_hat from the log-mean density",
+     "real p_hat = ((M->rho + P->rho) / 2) / (2 * ((M->b + P->b) / 2));",
+     "real p_hat = rho_hat / (2 * ((M->b + P->b) / 2));"),
+]
+
+
+def _copy_tree(dst):
+    ign = shutil.ignore_patterns("_build", "__pycache__", "*.so", "*.o", ".pytest_cache")
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"), ignore=ign)
+    os.makedirs(os.path.join(dst, "tests", "golden"))
+    for f in PIN_TESTS + ["conftest.py"]:
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
+    shutil.copy(os.path.join(ROOT, "tests", "golden", "paper_runs.txt"),
+                os.path.join(dst, "tests", "golden", "paper_runs.txt"))
+    pkg = os.path.join(dst, "paper_2605_16684_gb300")
+    os.makedirs(pkg)
+    for f in ("__init__.py", "inputs.py"):
+        shutil.copy(os.path.join(ROOT, "paper_2605_16684_gb300", f), os.path.join(pkg, f))
+    for f in ("bench.py", "pytest.ini"):
+        shutil.copy(os.path.join(ROOT, f), os.path.join(dst, f))
+
+
+def _run(tmp_root, k, old, new):
+    dst = os.path.join(tmp_root, f"m{k:02d}")
+    _copy_tree(dst)
+    src = os.path.join(dst, "oracle", "oracle.c")
+    text = open(src).read()
+    i = text.find(old)
+    if i < 0:
+        return "pattern not found"
+    open(src, "w").write(text[:i] + new + text[i + len(old):])
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu",
+                        "-p", "no:cacheprovider"] + [os.path.join("tests", t) for t in PIN_TESTS],
+                       cwd=dst, capture_output=True, text=True, timeout=600, env=env)
+    shutil.rmtree(dst, ignore_errors=True)
+    return "caught" if r.returncode != 0 else "passed the pins"
+
+
+def test_planted_mistakes_are_caught(tmp_path):
+    cases = MUTATIONS + UNPINNED
+    workers = max(2, min(8, os.cpu_count() or 2))
+    with ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(lambda kc: _run(str(tmp_path), kc[0], kc[1][1], kc[1][2]),
+                              enumerate(cases)))
+    missed = [(c[0], r) for c, r in zip(MUTATIONS, results) if r != "caught"]
+    assert not missed, missed
+    # the unpinned reading passes every pin; if it ever fails one, move it up
+    for c, r in zip(UNPINNED, results[len(MUTATIONS):]):
+        assert r == "passed the pins", (c[0], r)
