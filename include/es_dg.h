@@ -118,8 +118,13 @@ int es_dg_init_bubble(es_dg_t* h, double theta0, double amp, const double centre
 enum { ES_DG_BUBBLE_SMOOTH = 0, ES_DG_BUBBLE_SHARP = 1 };
 int es_dg_init_bubble_profile(es_dg_t* h, double theta0, double amp, const double centre[3],
                               double radius, int profile);
-/* Synthetic baroclinic-channel state (balanced zonal jet of isothermal columns
- * plus a 1 m/s Gaussian wind perturbation; see the oracle for the formulas). */
+/* Synthetic baroclinic-channel state (Section 5.2 configuration; the benchmark's
+ * own balanced-jet formulas are not in the paper, so this is a stand-in):
+ * isothermal columns p = p0 exp(-z/H(y)), H(y) = 7500 m + 60 m (1 - tanh((y -
+ * 3000 km)/600 km)), rho = p/(g H), zonal wind in geostrophic balance
+ * u = -g z H'(y)/(f H) with f = f0 + beta (y - y0), plus the perturbation
+ * 1 m/s exp(-((x - 2000 km)^2 + (y - 2500 km)^2)/(600 km)^2); v = w = 0.
+ * Needs f != 0 somewhere (ES_DG_EINVAL when f0 = beta = 0). */
 int es_dg_init_channel(es_dg_t* h);
 
 /* Hydrostatic background of the mixed-precision path (the perturbation-variable
