@@ -440,3 +440,19 @@ def test_integrals_of_a_uniform_state():
     s = np.log(p) - GAMMA * np.log(rho)
     want = np.array([rho * V, q[0, 4, 0] * V, -rho * s / (GAMMA - 1) * V])
     assert np.allclose(o.integrals(q), want, rtol=1e-12, atol=0)
+
+
+def test_rhs_scale_bounds_the_volume_term():
+    # or_rhs_scale (the round-off floor of the GPU parity bars on near-hydrostatic states)
+    # is sum_l |Dt_il| |H| / J plus face terms: by the triangle inequality it bounds the
+    # volume term node by node, and at a rest state it is far larger than the right-hand
+    # side (the cancellation the floor accounts for)
+    o = O.Oracle(2, 2, 2, 3, lo=BOX[0], hi=BOX[1], warp=0.05)
+    q = generic_state(o, seed=2)
+    v, _, _ = o.rhs_parts(q)
+    sc = o.rhs_scale(q)
+    assert np.all(sc >= np.abs(v) * (1 - 1e-12))
+    qb = o.bubble()
+    r = o.rhs(qb)
+    scb = o.rhs_scale(qb)
+    assert np.linalg.norm(scb[:, 3]) > 1e3 * np.linalg.norm(r[:, 3])
