@@ -82,6 +82,17 @@ MUTATIONS = [
      "2526269341429.0L / 6820363962886.0L"),
     ("CFL without the square root", "real lam = (fabs(un) + cs * sqrt(a2)) / J;",
      "real lam = (fabs(un) + cs * a2) / J;"),
+    ("CFL node spacing", "(real)C * (B->xi[1] - B->xi[0]) / lam_max",
+     "(real)C * (B->xi[2] - B->xi[0]) / lam_max"),
+    ("face normal not outward on the low face",
+     "nh[k] = (side ? 1 : -1) * jn[k] / s;", "nh[k] = jn[k] / s;"),
+    ("surface term sign",
+     "surf[((size_t)e * NV + v) * np + i] -= s / (J[i] * B->w[own_end]) * Fs[v];",
+     "surf[((size_t)e * NV + v) * np + i] += s / (J[i] * B->w[own_end]) * Fs[v];"),
+    ("volume term sign", "vol[((size_t)e * NV + v) * np + i] = -acc[v] / J[i];",
+     "vol[((size_t)e * NV + v) * np + i] = acc[v] / J[i];"),
+    ("warp amplitude doubled in x", "out[0] += a * L[0] * s1 * s2;",
+     "out[0] += 2 * a * L[0] * s1 * s2;"),
     ("smooth bubble profile", "(real)amp * (1 + cos(pi * r / (real)radius)) / 2",
      "(real)amp * cos(pi * r / (real)radius / 2)"),
     ("sharp bubble amplitude", "dth = profile ? (real)amp :", "dth = profile ? (real)amp / 2 :"),
