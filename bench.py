@@ -12,6 +12,13 @@ path (FP32 pairs, FP64 state) next to it; the roofline object is the FP64
 volume kernel's achieved algorithmic FLOP rate (events around every volume
 launch of the timed region) against the FP64 vector peak; e2e is the same
 metric through the C ABI with pinned host buffers copied in and out every step.
+At one GPU the line also carries the other two halves of the metric: "ensemble"
+(64 heterogeneous rising-bubble members, 100 steps, batched in mixed precision:
+DOF-updates/s, p50/p99 solve latency, speed-up over the same members solved one
+after another in plain FP64, per-variable error against those FP64 solves) and
+"serving" (a Poisson stream of the serving workload's requests at 8x the
+sequential-FP64 service rate: p50/p99 latency, throughput and its ratio to
+sequential FP64).
 
 Multi-GPU (torchrun): every rank advances its own replica (ensemble members are
 independent, no data-path collective); value = all ranks' DOF-updates / max time.
@@ -52,13 +59,31 @@ FACE_BYTES_PER_NODE = {"fp64": 160, "mixed": 140}
 
 # DRAM traffic of one FP64 volume launch (k_volume_pipe64<4, 1, 0>): ncu capture of the same
 # kernel on the 24^3 case (dram__bytes_read.sum + dram__bytes_write.sum = 332.80 MB +
-# 99.38 MB for 13 824 elements), scaled to the 32^3 launch by the element count
-# (profiles/volume_fp64_N4_24cubed.md).
+# 99.38 MB for 13 824 elements), scaled to the 32^3 launch by the element count.
 VOLUME_FP64_TRAFFIC_BYTES = (332.80e6 + 99.38e6) * 32768 / 13824
 
-SM_COUNT, SM_MAX_MHZ = 152, 2070.0
-FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2     # 2 DFMA / clk / SM -> 1.258 TFLOP/s
-FP32_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2   # 128 FFMA / clk / SM -> 80.5 TFLOP/s
+# Vector issue rates of the part (per SM and clock): 2 FP64 FMA, 128 FP32 FMA.
+DFMA_PER_CLK_SM, FFMA_PER_CLK_SM = 2, 128
+
+
+def device_peaks(device=0):
+    """FP64 / FP32 vector peaks (FLOP/s) from the device's SM count and maximum SM
+    clock: the SM count from the CUDA device properties, the clock from nvidia-smi's
+    clocks.max.sm (a read-only query), else MEASURED_PEAKS.json's sm_max_mhz."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz, src = None, "nvidia-smi clocks.max.sm"
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(device), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=20).stdout.strip().splitlines()
+        mhz = float(out[0])
+    except Exception:
+        peaks, _ = measured_peaks()
+        mhz, src = float(peaks.get("sm_max_mhz", 2070.0)), "MEASURED_PEAKS.json sm_max_mhz"
+    hz = mhz * 1e6
+    return {"sms": sms, "sm_max_mhz": mhz, "clock_source": src,
+            "fp64": sms * hz * DFMA_PER_CLK_SM * 2, "fp32": sms * hz * FFMA_PER_CLK_SM * 2}
 
 
 def measured_peaks():
@@ -285,13 +310,14 @@ def main_ours(args):
             dist.destroy_process_group()
         return
     peaks, peak_src = measured_peaks()
+    dev = device_peaks(int(os.environ.get("LOCAL_RANK", "0")))
+    FP64_PEAK, FP32_PEAK = dev["fp64"], dev["fp32"]
     r64, r32 = res["fp64"], res["mixed"]
     w = WORKLOAD
     value = replica_throughput(world, r64["ndof"], args.steps, r64["ms"] * 1e-3)
     value32 = replica_throughput(world, r32["ndof"], args.steps, r32["ms"] * 1e-3)
     vflops = volume_flops(r64["E"], w["N"])
     achieved = vflops / (r64["t_vol"] * 1e-3)
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps, "higher_is_better": True,
@@ -301,7 +327,9 @@ def main_ours(args):
                      "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK,
                      "traffic": VOLUME_FP64_TRAFFIC_BYTES if w["K"] == (32, 32, 32) else None,
-                     "peak_source": "152 SMs x 2 DFMA/clk x 2070 MHz (recipe's 1.25 TFLOP/s FP64)",
+                     "peak_source": f"{dev['sms']} SMs x {DFMA_PER_CLK_SM} DFMA/clk x "
+                                    f"{dev['sm_max_mhz']:.0f} MHz ({dev['clock_source']}); the "
+                                    "recipe's nominal FP64 rate is 1.25 TFLOP/s",
                      "flops_per_launch": vflops, "ms_per_launch": r64["t_vol"]},
         "kernels_ms_per_stage": {"fp64": {"interface": r64["t_face"], "volume_rk": r64["t_vol"]},
                                  "mixed": {"interface": r32["t_face"], "volume_rk": r32["t_vol"]}},
@@ -324,6 +352,13 @@ def main_ours(args):
     }
     if not args.no_cpu_baseline and world >= 1:
         out["cpu_baseline"] = cpu_sample(args.cpu_seconds)
+    if world == 1 and not args.no_ensemble:
+        # the batched-ensemble and serving halves of the metric (single-GPU measurements)
+        out["ensemble"] = ensemble_measure(args.members, ENSEMBLE_STEPS)
+        out["serving"] = serving_measure(SERVING_DEFAULT["requests"], SERVING_DEFAULT["steps"],
+                                         SERVING_DEFAULT["rates"], SERVING_DEFAULT["calib"],
+                                         args.slots, args.budget_gb,
+                                         check=SERVING_DEFAULT["check"])
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
@@ -374,7 +409,7 @@ def _sequential(req, precision):
         s = _lib.Solver(*req["K"], req["N"], lo=(0, 0, 0), hi=(40000e3, 6000e3, 30e3),
                         periodic=(1, 0, 0), precision=precision, f0=1e-4)
         s.init_channel()
-    dt = s.cfl_dt(0.5)
+    dt = s.cfl_dt(req.get("cfl", SERVER_CFL))
     torch.cuda.synchronize()
     t = time.perf_counter()
     s.step(dt, req["nsteps"])
@@ -391,16 +426,44 @@ def _pct(x, p):
     return float(np.percentile(np.asarray(x), p)) if len(x) else None
 
 
-def run_ensemble(args):
+ENSEMBLE_STEPS = 100  # the batched-ensemble workload's step count
+# Courant number of the batched workloads (their definition gives none): the server's
+# default, 0.4 -- C = 0.5 is on the stability boundary for unwarped meshes at N >= 4
+SERVER_CFL = 0.4
+
+
+def _state_errors(q, q_ref):
+    """Relative L2 error per variable (rho, rho u, rho v, rho w, E) of a final state,
+    the momentum components against the norm of the momentum vector (a rising
+    bubble starts at rest, so a single component's norm is that of the flow's
+    smallest part)."""
+    import numpy as np
+    q, q_ref = q.reshape(q_ref.shape), q_ref
+    mom = np.sqrt(sum(np.linalg.norm(q_ref[:, v]) ** 2 for v in (1, 2, 3)))
+    return [float(np.linalg.norm(q[:, v] - q_ref[:, v]) /
+                  (mom if v in (1, 2, 3) else np.linalg.norm(q_ref[:, v]))) for v in range(5)]
+
+
+def ensemble_measure(n_members, steps):
+    """Config 3: n_members rising-bubble members (K^3, K ~ U{8..24}, N ~ U{3,4,7},
+    amplitude ~ U(0.25, 1) K, centre jitter +-100 m, one seed) solved together by the
+    server in mixed precision (one persistent interface + volume launch per order group
+    and stage, one CUDA-graph replay per step), the autotuner warmed first.  Then every
+    member solved alone in plain FP64 through the single-handle path: the speed-up is
+    measured on the same solves, and each member's final mixed state is compared with
+    its FP64 state, per variable."""
     import numpy as np
     import torch
     from paper_2605_16684_gb300 import _build, _lib, inputs
     _build.build()
     torch.cuda.init()
-    members = inputs.ensemble_members(args.members)
+    members = inputs.ensemble_members(n_members)
     reqs = [dict(kind="bubble", K=(m["K"],) * 3, N=m["N"], amp=m["amp"], centre=m["centre"],
-                 nsteps=args.steps) for m in members]
+                 nsteps=steps) for m in members]
     srv = _lib.Server(hbm_budget_bytes=200 << 30, max_slots=len(reqs))
+    tw = time.perf_counter()
+    srv.warmup((3, 4, 7), "mixed")
+    warm_s = time.perf_counter() - tw
     t0 = time.perf_counter()
     tickets = [srv.submit(precision="mixed", **r) for r in reqs]
     res = [srv.wait(t) for t in tickets]
@@ -411,29 +474,35 @@ def run_ensemble(args):
     dof_updates = sum(r["ndof"] * 5 * r["nsteps"] for r in res)
     run = max(r["t_finish"] for r in res) - max(r["t_admit"] for r in res)
     lat = [r["t_finish"] - r["t_submit"] for r in res]
-    # sequential plain FP64 solves of the same members (stepping time only)
-    seq_t, seq_err = 0.0, []
+    seq_t, errs = 0.0, []
     for i, r in enumerate(reqs):
         el, nd, q64 = _sequential(r, "fp64")
         seq_t += el
-        if i < args.check:
-            qb = res[i]["q"].reshape(q64.shape)
-            seq_err.append([float(np.linalg.norm(qb[:, v] - q64[:, v]) / np.linalg.norm(q64[:, v]))
-                            for v in (0, 4)])
-    out = {"metric": "ensemble DOF-updates/s per RK stage", "value": dof_updates / run,
-           "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
-           "config": {"workload": "batched_ensemble_64_bubbles", "members": len(reqs),
-                      "grids": "K^3, K ~ U{8..24}", "orders": "N ~ U{3,4,7}",
-                      "precision": "mixed (FP32 pairs, FP64 state)",
-                      "launches": "one persistent interface + volume launch per (N) group per "
-                                  "stage, one LSRK step per CUDA graph replay"},
-           "batched_run_seconds": run, "wall_seconds_incl_admission": wall,
-           "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
-           "sequential_fp64_value": dof_updates / seq_t,
-           "speedup_vs_sequential_fp64": (dof_updates / run) / (dof_updates / seq_t),
-           "mixed_vs_fp64_state_rel_err_rho_E_first_members": seq_err,
-           "server_steps": stats["steps"]}
-    print(json.dumps(out))
+        errs.append(_state_errors(res[i]["q"], q64))
+    errs = np.array(errs)
+    value = dof_updates / run
+    return {"metric": "ensemble DOF-updates/s per RK stage; p50/p99 solve latency",
+            "value": value, "unit": UNIT, "steps": steps,
+            "config": {"workload": f"batched_ensemble_{len(reqs)}_bubbles", "members": len(reqs),
+                       "grids": "K^3, K ~ U{8..24}", "orders": "N ~ U{3,4,7}",
+                       "precision": "mixed (FP32 pairs, FP64 state)",
+                       "launches": "one persistent interface + volume launch per order group and "
+                                   "stage, one LSRK step per CUDA graph replay"},
+            "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+            "batched_run_seconds": run, "wall_seconds_incl_admission": wall,
+            "autotuner_warmup_seconds": warm_s,
+            "sequential_fp64_value": dof_updates / seq_t,
+            "speedup_vs_sequential_fp64": value / (dof_updates / seq_t),
+            "mixed_vs_fp64_state_rel_err_max_over_members": {
+                k: float(errs[:, v].max()) for v, k in enumerate(("rho", "rho_u", "rho_v",
+                                                                   "rho_w", "E"))},
+            "members_within_1e-4": int((errs.max(axis=1) <= 1e-4).sum()),
+            "server_steps": stats["steps"]}
+
+
+def run_ensemble(args):
+    steps = args.steps if args.steps_given else ENSEMBLE_STEPS
+    print(json.dumps(ensemble_measure(args.members, steps)))
 
 
 CHANNEL = dict(K=(120, 24, 12), N=4, lo=(0.0, 0.0, 0.0), hi=(40000e3, 6000e3, 30e3),
@@ -651,23 +720,50 @@ def run_slabs(args):
     print(json.dumps(out))
 
 
-def run_serving(args):
+# The serving line of the default run: a reduced stream of the serving workload
+# (its request mix and 200 steps per request; 24 requests instead of 2000) at one
+# offered rate, 8x what sequential plain FP64 solves can serve, so the server runs
+# saturated and its throughput is its capacity.  --workload serving runs the rate sweep.
+SERVING_DEFAULT = dict(requests=24, steps=200, rates=(8.0,), calib=6, check=2)
+
+
+def serving_measure(n_requests, steps, rates, calib, slots, budget_gb, check=0):
+    """Serving workload: Poisson streams of n_requests solve requests (70 % rising
+    bubbles K^3, K ~ U{8..32}; 30 % channels (40s, 8s, 4s), s ~ U[1,3]; N ~ U{3,4,7};
+    `steps` LSRK steps each) submitted by a client thread at each offered rate (a
+    multiple of the sequential plain-FP64 service rate) to a server in mixed
+    precision (FIFO admission by HBM footprint, continuous batching), autotuner warmed.
+    The sequential FP64 rate is measured on the first `calib` requests of the stream
+    (single-handle solves, 20 steps each: DOF-updates/s does not depend on the step
+    count); the service rate follows from the stream's mean work per request.  The
+    `check` smallest requests are also solved alone in FP64 for their full step count
+    and compared with their served results, per variable."""
     import threading
     import numpy as np
     import torch
     from paper_2605_16684_gb300 import _build, _lib, inputs
     _build.build()
     torch.cuda.init()
-    # sequential FP64 service rate from a sample of the stream
-    sample = inputs.request_stream(args.requests, 1.0, seed=inputs.DEFAULT_SEED + 1,
-                                   steps=args.steps)[: args.calib]
-    t_seq = [_sequential(dict(r, nsteps=r["steps"]), "fp64")[0] for r in sample]
-    seq_rate = 1.0 / float(np.mean(t_seq))
+    base = inputs.request_stream(n_requests, 1.0, seed=inputs.DEFAULT_SEED + 1, steps=steps)
+    cal_t = cal_dof = 0.0
+    for r in base[:calib]:
+        el, nd, _ = _sequential(dict(r, nsteps=20), "fp64")
+        cal_t += el
+        cal_dof += nd * 5 * 20
+    seq_value = cal_dof / cal_t
+
+    def work(r):
+        Nq = r["N"] + 1
+        return r["K"][0] * r["K"][1] * r["K"][2] * Nq ** 3 * 5 * r["steps"]
+
+    mean_work = float(np.mean([work(r) for r in base]))
+    seq_rate = seq_value / mean_work  # requests/s that sequential FP64 solves can serve
     points = []
-    for mult in [float(x) for x in args.rates.split(",")]:
+    for mult in rates:
         rate = mult * seq_rate
-        stream = inputs.request_stream(args.requests, rate, steps=args.steps)
-        srv = _lib.Server(hbm_budget_bytes=args.budget_gb << 30, max_slots=args.slots)
+        stream = inputs.request_stream(n_requests, rate, seed=inputs.DEFAULT_SEED + 1, steps=steps)
+        srv = _lib.Server(hbm_budget_bytes=budget_gb << 30, max_slots=slots)
+        srv.warmup((3, 4, 7), "mixed")
         tickets = [None] * len(stream)
 
         def submitter():
@@ -692,19 +788,37 @@ def run_serving(args):
         ok = [r for r in res if r["status"] == 0]
         lat = [r["t_finish"] - r["t_submit"] for r in ok]
         dof = sum(r["ndof"] * 5 * r["nsteps"] for r in ok)
-        points.append({"rate_x_seq_fp64": mult, "rate_hz": rate, "completed": len(ok),
-                       "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
-                       "throughput": dof / makespan, "makespan_s": makespan,
-                       "error": st["error"]})
-    out = {"metric": "serving p50/p99 solve latency and DOF-updates/s per RK stage",
-           "unit": "s / DOF-updates/s", "higher_is_better": False, "n_gpus": 1,
-           "config": {"workload": "poisson_serving", "requests": args.requests,
-                      "steps_per_request": args.steps,
-                      "mix": "70% bubbles K^3 (K 8..32), 30% channels (40s,8s,4s), N in {3,4,7}",
-                      "precision": "mixed", "admission": "FIFO by HBM footprint"},
-           "sequential_fp64_service_rate_hz": seq_rate,
-           "sequential_fp64_mean_service_s": float(np.mean(t_seq)), "points": points}
-    print(json.dumps(out))
+        pt = {"rate_x_seq_fp64": mult, "rate_hz": rate, "completed": len(ok),
+              "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+              "throughput": dof / makespan, "makespan_s": makespan,
+              "sequential_fp64_value": seq_value,
+              "throughput_over_sequential_fp64": dof / makespan / seq_value, "error": st["error"]}
+        if check and mult == rates[-1]:
+            small = sorted(range(len(stream)), key=lambda i: work(stream[i]))[:check]
+            errs = []
+            for i in small:
+                r = stream[i]
+                _, _, q64 = _sequential(dict(r, nsteps=r["steps"]), "fp64")
+                errs.append({"request": i, "kind": r["kind"], "K": list(r["K"]), "N": r["N"],
+                             "rel_err_rho_rhou_rhov_rhow_E": _state_errors(res[i]["q"], q64)})
+            pt["mixed_vs_fp64_state_rel_err"] = errs
+        points.append(pt)
+    return {"metric": "serving p50/p99 solve latency and DOF-updates/s per RK stage",
+            "unit": "s / DOF-updates/s", "higher_is_better": False, "n_gpus": 1,
+            "config": {"workload": "poisson_serving", "requests": n_requests,
+                       "steps_per_request": steps,
+                       "mix": "70% bubbles K^3 (K 8..32), 30% channels (40s,8s,4s), N in {3,4,7}",
+                       "precision": "mixed", "admission": "FIFO by HBM footprint",
+                       "autotuner": "warmed for N in {3,4,7} before the stream"},
+            "sequential_fp64_value": seq_value, "sequential_fp64_service_rate_hz": seq_rate,
+            "points": points}
+
+
+def run_serving(args):
+    rates = tuple(float(x) for x in args.rates.split(","))
+    steps = args.steps if args.steps_given else SERVING_DEFAULT["steps"]
+    print(json.dumps(serving_measure(args.requests, steps, rates, args.calib, args.slots,
+                                     args.budget_gb, check=args.check)))
 
 
 def main():
@@ -720,13 +834,17 @@ def main():
     ap.add_argument("--workload", default="bubble32",
                     choices=["bubble32", "ensemble", "serving", "channel", "sharp", "slabs"])
     ap.add_argument("--members", type=int, default=64)
-    ap.add_argument("--check", type=int, default=4, help="ensemble members compared with FP64")
+    ap.add_argument("--check", type=int, default=2,
+                    help="served requests also solved alone in FP64 and compared")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="leave the ensemble and serving objects out of the default line")
     ap.add_argument("--requests", type=int, default=60)
     ap.add_argument("--rates", default="0.25,0.5,1,2,4")
     ap.add_argument("--calib", type=int, default=6)
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--budget-gb", type=int, default=200)
     args = ap.parse_args()
+    args.steps_given = any(a == "--steps" or a.startswith("--steps=") for a in sys.argv[1:])
     if args.workload == "ensemble":
         run_ensemble(args)
         return

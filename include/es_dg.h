@@ -161,8 +161,11 @@ int es_dg_step(es_dg_t* h, double dt, int nsteps);
 /* Wait for the handle's stream.  Returns ES_DG_ETIMEOUT if, since the last
  * call, a bounded device wait of the pipelined volume kernels ran out (their
  * tile copies never completed; the kernel stopped and the state is not
- * valid), ES_DG_ECUDA on a CUDA error, else ES_DG_OK.  The timeout flag is
- * process-wide per device and cleared by the call. */
+ * valid), ES_DG_ENAN if a stage update of this handle (es_dg_step) produced a
+ * state value that is an infinity or a NaN, or a density that is not positive
+ * (the kernels keep stepping; the state is not valid), ES_DG_ECUDA on a CUDA
+ * error, else ES_DG_OK.  The timeout flag is process-wide per device, the
+ * state flag is the handle's; the call clears both. */
 int es_dg_sync(es_dg_t* h);
 
 /* Test hook for the failure path above: the next single-mesh volume launch
@@ -172,6 +175,28 @@ int es_dg_sync(es_dg_t* h);
  * the next es_dg_sync returns ES_DG_ETIMEOUT.  The state of that handle is
  * then undefined; the context stays usable.  One-shot. */
 void es_dg_debug_inject_wait_timeout(void);
+
+/* Test hook for the numeric helpers that the kernels use in place of FP64-pipe
+ * instructions: out[i] = helper(in[i]) for i < n, on device arrays (in: doubles,
+ * or floats for F2D and F2D_POS; out: floats for D2F and D2F_TAIL, else
+ * doubles), asynchronous on cuda_stream.  k is the power of two for LDEXP.
+ *   D2F       double -> float, round to nearest even, for |x| < 2^128 (a
+ *             rounding past FLT_MAX gives +-inf; results below the float normal
+ *             range flush to +-0; larger magnitudes, infinities and NaNs are
+ *             outside the helper's domain and give an unspecified value)
+ *   F2D       float -> double (exact; zero and subnormal floats give +-0)
+ *   LDEXP     x 2^k (exact for normal x and results; +-inf / NaN kept;
+ *             subnormal inputs and results flush to +-0; overflow to +-inf)
+ *   RCP       1/x to about one rounding (MUFU seed + cubic refinement)
+ *   RCP_LO    1/x to about 2^-39 (one Newton step)
+ *   D2F_TAIL  0 <= u < 2^128 to float by mantissa truncation (0 below the float
+ *             normal range)
+ *   F2D_POS   positive normal float -> double (exact)
+ * ES_DG_EINVAL for an unknown helper, n < 0 or missing arrays. */
+enum { ES_DG_NUM_D2F = 0, ES_DG_NUM_F2D = 1, ES_DG_NUM_LDEXP = 2, ES_DG_NUM_RCP = 3,
+       ES_DG_NUM_RCP_LO = 4, ES_DG_NUM_D2F_TAIL = 5, ES_DG_NUM_F2D_POS = 6 };
+int es_dg_debug_numeric(int which, const void* in, void* out, long long n, int k,
+                        void* cuda_stream);
 
 /* Global integrals of the handle's state: mass, total energy, entropy
  * (sum over elements of the quadrature of rho, E and -rho s/(gamma-1)).
@@ -261,6 +286,13 @@ const char* es_dg_strerror(int status);
  * is independent of the others, so a result is the same alone and in a mix. */
 typedef struct es_dg_server es_dg_server;
 
+/* Courant number of requests that give none.  With the es_dg_cfl_dt rule,
+ * C = 0.5 lies on the stability boundary of LSRK(5,4) on unwarped isotropic
+ * meshes for N >= 4 (a 1e-10 perturbation grows by 1e5 to overflow within 300
+ * steps at N = 4..7), C = 0.45 and below are stable for every order; requests
+ * of mixed orders default to 0.4. */
+#define ES_DG_SERVER_DEFAULT_CFL 0.4
+
 typedef struct {
   int kind;                  /* 0 = rising bubble (1000 m cube, periodic x/y, walls z),
                                 1 = baroclinic channel stand-in (40000 x 6000 x 30 km,
@@ -269,7 +301,8 @@ typedef struct {
   int kx, ky, kz, N;         /* elements per direction, order (1..7) */
   es_dg_precision precision;
   int nsteps;                /* LSRK steps to run */
-  double cfl;                /* Courant number for dt (0 = 0.5); dt fixed at admission */
+  double cfl;                /* Courant number for dt (0 = ES_DG_SERVER_DEFAULT_CFL); dt
+                                fixed at admission */
   double amp, centre[3], radius, theta0;  /* bubble: amplitude (K), centre, radius, theta0 */
   double warp;               /* bubble mesh warp (fraction of the edge) */
 } es_dg_request;
@@ -303,6 +336,15 @@ typedef struct {
  * its own. */
 int es_dg_server_create(size_t hbm_budget_bytes, int max_slots, void* cuda_stream,
                         es_dg_server** out);
+/* Tune the batched kernels of the given polynomial orders (each 1..7) and
+ * precision before requests arrive, so that the first request of each order
+ * does not wait for the autotuner: for every order not tuned yet, a
+ * representative rising-bubble member (16^3 elements at N <= 4, 8^3 above) is
+ * created, the tile shape and grid size are timed on it, and it is discarded.
+ * Blocks until done.  The choice is kept for the process (every server on
+ * this device uses it). */
+int es_dg_server_warmup(es_dg_server* s, const int* orders, int n_orders,
+                        es_dg_precision precision);
 /* Queue a request (copied); -ES_DG_ENOMEM if it can never fit the budget,
  * -ES_DG_EBUSY if the queue is full.  Thread-safe. */
 int es_dg_batch_submit(es_dg_server* s, const es_dg_request* req, uint64_t* ticket);
@@ -311,6 +353,10 @@ int es_dg_batch_submit(es_dg_server* s, const es_dg_request* req, uint64_t* tick
 int es_dg_batch_poll(es_dg_server* s, uint64_t ticket, es_dg_result* out);
 /* Blocking poll with a timeout (seconds); -ES_DG_ETIMEOUT when it runs out. */
 int es_dg_batch_wait(es_dg_server* s, uint64_t ticket, double timeout_s, es_dg_result* out);
+/* A request whose state turns non-finite (or whose density turns non-positive)
+ * during a step is finished early with status -ES_DG_ENAN, without a state;
+ * the server reads the members' status words before a member retires and every
+ * 16 steps, and the other members go on unaffected. */
 /* Cancel a queued or running request (its result gets -ES_DG_ECANCELED). */
 int es_dg_batch_cancel(es_dg_server* s, uint64_t ticket);
 void es_dg_result_free(es_dg_result* r);
@@ -334,9 +380,13 @@ void es_dg_server_destroy(es_dg_server* s);
  * Scratch: the per-element partial sums live in a static device array sized
  * for ES_DG_NOALLOC_MAX_ELEMS elements (3 doubles each, 6 MiB), present on
  * every GPU that loads the library until the process exits.  Meshes with more
- * elements are rejected with -ES_DG_EINVAL.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * elements, and physics that es_dg_create would reject (gamma <= 1, R <= 0,
+ * p0 <= 0), get -ES_DG_EINVAL before any CUDA call.  Each call made while
+ * cuda_stream is not capturing looks up the array's device address
+ * (cudaGetSymbolAddress) with the current device, so a device reset, which may
+ * move the array, is picked up; a call made during a capture reuses the
+ * address of the last call outside one, so make the first call on each device
+ * before any stream capture, and again after a device reset.  All calls share
  * the one array: calls whose work overlaps on the GPU (different streams
  * without ordering) race and must be serialised by the caller. */
 #define ES_DG_NOALLOC_MAX_ELEMS 262144

@@ -108,6 +108,8 @@ SIGNATURES = {
     "es_dg_integrals_noalloc": (C.c_int, [C.POINTER(es_dg_mesh), C.c_int, C.POINTER(es_dg_physics),
                                           _VP, _VP, _VP, _VP, _VP]),
     "es_dg_server_create": (C.c_int, [C.c_size_t, C.c_int, _VP, C.POINTER(_VP)]),
+    "es_dg_server_warmup": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int, C.c_int]),
+    "es_dg_debug_numeric": (C.c_int, [C.c_int, _VP, _VP, C.c_longlong, C.c_int, _VP]),
     "es_dg_batch_submit": (C.c_int, [_VP, C.POINTER(es_dg_request), C.POINTER(C.c_uint64)]),
     "es_dg_batch_poll": (C.c_int, [_VP, C.c_uint64, C.POINTER(es_dg_result)]),
     "es_dg_batch_wait": (C.c_int, [_VP, C.c_uint64, C.c_double, C.POINTER(es_dg_result)]),
@@ -435,11 +437,18 @@ class Server:
         self.h = h
 
     @staticmethod
-    def request(kind="bubble", K=(4, 4, 4), N=3, precision="fp64", nsteps=10, cfl=0.5, amp=0.5,
+    def request(kind="bubble", K=(4, 4, 4), N=3, precision="fp64", nsteps=10, cfl=0.4, amp=0.5,
                 centre=(500.0, 500.0, 350.0), radius=250.0, theta0=300.0, warp=0.0):
         return es_dg_request({"bubble": 0, "channel": 1, "sharp_bubble": 2}[kind], *K, N,
                              {"fp64": ES_DG_FP64, "mixed": ES_DG_FP32_MIXED}[precision], nsteps,
                              cfl, amp, (C.c_double * 3)(*centre), radius, theta0, warp)
+
+    def warmup(self, orders=(3, 4, 7), precision="mixed"):
+        """Tune the batched kernels of these orders before requests arrive."""
+        arr = (C.c_int * len(orders))(*orders)
+        check(self.lib.es_dg_server_warmup(self.h, arr, len(orders),
+                                           {"fp64": ES_DG_FP64, "mixed": ES_DG_FP32_MIXED}[precision]),
+              "es_dg_server_warmup")
 
     def submit(self, **req) -> int:
         t = C.c_uint64()

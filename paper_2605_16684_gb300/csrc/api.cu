@@ -41,12 +41,19 @@ struct es_dg {
   double* rhs;      // lazily allocated
   double* qtmp;     // lazily allocated
   double* scratch;  // reductions
-  double* result;   // small device result slots (4 doubles)
+  double* result;   // small device result slots (3 doubles, then the status word)
+  int* status;      // set by a stage update whose new state is not finite or has a
+                    // non-positive density; read and cleared by es_dg_sync
   // mixed precision relative to a hydrostatic background
   int has_bg;
   double* bg;       // [E][3][np] rho_bg, b_bg, p_bg
   double* rhs_bg;   // [E][3][np] FP64 momentum right-hand side of the background at rest
   double* fflux64;  // FP64 face fluxes for evaluating that right-hand side
+  // the mixed volume kernels' copy: bg2 [E][2][np] rho_bg, E_bg; bgp [E][4][np] FP32
+  // rho_bg/4, b_bg/2, 1/b_bg, p_bg; rhs_bg32 [E][3][np] the momentum rhs in FP32
+  double* bg2;
+  float* bgp;
+  float* rhs_bg32;
   // a partition's trace buffers (caller-owned device memory; [0] low x plane, [1] high)
   double* tr_send[2];
   double* tr_recv[2];
@@ -148,11 +155,13 @@ EsdgVolArgs vol_args(es_dg_t* h, const double* q_in, double* rhs_out) {
   a.vgeo64 = h->vgeo;
   a.fflux = h->fflux;
   a.x = h->x;
-  a.bg = (h->mixed && h->has_bg) ? h->bg : nullptr;
-  a.rhs_bg = h->rhs_bg;
+  a.bg = (h->mixed && h->has_bg) ? h->bg2 : nullptr;
+  a.bgp = h->bgp;
+  a.rhs_bg = h->rhs_bg32;
   a.rkA = 0.0;
   a.rkB = 0.0;
   a.dt = 0.0;
+  a.status = h->status;
   return a;
 }
 
@@ -207,10 +216,15 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
   if (!st && !h->rhs_bg) st = dev_alloc(h, (void**)&h->rhs_bg, E * 3 * np * sizeof(double));
   if (!st && !h->fflux64)
     st = dev_alloc(h, (void**)&h->fflux64, (size_t)h->g.nfaces * 5 * nf2 * sizeof(double));
+  if (!st && !h->bg2) st = dev_alloc(h, (void**)&h->bg2, E * 2 * np * sizeof(double));
+  if (!st && !h->bgp) st = dev_alloc(h, (void**)&h->bgp, E * 4 * np * sizeof(float));
+  if (!st && !h->rhs_bg32) st = dev_alloc(h, (void**)&h->rhs_bg32, E * 3 * np * sizeof(float));
   if (st) return st;
   double* q0 = h->qtmp;
   if (q_dev == q0) return ES_DG_EINVAL;
   cudaError_t e = esdg_launch_background(h->g, h->P, h->vgeo, q_dev, h->bg, q0, h->stream);
+  if (e == cudaSuccess)
+    e = esdg_launch_background_vol(h->g, h->P, h->vgeo, h->bg, h->bg2, h->bgp, h->stream);
   if (e != cudaSuccess) return cuda_status(e);
   if (is_partition(h)) {
     // the faces of the cut planes need the neighbours' background: evaluated at the
@@ -227,10 +241,11 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
     a.bg = nullptr;
     e = esdg_launch_volume(h->g, h->L, h->P, 0, 0, a, h->stream);
   }
-  // momentum components: rhs[e][1..3][n] -> rhs_bg[e][0..2][n]
+  // momentum components: rhs[e][1..3][n] -> rhs_bg[e][0..2][n], and its FP32 copy
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(h->rhs_bg, 3 * np * sizeof(double), h->rhs + np, 5 * np * sizeof(double),
                           3 * np * sizeof(double), E, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = esdg_launch_to_f32(h->rhs_bg, h->rhs_bg32, (long long)E * 3 * np, h->stream);
   if (e != cudaSuccess) return cuda_status(e);
   h->has_bg = 1;
   return ES_DG_OK;
@@ -259,12 +274,28 @@ int resolve_background(es_dg_t* h) {
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(h->rhs_bg, 3 * np * sizeof(double), h->rhs + np, 5 * np * sizeof(double),
                           3 * np * sizeof(double), E, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = esdg_launch_to_f32(h->rhs_bg, h->rhs_bg32, (long long)E * 3 * np, h->stream);
   if (e != cudaSuccess) return cuda_status(e);
   h->bg_pending = 0;
   return ES_DG_OK;
 }
 
 }  // namespace
+
+// The handle's status word (internal; the server reads its members' flags this
+// way): 1 if a stage update since the last call produced a non-finite state or
+// a non-positive density, 0 if not, -1 on a CUDA error.  Synchronous; clears it.
+int esdg_take_status(es_dg_t* h) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && v) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return v ? 1 : 0;
+}
 
 // Batch descriptor of a handle for the server's persistent kernels (not part of
 // the C ABI).  Mixed-precision members must carry a background.
@@ -366,7 +397,10 @@ int create_impl(const es_dg_mesh* mesh, int N, es_dg_precision precision,
     es_dg_destroy(h);
     return st;
   }
-  cudaError_t e = cudaMemsetAsync(h->dq, 0, nq * (h->mixed ? sizeof(float) : sizeof(double)), h->stream);
+  h->status = reinterpret_cast<int*>(h->result + 3);
+  cudaError_t e = cudaMemsetAsync(h->result, 0, 4 * sizeof(double), h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->dq, 0, nq * (h->mixed ? sizeof(float) : sizeof(double)), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->q, 0, nq * sizeof(double), h->stream);
   if (e == cudaSuccess) {
     if (same_geometry(geometry_of, h->g, h->P.g)) {
@@ -574,7 +608,10 @@ int es_dg_sync(es_dg_t* h) {
   if (st != ES_DG_OK) return st;
   const int t64 = esdg_volume_f64_take_timeout(), t32 = esdg_volume_mixed_take_timeout();
   if (t64 < 0 || t32 < 0) return ES_DG_ECUDA;
-  return (t64 || t32) ? ES_DG_ETIMEOUT : ES_DG_OK;
+  if (t64 || t32) return ES_DG_ETIMEOUT;
+  const int bad = esdg_take_status(h);
+  if (bad < 0) return ES_DG_ECUDA;
+  return bad ? ES_DG_ENAN : ES_DG_OK;
 }
 
 int es_dg_integrals(es_dg_t* h, double out[3]) {

@@ -109,26 +109,38 @@ __device__ __forceinline__ double esdg_rcp_lo(double x) {
   return fma(r, e, r);
 }
 
-// IEEE-754 double <-> float repacking with integer instructions (normal
-// numbers; round to nearest even; magnitudes below the float range flush to
-// zero).  cvt.f32.f64 and cvt.f64.f32 occupy the FP64 pipe on this GPU, which
-// is the bottleneck of the FP64 kernels; these run on the integer pipes and
-// agree bit for bit with cvt.rn on normal inputs (checked on 1M random values).
+// IEEE-754 double <-> float repacking with integer instructions.  cvt.f32.f64
+// and cvt.f64.f32 occupy the FP64 pipe on this GPU, which is the bottleneck of
+// the FP64 kernels; these run on the integer pipes.
+// esdg_d2f rounds to nearest even like cvt.rn.f32.f64 for every |x| < 2^128
+// whose result is a normal float (a rounding past FLT_MAX gives the signed
+// infinity); magnitudes below the float normal range flush to a signed zero.
+// Larger magnitudes, infinities and NaNs are outside its domain (the value is
+// unspecified): the kernels convert only state-derived values, which lie far
+// inside the range unless the run has diverged, and a diverged state is
+// reported by the stage update's status word (the FP64 state itself carries
+// the non-finite values), so the hot paths spend no instructions on them.
+// esdg_f2d is exact for normal floats, infinities and NaNs; zero and
+// subnormal floats give +-0.  (Both are checked against the IEEE conversions
+// by the numeric test hook.)
 __device__ __forceinline__ float esdg_d2f(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
   const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
   const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
   const unsigned rest = lo & 0x1fffffffu;
-  unsigned f = (hi & 0x80000000u) | ((unsigned)e << 23) | m;
+  const unsigned sign = hi & 0x80000000u;
+  unsigned f = sign | ((unsigned)e << 23) | m;
   f += (rest > 0x10000000u) | ((rest == 0x10000000u) & (f & 1u));
-  return (e <= 0) ? 0.0f : __uint_as_float(f);
+  return (e <= 0) ? __uint_as_float(sign) : __uint_as_float(f);
 }
 __device__ __forceinline__ double esdg_f2d(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
-  return (e == 0) ? 0.0 : __longlong_as_double((long long)(((unsigned long long)hi << 32) | (m << 29)));
+  const unsigned eb = e == 0xffu ? 0x7ffu : e + 896u;  // infinities and NaNs keep all ones
+  const unsigned hi = (u & 0x80000000u) | (eb << 20) | (m >> 3);
+  return (e == 0) ? __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32))
+                  : __longlong_as_double((long long)(((unsigned long long)hi << 32) | (m << 29)));
 }
 // x * 2^k (|k| small) with an integer add on the exponent field instead of an
 // FP64-pipe multiply: exact for normal x and normal results; infinities and
@@ -211,6 +223,13 @@ __device__ __forceinline__ void esdg_cp_async(T* dst, const T* src) {  // sizeof
 __device__ __forceinline__ void esdg_cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
+// A state value the stage update must flag: an infinity or a NaN (exponent
+// field all ones), or, for a density (dens = true), a value that is not
+// positive.  Integer tests only.
+__device__ __forceinline__ bool esdg_bad_state(double x, bool dens) {
+  const long long b = __double_as_longlong(x);
+  return ((int)(b >> 32) & 0x7ff00000) == 0x7ff00000 || (dens && b <= 0);
+}
 // x < y for non-negative doubles, compared as integers (no FP64-pipe compare)
 __device__ __forceinline__ bool esdg_lt_pos(double x, double y) {
   return __double_as_longlong(x) < __double_as_longlong(y);
@@ -287,6 +306,12 @@ cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, co
 // layer's i = N nodes into send_hi (if remote[1]), layout of EsdgTraces.
 cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, const double* bg, int nv,
                                    double* send_lo, double* send_hi, cudaStream_t s);
+// The mixed volume kernels' background copy (bg2: rho_bg, E_bg FP64; bgp:
+// rho_bg/4, b_bg/2, 1/b_bg, p_bg FP32) from the stored background bg.
+cudaError_t esdg_launch_background_vol(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
+                                       const double* bg, double* bg2, float* bgp, cudaStream_t s);
+// dst[i] = src[i] rounded to FP32, i < n
+cudaError_t esdg_launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 // The background state at rest from the stored background, per node:
 // (rho_bg, 0, 0, 0, p_bg/(gamma-1) + rho_bg phi) -- the expression the
 // background kernel uses, so the result equals its own at-rest state.
@@ -302,9 +327,12 @@ struct EsdgVolArgs {
   const double* vgeo64;  // [E][11][np] double (geopotential for the pressure recovery)
   const void* fflux;     // face fluxes, double or float
   const double* x;       // coordinates (Coriolis parameter)
-  const double* bg;      // mixed mode with a background: [E][3][np] rho_bg, b_bg, p_bg (else null)
-  const double* rhs_bg;  // mixed mode with a background: [E][3][np] FP64 momentum rhs of it
+  const double* bg;      // mixed mode with a background: [E][2][np] rho_bg, E_bg (else null)
+  const float* bgp;      // mixed mode with a background: [E][4][np] rho_bg/4, b_bg/2, 1/b_bg, p_bg
+  const float* rhs_bg;   // mixed mode with a background: [E][3][np] momentum rhs of it (FP32)
   double rkA, rkB, dt;
+  int* status;           // mode 1: set to 1 when an updated state value is not finite or a
+                         // density is not positive (null: not checked)
 };
 // One mesh of a batch: everything its kernels need, read by the persistent
 // batched kernels from a device array (one entry per resident solve).
@@ -313,7 +341,7 @@ struct EsdgMember {
   EsdgPhys P;
   EsdgVolArgs a;       // q_in == q_io: the member's state; dq, geometry, face fluxes, dt
   const double* fgeo;  // face geometry
-  const double* bg;    // mixed background or null
+  const double* bg;    // mixed background (rho_bg, b_bg, p_bg, for the faces) or null
   long long pad;
 };
 

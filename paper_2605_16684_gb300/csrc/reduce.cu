@@ -156,15 +156,23 @@ double* g_noalloc_addr[kMaxDevices] = {nullptr};
 
 // Device address of g_noalloc_partials on the current device.  In host code the
 // symbol is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
-int noalloc_scratch(double** out) {
+// cudaGetSymbolAddress with that device current.  It is looked up again on
+// every call made while the stream is not capturing (a device reset reloads
+// the module, possibly at another address); a call made during a capture uses
+// the address found by the last call outside one.
+int noalloc_scratch(cudaStream_t stream, double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return ES_DG_ECUDA;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return ES_DG_ECUDA;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_noalloc_addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -206,9 +214,12 @@ extern "C" int es_dg_integrals_noalloc(const es_dg_mesh* mesh, int N, const es_d
     P.y0 = physics->y0;
     P.dissipation = physics->dissipation;
   }
+  // the checks es_dg_create applies: a bad gas constant would make every
+  // integral NaN without any error being reported
+  if (!(P.gamma > 1.0) || !(P.R > 0.0) || !(P.p0 > 0.0)) return ES_DG_EINVAL;
   esdg_phys_derive(&P);
   double* scratch = nullptr;
-  int st = noalloc_scratch(&scratch);
+  int st = noalloc_scratch((cudaStream_t)cuda_stream, &scratch);
   if (st) return st;
   // every partial the fold reads (the first E triples) is written by this
   // call, so nothing needs clearing between calls

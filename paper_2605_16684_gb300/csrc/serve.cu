@@ -61,6 +61,7 @@ struct Member {
   double t_submit = 0, t_admit = 0, t_finish = 0;
   size_t bytes = 0;
   long long ndof = 0;
+  int failed = 0;  // ES_DG_ENAN once its state was flagged: finished early, alone
 };
 
 struct Group {
@@ -76,6 +77,15 @@ struct Group {
 
 struct Result {
   es_dg_result r{};
+};
+
+// es_dg_server_warmup's request to the scheduler thread (lives on the caller's
+// stack until done is set)
+struct WarmJob {
+  std::vector<int> orders;
+  int mixed = 0;
+  int status = 0;
+  bool done = false;
 };
 
 size_t estimate_bytes(const es_dg_request& q) {
@@ -100,6 +110,7 @@ struct es_dg_server {
   std::vector<std::unique_ptr<Member>> active;
   std::map<uint64_t, Result> done;
   std::map<uint64_t, int> cancelled;
+  std::deque<WarmJob*> warm_jobs;
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread worker;
@@ -108,6 +119,12 @@ struct es_dg_server {
   EsdgMember* d_members = nullptr;
   int cap_members = 0;
   std::vector<EsdgMember> h_members;
+  // per-member status words of the descriptor table (set by a stage update whose
+  // state is not finite or has a non-positive density), polled every few steps
+  int* d_flags = nullptr;
+  int* h_flags = nullptr;  // pinned
+  int n_table = 0;         // members in the uploaded table (the first n_table of active)
+  int steps_since_poll = 0;
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
   int use_graph = 1;
@@ -174,18 +191,31 @@ int upload(es_dg_server* s) {
   const int nm = (int)s->active.size();
   if (nm > s->cap_members) {
     if (s->d_members) cudaFree(s->d_members);
+    if (s->d_flags) cudaFree(s->d_flags);
+    if (s->h_flags) cudaFreeHost(s->h_flags);
+    s->d_flags = nullptr;
+    s->h_flags = nullptr;
     s->cap_members = std::max(nm, 2 * s->cap_members);
-    if (cudaMalloc(&s->d_members, sizeof(EsdgMember) * s->cap_members) != cudaSuccess) {
+    if (cudaMalloc(&s->d_members, sizeof(EsdgMember) * s->cap_members) != cudaSuccess ||
+        cudaMalloc(&s->d_flags, sizeof(int) * s->cap_members) != cudaSuccess ||
+        cudaMallocHost(&s->h_flags, sizeof(int) * s->cap_members) != cudaSuccess) {
       cudaGetLastError();
+      if (s->d_members) cudaFree(s->d_members);
+      if (s->d_flags) cudaFree(s->d_flags);
       s->d_members = nullptr;
+      s->d_flags = nullptr;
+      s->h_flags = nullptr;
       s->cap_members = 0;
       return ES_DG_ENOMEM;
     }
     s->graph_valid = false;
   }
+  for (int m = 0; m < nm; m++) s->h_members[m].a.status = s->d_flags + m;
+  s->n_table = nm;
   if (nm) {
     cudaError_t e = cudaMemcpyAsync(s->d_members, s->h_members.data(), sizeof(EsdgMember) * nm,
                                     cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_flags, 0, sizeof(int) * nm, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "member upload");
   }
   for (Group& g : s->groups) {
@@ -310,6 +340,21 @@ int rebuild(es_dg_server* s) {
       s->graph_valid = false;
     }
   }
+  // groups left without members are dropped (their tuning stays in s->tuned)
+  for (size_t gi = 0; gi < s->groups.size();) {
+    Group& g = s->groups[gi];
+    bool any = false;
+    for (auto& m : s->active) any |= (m->N == g.N && m->mixed == g.mixed);
+    if (any) {
+      gi++;
+      continue;
+    }
+    if (g.d_vt) cudaFree(g.d_vt);
+    if (g.d_ft) cudaFree(g.d_ft);
+    if (g.d_n) cudaFree(g.d_n);
+    s->groups.erase(s->groups.begin() + gi);
+    s->graph_valid = false;
+  }
   for (Group& g : s->groups) {
     if (g.variant < 0) {
       // first time: tune on the members present (tables are built inside)
@@ -407,7 +452,7 @@ int admit_one(es_dg_server* s, Member& m) {
   } else {
     st = es_dg_init_channel(m.h);
   }
-  if (!st) st = es_dg_cfl_dt(m.h, q.cfl > 0 ? q.cfl : 0.5, &m.dt);
+  if (!st) st = es_dg_cfl_dt(m.h, q.cfl > 0 ? q.cfl : ES_DG_SERVER_DEFAULT_CFL, &m.dt);
   if (st) {
     std::snprintf(s->msg, sizeof(s->msg), "initial state: %s", es_dg_strerror(st));
     es_dg_destroy(m.h);
@@ -419,6 +464,62 @@ int admit_one(es_dg_server* s, Member& m) {
   m.N = q.N;
   m.mixed = (q.precision == ES_DG_FP32_MIXED);
   m.ndof = info.ndof;
+  return ES_DG_OK;
+}
+
+// Tune the group (N, mixed) on a representative member that is created,
+// timed and discarded (es_dg_server_warmup).  Worker thread.
+int warm_one(es_dg_server* s, int N, int mixed) {
+  const long long key = N * 2 + mixed;
+  if (s->tuned.count(key)) return ES_DG_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto jt = g_tuned.find(((long long)s->device << 8) | key);
+    if (jt != g_tuned.end()) {
+      s->tuned[key] = jt->second;
+      return ES_DG_OK;
+    }
+  }
+  auto m = std::make_unique<Member>();
+  es_dg_request& q = m->req;
+  q.kind = 0;
+  q.kx = q.ky = q.kz = N <= 4 ? 16 : 8;
+  q.N = N;
+  q.precision = mixed ? ES_DG_FP32_MIXED : ES_DG_FP64;
+  q.cfl = ES_DG_SERVER_DEFAULT_CFL;
+  q.amp = 0.5;
+  q.centre[0] = q.centre[1] = 500.0;
+  q.centre[2] = 350.0;
+  q.radius = 250.0;
+  q.theta0 = 300.0;
+  q.warp = 0.05;
+  int st = admit_one(s, *m);
+  if (st) return st;
+  s->active.push_back(std::move(m));
+  st = rebuild(s);  // creates the group and tunes it on this member
+  es_dg_destroy(s->active.back()->h);
+  s->active.pop_back();
+  const int st2 = rebuild(s);  // the tables of the members that stay
+  return st ? st : st2;
+}
+
+// Read the members' status words (synchronous): a member whose state went
+// non-finite (or its density non-positive) is marked to finish with
+// ES_DG_ENAN; the others go on.
+int poll_flags(es_dg_server* s) {
+  s->steps_since_poll = 0;
+  const int n = std::min(s->n_table, (int)s->active.size());
+  if (n == 0 || !s->d_flags) return ES_DG_OK;
+  cudaError_t e = cudaMemcpyAsync(s->h_flags, s->d_flags, sizeof(int) * n, cudaMemcpyDeviceToHost,
+                                  s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "status poll");
+  for (int m = 0; m < n; m++)
+    if (s->h_flags[m] && !s->active[m]->failed) {
+      s->active[m]->failed = ES_DG_ENAN;
+      std::snprintf(s->msg, sizeof(s->msg), "request %llu: non-finite state after step %d",
+                    (unsigned long long)s->active[m]->ticket, s->active[m]->steps_done);
+    }
   return ES_DG_OK;
 }
 
@@ -457,9 +558,22 @@ void worker(es_dg_server* s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv.wait_for(lk, std::chrono::milliseconds(s->active.empty() ? 50 : 0), [&] {
-        return s->stop || !s->pending.empty() || !s->active.empty();
+        return s->stop || !s->pending.empty() || !s->active.empty() || !s->warm_jobs.empty();
       });
-      if (s->stop && s->pending.empty() && s->active.empty()) break;
+      if (s->stop && s->pending.empty() && s->active.empty() && s->warm_jobs.empty()) break;
+      // warm-up jobs first (the callers wait for them)
+      while (!s->warm_jobs.empty()) {
+        WarmJob* job = s->warm_jobs.front();
+        s->warm_jobs.pop_front();
+        lk.unlock();
+        int st = ES_DG_OK;
+        for (int N : job->orders)
+          if (!st) st = warm_one(s, N, job->mixed);
+        lk.lock();
+        job->status = st;
+        job->done = true;
+        s->cv.notify_all();
+      }
       // FIFO admission by HBM footprint and slots
       while (!s->pending.empty()) {
         Member& head = *s->pending.front();
@@ -489,10 +603,19 @@ void worker(es_dg_server* s) {
       for (auto& m : s->active)
         if (s->cancelled.count(m->ticket)) m->req.nsteps = m->steps_done;  // finish now
     }
+    // status words: before any member of the table retires, and every 16 steps
+    {
+      bool due = s->steps_since_poll >= 16;
+      for (int m = 0; m < s->n_table && m < (int)s->active.size() && !due; m++)
+        due = s->active[m]->steps_done >= s->active[m]->req.nsteps;
+      if (due && poll_flags(s) == ES_DG_OK)
+        for (auto& m : s->active)
+          if (m->failed) m->req.nsteps = m->steps_done;  // finish now, alone
+    }
     // retire members that reached their step count
     for (size_t i = 0; i < s->active.size();) {
       if (s->active[i]->steps_done >= s->active[i]->req.nsteps) {
-        int status = ES_DG_OK;
+        int status = s->active[i]->failed ? s->active[i]->failed : ES_DG_OK;
         {
           std::lock_guard<std::mutex> lk(s->mu);
           if (s->cancelled.count(s->active[i]->ticket)) status = ES_DG_ECANCELED;
@@ -525,6 +648,7 @@ void worker(es_dg_server* s) {
       continue;
     }
     for (auto& m : s->active) m->steps_done++;
+    s->steps_since_poll++;
     std::lock_guard<std::mutex> lk(s->mu);
     s->st.steps++;
     s->st.launch_seconds += now_s() - ts;
@@ -570,6 +694,24 @@ int es_dg_server_create(size_t hbm_budget_bytes, int max_slots, void* cuda_strea
   s->worker = std::thread(worker, s);
   *out = s;
   return ES_DG_OK;
+}
+
+int es_dg_server_warmup(es_dg_server* s, const int* orders, int n_orders,
+                        es_dg_precision precision) {
+  if (!s || n_orders < 0 || (n_orders > 0 && !orders)) return ES_DG_EINVAL;
+  if (precision != ES_DG_FP64 && precision != ES_DG_FP32_MIXED) return ES_DG_EINVAL;
+  WarmJob job;
+  for (int i = 0; i < n_orders; i++) {
+    if (orders[i] < 1 || orders[i] > 7) return ES_DG_EINVAL;
+    job.orders.push_back(orders[i]);
+  }
+  job.mixed = precision == ES_DG_FP32_MIXED;
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->stop) return ES_DG_EINVAL;
+  s->warm_jobs.push_back(&job);
+  s->cv.notify_all();
+  s->cv.wait(lk, [&] { return job.done; });
+  return job.status;
 }
 
 int es_dg_batch_submit(es_dg_server* s, const es_dg_request* req, uint64_t* ticket) {
@@ -681,6 +823,8 @@ void es_dg_server_destroy(es_dg_server* s) {
     if (g.d_n) cudaFree(g.d_n);
   }
   if (s->d_members) cudaFree(s->d_members);
+  if (s->d_flags) cudaFree(s->d_flags);
+  if (s->h_flags) cudaFreeHost(s->h_flags);
   if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
 }

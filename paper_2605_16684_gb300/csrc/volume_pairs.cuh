@@ -384,19 +384,12 @@ __device__ __forceinline__ bool out_of_series64(const double* S, int n) {
   return fabsf(rn - r0) > 0.0095f * r0 || fabsf(bn - b0) > 0.0095f * b0;
 }
 
-// Mixed-precision node prologue: FP32 primitives, the pressure recovered in
-// FP64 (E - rho phi cancels there) and, with a background, the FP64
-// perturbations rho' = rho - rho_bg and p' = p - p_bg rounded to FP32; the
-// perturbation of b = rho/(2p) follows exactly from them,
-//   b - b_bg = (rho' p_bg - rho_bg p') / (2 p p_bg),
-// evaluated in FP32 (its rounding is relative to the perturbations).  phh is
-// the geopotential relative to the element's first node, halved (FP32
-// geometry).  5 FP64 instructions per node with a background.
-template <int NP, bool BG>
+// Mixed-precision node prologue without a background: FP32 primitives, the
+// pressure recovered in FP64 (E - rho phi cancels there).  phh is the
+// geopotential relative to the element's first node, halved (FP32 geometry).
+template <int NP>
 __device__ __forceinline__ void prims32(double q0, double q1, double q2, double q3, double q4,
-                                        double phi, float phh, double gm1, float* S, int n,
-                                        double rb = 0.0, double bb = 0.0, double pbg = 0.0,
-                                        float* Bf = nullptr) {
+                                        double phi, float phh, double gm1, float* S, int n) {
   const float q0f = esdg_d2f(q0), q1f = esdg_d2f(q1), q2f = esdg_d2f(q2), q3f = esdg_d2f(q3);
   const float irf = esdg_rcpf(q0f);
   const float hf = 0.5f * irf;
@@ -412,33 +405,73 @@ __device__ __forceinline__ void prims32(double q0, double q1, double q2, double 
   S[4 * NP + n] = u1;
   S[5 * NP + n] = u2;
   S[6 * NP + n] = phh;
-  if constexpr (BG) {
-    const float rpf = esdg_d2f(q0 - rb), ppf = esdg_d2f(p - pbg);
-    const float rbf = esdg_d2f(rb), bbf = esdg_d2f(bb), pbf = esdg_d2f(pbg);
-    Bf[0 * NP + n] = 0.25f * rpf;
-    Bf[1 * NP + n] = 0.25f * fmaf(rpf, pbf, -rbf * ppf) * esdg_rcpf(pf * pbf);  // b'/2
-    Bf[2 * NP + n] = 0.25f * rbf;
-    Bf[3 * NP + n] = 0.5f * bbf;
-    Bf[4 * NP + n] = esdg_rcpf(bbf);
-    Bf[5 * NP + n] = pbf;
-    Bf[6 * NP + n] = ppf;
-  }
+}
+
+// The node fields of the FP32 pair loop relative to a hydrostatic background
+// (Shape field order): s[0..6] = rho/4, b/2, 1/b, u/2 (3), phi_rel/2 and
+// bgf[0..6] = rho'/4, b'/2, rho_bg/4, b_bg/2, 1/b_bg, p_bg, p'.
+struct Prim32 {
+  float s[7], bgf[7];
+};
+// Inputs: the FP64 state, phi (FP64) and phh = (phi - phi_0)/2 (FP32), the
+// background's rho_bg and E_bg = p_bg/(gamma-1) + rho_bg phi (FP64) and its
+// FP32 fields rqb = rho_bg/4, bhb = b_bg/2, ibb = 1/b_bg, pbf = p_bg.  FP64
+// only where the state cancels against the background, three instructions:
+//   rho' = rho - rho_bg,  E' = E - E_bg,  e' = E' - phi rho',
+// then in FP32 (rounding relative to the perturbations, or to FP32 accuracy
+// of fields that need no more):  rho and rho u rounded once, u = (rho u)/rho,
+// p' = (gamma - 1)(e' - |rho u|^2/(2 rho)), p = p_bg + p', b = rho/(2p) and
+//   b - b_bg = (rho' p_bg - rho_bg p') / (2 p p_bg)
+// (exact identity, its rounding relative to the perturbations).
+__device__ __forceinline__ Prim32 prims32bg(double q0, double q1, double q2, double q3, double q4,
+                                            double phi, float phh, float gm1f, double rb,
+                                            double eb, float rqb, float bhb, float ibb,
+                                            float pbf) {
+  const double rp = q0 - rb;
+  const double ep = fma(-phi, rp, q4 - eb);
+  const float rpf = esdg_d2f(rp), epf = esdg_d2f(ep);
+  const float q0f = esdg_d2f(q0), q1f = esdg_d2f(q1), q2f = esdg_d2f(q2), q3f = esdg_d2f(q3);
+  const float irf = esdg_rcpf(q0f);
+  const float hf = 0.5f * irf;
+  const float u0 = q1f * hf, u1 = q2f * hf, u2 = q3f * hf;
+  const float ke = fmaf(q3f, u2, fmaf(q2f, u1, q1f * u0));
+  const float ppf = gm1f * (epf - ke);
+  const float pf = pbf + ppf;
+  const float rq = 0.25f * q0f;
+  Prim32 o;
+  o.s[0] = rq;
+  o.s[1] = rq * esdg_rcpf(pf);
+  o.s[2] = 2.0f * pf * irf;
+  o.s[3] = u0;
+  o.s[4] = u1;
+  o.s[5] = u2;
+  o.s[6] = phh;
+  o.bgf[0] = 0.25f * rpf;
+  o.bgf[1] = fmaf(rpf, pbf, -4.0f * rqb * ppf) * esdg_rcpf(4.0f * pf * pbf);  // b'/2
+  o.bgf[2] = rqb;
+  o.bgf[3] = bhb;
+  o.bgf[4] = ibb;
+  o.bgf[5] = pbf;
+  o.bgf[6] = ppf;
+  return o;
 }
 
 // Mixed-precision stage update of one node: r = -(1/J) (volume + lifts) in
-// FP32, plus the background's right-hand side and the Coriolis source, all in
-// FP32 (they join an FP32 increment); FP64 only in q += B dq.  Arrays are per
-// node with stride NP between variables: rbg (3, background rhs), qin (5),
+// FP32, plus the background's right-hand side (stored in FP32) and the
+// Coriolis source, all in FP32 (they join an FP32 increment); FP64 only in
+// q += B dq.  Arrays are per node with stride NP between variables: rbg (3,
+// background momentum rhs), qin (5),
 // dqold (5) may be in shared or global memory; dq and qio are the node's
-// global locations.
+// global locations.  Returns true if the updated state is not finite or its
+// density is not positive.
 template <int NP, bool BG>
-__device__ __forceinline__ void stage32(float (&r)[5], const double* rbg, const EsdgPhys& P,
+__device__ __forceinline__ bool stage32(float (&r)[5], const float* rbg, const EsdgPhys& P,
                                         double y, const double* qin, const float* dqold, float* dq,
                                         double* qio, double rkA, double rkB, double dt) {
   if constexpr (BG) {
-    r[1] += esdg_d2f(rbg[0]);
-    r[2] += esdg_d2f(rbg[NP]);
-    r[3] += esdg_d2f(rbg[2 * NP]);
+    r[1] += rbg[0];
+    r[2] += rbg[NP];
+    r[3] += rbg[2 * NP];
   }
   if ((P.f0 != 0.0) || (P.beta != 0.0)) {
     const float f = esdg_d2f(P.f0 + P.beta * (y - P.y0));
@@ -446,12 +479,18 @@ __device__ __forceinline__ void stage32(float (&r)[5], const double* rbg, const 
     r[2] = fmaf(-f, esdg_d2f(qin[NP]), r[2]);
   }
   const float A = esdg_d2f(rkA), B = esdg_d2f(rkB), dtf = esdg_d2f(dt);
+  bool bad = false;
 #pragma unroll
   for (int v = 0; v < 5; v++) {
-    const float dv = fmaf(A, dqold[(size_t)v * NP], dtf * r[v]);
+    // the first stage (A = 0) does not read the register: a register left
+    // non-finite by an earlier diverged run must not poison a new one
+    const float dv = A == 0.0f ? dtf * r[v] : fmaf(A, dqold[(size_t)v * NP], dtf * r[v]);
     dq[(size_t)v * NP] = dv;
-    qio[(size_t)v * NP] = qin[(size_t)v * NP] + esdg_f2d(B * dv);
+    const double qn = qin[(size_t)v * NP] + esdg_f2d(B * dv);
+    qio[(size_t)v * NP] = qn;
+    bad |= esdg_bad_state(qn, v == 0);
   }
+  return bad;
 }
 
 }  // namespace esdg_vol

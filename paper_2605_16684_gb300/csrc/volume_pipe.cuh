@@ -24,8 +24,49 @@ namespace esdg_vol {
 // translation unit; read and cleared through es_dg_sync)
 static __device__ int g_esdg_vol_timeout;
 static_assert(sizeof(EsdgMember) % 16 == 0, "descriptors are bulk-copied");
+// Leaving a CTA on a timeout.  A timeout of the first barrier (this tile's
+// data) happens before any other copy of the tile is issued.  A timeout of the
+// second (this tile's dq) happens after the next tile's bulk copies were issued
+// on the first barrier; they may still be landing in this CTA's shared memory,
+// so one thread waits for them (bounded, the same limit) before the CTA exits
+// and its shared memory can be handed to another CTA.  The issuing lanes'
+// cp.async tails were already waited for before the second barrier.
+__device__ __forceinline__ void pipe_drain(unsigned long long* bar, unsigned parity, bool issued) {
+  if (issued) esdg_mbar_wait(bar, parity, ESDG_WAIT_LIMIT);
+}
 // dynamic shared memory a pipelined tile may use (227 KB less static use)
 #define ESDG_PIPE_SMEM_MAX (232448 - 1024)
+
+// Tile shape of the pipelined kernels: elements per tile (EPB) and the CTAs
+// the launch bounds plan per SM (MINB).  With MINB = 2 two CTAs share an SM,
+// so one CTA's FP64 prologue and epilogue run under the other's pair pass.
+#ifndef ESDG_PIPE4_EPB64
+#define ESDG_PIPE4_EPB64 5
+#endif
+#ifndef ESDG_PIPE4_MINB64
+#define ESDG_PIPE4_MINB64 1
+#endif
+#ifndef ESDG_PIPE4_EPB32
+#define ESDG_PIPE4_EPB32 5
+#endif
+#ifndef ESDG_PIPE4_MINB32
+#define ESDG_PIPE4_MINB32 1
+#endif
+template <int N, bool MIXED>
+struct PipeCfg {
+  static constexpr int EPB = Cfg<N, MIXED>::EPB, MINB = 1;
+};
+template <>
+struct PipeCfg<4, false> {
+  static constexpr int EPB = ESDG_PIPE4_EPB64, MINB = ESDG_PIPE4_MINB64;
+};
+template <>
+struct PipeCfg<4, true> {
+  static constexpr int EPB = ESDG_PIPE4_EPB32, MINB = ESDG_PIPE4_MINB32;
+};
+// the pipelined kernels' Shape (the mixed one carries the background fields)
+template <int N, bool MIXED>
+using PipeShape = Shape<N, MIXED, MIXED, PipeCfg<N, MIXED>::EPB>;
 
 // The tile with index t: (member, first element, elements).  TABLE: from the
 // work table (EPB elements, fewer at a member's end).  SINGLE: EPB-element
@@ -60,7 +101,7 @@ struct PipeCtl {
 
 template <int N, int MODE>
 struct Pipe64 {
-  using SH = Shape<N, false, false>;
+  using SH = PipeShape<N, false>;
   static constexpr int P = SH::NP * SH::EPB;  // nodes per tile
   static constexpr int even(int x) { return (x + 1) & ~1; }
   // offsets in doubles, all even (16-byte aligned); each copy target holds
@@ -165,12 +206,12 @@ __device__ __forceinline__ void pipe_issue(int tid, const BlockCopy (&bl)[MAXB],
 }
 
 template <int N, int MODE, bool TABLE>
-__global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
+__global__ void __launch_bounds__(PipeShape<N, false>::THREADS, PipeCfg<N, false>::MINB)
     k_volume_pipe64(const EsdgMember one, const EsdgMember* __restrict__ members,
                     const int2* __restrict__ tiles, const int* __restrict__ ntiles_d, int ntiles_1,
                     EsdgLGL L, double rkA, double rkB, unsigned phantom, int t1, int s1) {
   static_assert(!TABLE || MODE == 1, "the batched kernel applies an RK stage");
-  using SH = Shape<N, false, false>;
+  using SH = PipeShape<N, false>;
   using PP = Pipe64<N, MODE>;
   constexpr int Nq = SH::Nq, NP = SH::NP, NPEN = SH::NPEN, EPB = SH::EPB, NF = SH::NF;
   constexpr int T = SH::THREADS;
@@ -339,7 +380,10 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
       const bool okd = esdg_mbar_wait(&ctl.bars[1], ph_cur, ESDG_WAIT_LIMIT);  // this tile's dq
       ph_cur ^= 1u;
       if (__syncthreads_or(!okd)) {
-        if (tid == 0) atomicExch(&g_esdg_vol_timeout, 1);
+        if (tid == 0) {
+          atomicExch(&g_esdg_vol_timeout, 1);
+          pipe_drain(&ctl.bars[0], ph_raw, next < ntiles);
+        }
         return;
       }
     } else {
@@ -357,6 +401,8 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
     double* const dqp = reinterpret_cast<double*>(a.dq);
     double* const qio = a.q_io;
     double* const rhsp = a.rhs;
+    int* const status = a.status;
+    bool bad = false;
     for (int idx = tid; idx < 5 * EPB * NP; idx += T) {
       const int v = idx / (EPB * NP), rem = idx - v * (EPB * NP);
       const int el2 = rem / NP, n = rem - el2 * NP, e2 = e0 + el2;
@@ -374,18 +420,22 @@ __global__ void __launch_bounds__(Shape<N, false, false>::THREADS, 1)
       if constexpr (MODE == 0) {
         rhsp[qv] = r;
       } else {
-        const double dv = fma(rkA, D0[((size_t)el2 * 5 + v) * NP + n], r);
+        // first stage (A = 0): the register is not read (see stage32)
+        const double dv = rkA == 0.0 ? r : fma(rkA, D0[((size_t)el2 * 5 + v) * NP + n], r);
         dqp[qv] = dv;
-        qio[qv] = fma(rkB, dv, X[v * NP + n]);
+        const double qn = fma(rkB, dv, X[v * NP + n]);
+        qio[qv] = qn;
+        bad |= esdg_bad_state(qn, v == 0);
       }
     }
+    if (MODE != 0 && bad && status) *status = 1;
   }
 }
 
 // ---- pipelined persistent mixed-precision kernel (with a background) ------
 template <int N, int MODE>
 struct Pipe32 {
-  using SH = Shape<N, true, true>;
+  using SH = PipeShape<N, true>;
   static constexpr int NP = SH::NP, EPB = SH::EPB, P = NP * EPB;
   static constexpr int up16(int b) { return (b + 15) & ~15; }
   static constexpr int PHS = (NP + 4) & ~1;  // even per-element stride: every target 16-byte aligned
@@ -393,51 +443,52 @@ struct Pipe32 {
   // aligned span around each block)
   static constexpr int RAW_Q = 0;                                  // [el][5][NP]  double
   static constexpr int RAW_PHI = up16(RAW_Q + 8 * (5 * P + 4));    // [el][PHS]    double
-  static constexpr int RAW_BG = up16(RAW_PHI + 8 * EPB * PHS);     // [el][3][NP]  double
-  static constexpr int RAW_G = up16(RAW_BG + 8 * (3 * P + 4));     // [el][11][NP] float
+  static constexpr int RAW_BG = up16(RAW_PHI + 8 * EPB * PHS);     // [el][2][NP]  double rho_bg, E_bg
+  static constexpr int RAW_BGP = up16(RAW_BG + 8 * (2 * P + 4));   // [el][4][NP]  float background fields
+  static constexpr int RAW_G = up16(RAW_BGP + 4 * (4 * P + 8));    // [el][11][NP] float
   static constexpr int S0 = up16(RAW_G + 4 * (ESDG_NVGEO * P + 8));  // [el][NF][NP] float
   static constexpr int EPI_Q = up16(S0 + 4 * SH::NF * P);         // [el][5][NP]  double
   static constexpr int EPI_J = up16(EPI_Q + 8 * 5 * P);           // [el][NP]     float
-  static constexpr int CUR_RB = up16(EPI_J + 4 * P);              // [el][3][NP]  double
-  static constexpr int CUR_DQ = up16(CUR_RB + 8 * (3 * P + 4));   // [el][5][NP]  float
+  static constexpr int CUR_RB = up16(EPI_J + 4 * P);              // [el][3][NP]  float
+  static constexpr int CUR_DQ = up16(CUR_RB + 4 * (3 * P + 8));   // [el][5][NP]  float
   static constexpr int TOTAL = MODE ? up16(CUR_DQ + 4 * (5 * P + 8)) : CUR_DQ;
   static constexpr size_t SMEM = (size_t)TOTAL;
 };
 
 template <int N, int MODE, bool TABLE>
-__global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
+__global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>::MINB)
     k_volume_pipe32(const EsdgMember one, const EsdgMember* __restrict__ members,
                     const int2* __restrict__ tiles, const int* __restrict__ ntiles_d, int ntiles_1,
                     EsdgLGL L, double rkA, double rkB, unsigned phantom, int t1, int s1) {
   static_assert(!TABLE || MODE == 1, "the batched kernel applies an RK stage");
-  using SH = Shape<N, true, true>;
+  using SH = PipeShape<N, true>;
   using PP = Pipe32<N, MODE>;
   constexpr int Nq = SH::Nq, NP = SH::NP, NPEN = SH::NPEN, EPB = SH::EPB, NF = SH::NF;
   constexpr int T = SH::THREADS;
+  constexpr int NN = EPB * NP;  // nodes of a tile
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ __align__(16) PipeCtl<TABLE> ctl;
   __shared__ float phi0s[EPB];  // each element's reference geopotential
   double* const rawq = reinterpret_cast<double*>(smraw + PP::RAW_Q);
   double* const rawphi = reinterpret_cast<double*>(smraw + PP::RAW_PHI);
   double* const rawbg = reinterpret_cast<double*>(smraw + PP::RAW_BG);
+  float* const rawbgp = reinterpret_cast<float*>(smraw + PP::RAW_BGP);
   float* const rawg = reinterpret_cast<float*>(smraw + PP::RAW_G);
   float* const sm = reinterpret_cast<float*>(smraw + PP::S0);
   double* const epq = reinterpret_cast<double*>(smraw + PP::EPI_Q);
   float* const epj = reinterpret_cast<float*>(smraw + PP::EPI_J);
-  double* const currb = reinterpret_cast<double*>(smraw + PP::CUR_RB);
+  float* const currb = reinterpret_cast<float*>(smraw + PP::CUR_RB);
   float* const curdq = reinterpret_cast<float*>(smraw + PP::CUR_DQ);
   const int tid = threadIdx.x;
   const int ntiles = TABLE ? *ntiles_d : ntiles_1;
 
-  auto phi_src = [](const EsdgMember* M, int e) {
-    return M->a.vgeo64 + ((size_t)e * ESDG_NVGEO + 10) * NP;
-  };
   using ISS = Issuers<T, SH::PENCILS>;
   struct Next {
     int4 tr;  // (member, first element, elements)
     int E;
     const double* q;
     const double* bg;
+    const float* bgp;
     const float* vg;
     const double* v64;
     const EsdgMember* Mg;
@@ -450,6 +501,7 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     x.tr = pipe_tile<TABLE, EPB>(tiles, t, t1, s1, x.E);
     x.q = x.Mg->a.q_in;
     x.bg = x.Mg->a.bg;
+    x.bgp = x.Mg->a.bgp;
     x.vg = reinterpret_cast<const float*>(x.Mg->a.vgeo);
     x.v64 = x.Mg->a.vgeo64;
     return x;
@@ -459,19 +511,20 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     if (tid == ISS::FIRST) ctl.info[s] = x.tr;
     const int e0 = x.tr.y, ne = x.tr.z;
     const double* v64end = x.v64 + (size_t)x.E * ESDG_NVGEO * NP;
-    BlockCopy bl[3 + EPB];
+    BlockCopy bl[4 + EPB];
     bl[0] = {rawq, x.q + (size_t)e0 * 5 * NP, x.q + (size_t)x.E * 5 * NP, ne * 5 * NP, 8};
-    bl[1] = {rawbg, x.bg + (size_t)e0 * 3 * NP, x.bg + (size_t)x.E * 3 * NP, ne * 3 * NP, 8};
-    bl[2] = {rawg, x.vg + (size_t)e0 * ESDG_NVGEO * NP, x.vg + (size_t)x.E * ESDG_NVGEO * NP,
+    bl[1] = {rawbg, x.bg + (size_t)e0 * 2 * NP, x.bg + (size_t)x.E * 2 * NP, ne * 2 * NP, 8};
+    bl[2] = {rawbgp, x.bgp + (size_t)e0 * 4 * NP, x.bgp + (size_t)x.E * 4 * NP, ne * 4 * NP, 4};
+    bl[3] = {rawg, x.vg + (size_t)e0 * ESDG_NVGEO * NP, x.vg + (size_t)x.E * ESDG_NVGEO * NP,
              ne * ESDG_NVGEO * NP, 4};
 #pragma unroll
     for (int el = 0; el < EPB; el++)
-      bl[3 + el] = {rawphi + (size_t)el * PP::PHS, x.v64 + ((size_t)(e0 + el) * ESDG_NVGEO + 10) * NP,
+      bl[4 + el] = {rawphi + (size_t)el * PP::PHS, x.v64 + ((size_t)(e0 + el) * ESDG_NVGEO + 10) * NP,
                     v64end, el < ne ? NP : 0, 8};
     if constexpr (TABLE)
-      pipe_issue<ISS>(tid, bl, 3 + EPB, &ctl.bars[0], (unsigned)sizeof(EsdgMember), x.Mg, &ctl.desc[s], ph);
+      pipe_issue<ISS>(tid, bl, 4 + EPB, &ctl.bars[0], (unsigned)sizeof(EsdgMember), x.Mg, &ctl.desc[s], ph);
     else
-      pipe_issue<ISS>(tid, bl, 3 + EPB, &ctl.bars[0], 0, nullptr, nullptr, ph);
+      pipe_issue<ISS>(tid, bl, 4 + EPB, &ctl.bars[0], 0, nullptr, nullptr, ph);
   };
 
   if (tid == 0) {
@@ -504,55 +557,97 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     if (ISS::is(tid)) {
       const float* dqg = reinterpret_cast<const float*>(a.dq);
       const BlockCopy cb[2] = {
-          {currb, a.rhs_bg + (size_t)e0 * 3 * NP, a.rhs_bg + (size_t)E * 3 * NP, ne * 3 * NP, 8},
+          {currb, a.rhs_bg + (size_t)e0 * 3 * NP, a.rhs_bg + (size_t)E * 3 * NP, ne * 3 * NP, 4},
           {curdq, dqg + (size_t)e0 * 5 * NP, dqg + (size_t)E * 5 * NP, MODE ? ne * 5 * NP : 0, 4}};
       pipe_issue<ISS>(tid, cb, 2, &ctl.bars[1]);
       if (TABLE && next < ntiles) nx = fetch(next);  // global loads: early
     }
-    // ---- prologue (descriptor fields held in registers: the shared-memory
-    // stores below would otherwise force their reloads) -----------------------
+    // ---- prologue, two nodes per thread and round (their FP64 chains and
+    // loads interleave; descriptor fields held in registers: the shared-memory
+    // stores below would otherwise force their reloads) ----------------------
     {
-      const double gm1 = P.gamma - 1.0;
+      const float gm1f = esdg_d2f(P.gamma - 1.0);
       const float* vg = reinterpret_cast<const float*>(a.vgeo);
       const double* v64 = a.vgeo64;
       const double* qr0 = rawq + esdg_block_shift(a.q_in + (size_t)e0 * 5 * NP);
-      const double* br0 = rawbg + esdg_block_shift(a.bg + (size_t)e0 * 3 * NP);
+      const double* br0 = rawbg + esdg_block_shift(a.bg + (size_t)e0 * 2 * NP);
+      const float* pr0 = rawbgp + esdg_block_shift(a.bgp + (size_t)e0 * 4 * NP);
       const float* gr0 = rawg + esdg_block_shift(vg + (size_t)e0 * ESDG_NVGEO * NP);
-      for (int idx = tid; idx < EPB * NP; idx += T) {
-        const int el2 = idx / NP, n = idx - el2 * NP;
-        float* S = sm + (size_t)el2 * NF * NP;
-        if (el2 < ne) {
-          const double* qr = qr0 + (size_t)el2 * 5 * NP;
-          const double* br = br0 + (size_t)el2 * 3 * NP;
-          const float* gr = gr0 + (size_t)el2 * ESDG_NVGEO * NP;
-          const double* phr = rawphi + (size_t)el2 * PP::PHS +
-                              esdg_block_shift(v64 + ((size_t)(e0 + el2) * ESDG_NVGEO + 10) * NP);
-          const double q0 = qr[n], q1 = qr[NP + n], q2 = qr[2 * NP + n], q3 = qr[3 * NP + n],
-                       q4 = qr[4 * NP + n];
-          prims32<NP, true>(q0, q1, q2, q3, q4, phr[n], gr[10 * NP + n], gm1, S, n, br[n],
-                            br[NP + n], br[2 * NP + n], S + SH::F_BG * NP);
-          if (n == 0) phi0s[el2] = esdg_d2f(phr[0]);
+      struct In {
+        double q0, q1, q2, q3, q4, rb, eb, phi;
+        float b0, b1, b2, b3, phh;
+        int el, n;
+        bool live, any;
+      };
+      auto load = [&](int idx) {
+        In x;
+        x.any = idx < NN;
+        x.el = idx / NP;
+        x.n = idx - x.el * NP;
+        x.live = x.any && x.el < ne;
+        const int el = x.live ? x.el : 0, n = x.live ? x.n : 0;
+        const double* qr = qr0 + (size_t)el * 5 * NP + n;
+        const double* br = br0 + (size_t)el * 2 * NP + n;
+        const float* pr = pr0 + (size_t)el * 4 * NP + n;
+        x.q0 = qr[0];
+        x.q1 = qr[NP];
+        x.q2 = qr[2 * NP];
+        x.q3 = qr[3 * NP];
+        x.q4 = qr[4 * NP];
+        x.rb = br[0];
+        x.eb = br[NP];
+        x.b0 = pr[0];
+        x.b1 = pr[NP];
+        x.b2 = pr[2 * NP];
+        x.b3 = pr[3 * NP];
+        x.phi = rawphi[(size_t)el * PP::PHS + n +
+                       esdg_block_shift(v64 + ((size_t)(e0 + el) * ESDG_NVGEO + 10) * NP)];
+        x.phh = gr0[((size_t)el * ESDG_NVGEO + 10) * NP + n];
+        return x;
+      };
+      auto store = [&](const In& x, const Prim32& o) {
+        if (!x.any) return;
+        const int el = x.el, n = x.n;
+        float* S = sm + (size_t)el * NF * NP;
+        if (x.live) {
 #pragma unroll
-          for (int k = 0; k < 9; k++) S[(SH::F_NH + k) * NP + n] = gr[k * NP + n];
-          double* X = epq + (size_t)el2 * 5 * NP;
-          X[n] = q0;
-          X[NP + n] = q1;
-          X[2 * NP + n] = q2;
-          X[3 * NP + n] = q3;
-          X[4 * NP + n] = q4;
-          epj[(size_t)el2 * NP + n] = gr[9 * NP + n];
+          for (int f = 0; f < 7; f++) {
+            S[f * NP + n] = o.s[f];
+            S[(SH::F_BG + f) * NP + n] = o.bgf[f];
+          }
+          const float* gr = gr0 + (size_t)el * ESDG_NVGEO * NP + n;
+#pragma unroll
+          for (int f = 0; f < 9; f++) S[(SH::F_NH + f) * NP + n] = gr[f * NP];
+          double* X = epq + (size_t)el * 5 * NP + n;
+          X[0] = x.q0;
+          X[NP] = x.q1;
+          X[2 * NP] = x.q2;
+          X[3 * NP] = x.q3;
+          X[4 * NP] = x.q4;
+          epj[(size_t)el * NP + n] = gr[9 * NP];
+          if (n == 0) phi0s[el] = esdg_d2f(x.phi);
         } else {  // padding element: any valid state, results are discarded
           S[0 * NP + n] = 0.25f;
           S[1 * NP + n] = 0.5f;
           S[2 * NP + n] = 1.0f;
-          for (int k = 3; k < NF; k++) S[k * NP + n] = 0.0f;
+          for (int f = 3; f < NF; f++) S[f * NP + n] = 0.0f;
         }
+      };
+      auto prim = [&](const In& x) {
+        return prims32bg(x.q0, x.q1, x.q2, x.q3, x.q4, x.phi, x.phh, gm1f, x.rb, x.eb, x.b0, x.b1,
+                         x.b2, x.b3);
+      };
+      for (int i0 = tid; i0 < NN; i0 += 2 * T) {
+        const In x0 = load(i0), x1 = load(i0 + T);
+        const Prim32 o0 = prim(x0), o1 = prim(x1);
+        store(x0, o0);
+        store(x1, o1);
       }
     }
     __syncthreads();  // RAW consumed
 
     int need_logs = 0;
-    for (int idx = tid; idx < EPB * NP; idx += T) {
+    for (int idx = tid; idx < NN; idx += T) {
       const int el2 = idx / NP, n = idx - el2 * NP;
       const float* S = sm + (size_t)el2 * NF * NP;
       const float r0 = S[0], rn = S[n], b0 = S[NP], bn = S[NP + n];
@@ -602,12 +697,15 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     const bool okc = esdg_mbar_wait(&ctl.bars[1], ph_cur, ESDG_WAIT_LIMIT);
     ph_cur ^= 1u;
     if (__syncthreads_or(!okc)) {
-      if (tid == 0) atomicExch(&g_esdg_vol_timeout, 1);
+      if (tid == 0) {
+        atomicExch(&g_esdg_vol_timeout, 1);
+        pipe_drain(&ctl.bars[0], ph_raw, next < ntiles);
+      }
       return;
     }
 
-    // ---- epilogue: one thread per node ----------------------------------------
-    const double* RB0 = currb + esdg_block_shift(a.rhs_bg + (size_t)e0 * 3 * NP);
+    // ---- epilogue, two nodes per thread and round ------------------------------
+    const float* RB0 = currb + esdg_block_shift(a.rhs_bg + (size_t)e0 * 3 * NP);
     const float* D0 = curdq + esdg_block_shift(reinterpret_cast<const float*>(a.dq) + (size_t)e0 * 5 * NP);
     const EsdgPhys Pl = P;
     const bool rot = (Pl.f0 != 0.0) || (Pl.beta != 0.0);
@@ -616,42 +714,46 @@ __global__ void __launch_bounds__(Shape<N, true, true>::THREADS, 1)
     double* const qio = a.q_io;
     double* const rhsp = a.rhs;
     const double dtv = a.dt;
-    for (int idx = tid; idx < EPB * NP; idx += T) {
-      const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
-      if (el2 >= ne) continue;
-      const float* S = sm + (size_t)el2 * NF * NP;
-      const double* X = epq + (size_t)el2 * 5 * NP;
-      const float iJ = epj[(size_t)el2 * NP + n];
-      const double* RB = RB0 + (size_t)el2 * 3 * NP;
-      const size_t qb = (size_t)e2 * 5 * NP + n;
-      if constexpr (MODE != 0) {
-        float r32[5];
+    int* const status = a.status;
+    bool bad = false;
+    for (int i0 = tid; i0 < NN; i0 += 2 * T) {
 #pragma unroll
-        for (int v = 0; v < 5; v++)
-          r32[v] = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
-        const double y = rot ? xg[((size_t)e2 * 3 + 1) * NP + n] : 0.0;
-        stage32<NP, true>(r32, RB + n, Pl, y, X + n, D0 + (size_t)el2 * 5 * NP + n, dqp + qb,
-                          qio + qb, rkA, rkB, dtv);
-      } else {  // right-hand side in FP64
-        double r[5];
+      for (int k = 0; k < 2; k++) {
+        const int idx = i0 + k * T;
+        const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
+        if (idx >= NN || el2 >= ne) continue;
+        const float* S = sm + (size_t)el2 * NF * NP;
+        const double* X = epq + (size_t)el2 * 5 * NP;
+        const float iJ = epj[(size_t)el2 * NP + n];
+        const float* RB = RB0 + (size_t)el2 * 3 * NP;
+        const size_t qb = (size_t)e2 * 5 * NP + n;
+        if constexpr (MODE != 0) {
+          float r32[5];
 #pragma unroll
-        for (int v = 0; v < 5; v++) {
-          const float rv = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
-          r[v] = esdg_f2d(rv);
+          for (int v = 0; v < 5; v++)
+            r32[v] = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
+          const double y = rot ? xg[((size_t)e2 * 3 + 1) * NP + n] : 0.0;
+          bad |= stage32<NP, true>(r32, RB + n, Pl, y, X + n, D0 + (size_t)el2 * 5 * NP + n,
+                                   dqp + qb, qio + qb, rkA, rkB, dtv);
+        } else {  // right-hand side in FP64
+          double r[5];
+#pragma unroll
+          for (int v = 0; v < 5; v++) {
+            const float rv = -iJ * (S[v * NP + n] + S[(5 + v) * NP + n] + S[(10 + v) * NP + n]);
+            r[v] = esdg_f2d(rv + (v >= 1 && v <= 3 ? RB[(v - 1) * NP + n] : 0.0f));
+          }
+          if (rot) {
+            const double y = xg[((size_t)e2 * 3 + 1) * NP + n];
+            const double f = Pl.f0 + Pl.beta * (y - Pl.y0);
+            r[1] = fma(f, X[2 * NP + n], r[1]);
+            r[2] = fma(-f, X[NP + n], r[2]);
+          }
+#pragma unroll
+          for (int v = 0; v < 5; v++) rhsp[qb + (size_t)v * NP] = r[v];
         }
-        r[1] += RB[n];
-        r[2] += RB[NP + n];
-        r[3] += RB[2 * NP + n];
-        if (rot) {
-          const double y = xg[((size_t)e2 * 3 + 1) * NP + n];
-          const double f = Pl.f0 + Pl.beta * (y - Pl.y0);
-          r[1] = fma(f, X[2 * NP + n], r[1]);
-          r[2] = fma(-f, X[NP + n], r[2]);
-        }
-#pragma unroll
-        for (int v = 0; v < 5; v++) rhsp[qb + (size_t)v * NP] = r[v];
       }
     }
+    if (MODE != 0 && bad && status) *status = 1;
   }
 }
 
@@ -711,7 +813,7 @@ inline EsdgMember pipe_member(const EsdgGrid& g, const EsdgPhys& P, const EsdgVo
 template <int N, int MODE>
 cudaError_t launch_pipe64(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
                           const EsdgVolArgs& a, cudaStream_t s) {
-  using SH = Shape<N, false, false>;
+  using SH = PipeShape<N, false>;
   constexpr auto k = k_volume_pipe64<N, MODE, false>;
   const int cap = pipe_grid_cap<k>(SH::THREADS, Pipe64<N, MODE>::SMEM);
   if (cap < 0) return cudaErrorInvalidConfiguration;
@@ -727,7 +829,7 @@ cudaError_t launch_pipe64(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L
 template <int N, int MODE>
 cudaError_t launch_pipe32(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
                           const EsdgVolArgs& a, cudaStream_t s) {
-  using SH = Shape<N, true, true>;
+  using SH = PipeShape<N, true>;
   constexpr auto k = k_volume_pipe32<N, MODE, false>;
   const int cap = pipe_grid_cap<k>(SH::THREADS, Pipe32<N, MODE>::SMEM);
   if (cap < 0) return cudaErrorInvalidConfiguration;
@@ -744,7 +846,7 @@ cudaError_t launch_pipe32(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L
 template <int N, bool MIXED>
 int pipe_batch(int what, const EsdgMember* members, const int2* tiles, const int* ntiles, int grid,
                const EsdgLGL& L, double A, double B, cudaStream_t s) {
-  using SH = Shape<N, MIXED, MIXED>;
+  using SH = PipeShape<N, MIXED>;
   constexpr size_t SMEM = MIXED ? Pipe32<N, 1>::SMEM : Pipe64<N, 1>::SMEM;
   if (what == 1) return SH::EPB;
   auto k = [] {

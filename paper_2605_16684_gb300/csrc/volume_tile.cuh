@@ -21,6 +21,7 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
   const int E = g.E;
   const R* vg = reinterpret_cast<const R*>(a.vgeo);
   const double gm1 = P.gamma - 1.0;
+  const float gm1f = esdg_d2f(gm1);
 
   // ---- prologue: primitives once per node -------------------------------
   int need_logs = 0;
@@ -35,11 +36,17 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       if constexpr (MIXED) {
         const float phh = vg[((size_t)e * ESDG_NVGEO + 10) * NP + n];
         if constexpr (BG) {
-          const double* bge = a.bg + (size_t)e * 3 * NP;
-          prims32<NP, true>(q0, q1, q2, q3, q4, phi, phh, gm1, S, n, bge[n], bge[NP + n],
-                            bge[2 * NP + n], S + SH::F_BG * NP);
+          const double* bge = a.bg + (size_t)e * 2 * NP;
+          const float* bpe = a.bgp + (size_t)e * 4 * NP;
+          const Prim32 o = prims32bg(q0, q1, q2, q3, q4, phi, phh, gm1f, bge[n], bge[NP + n],
+                                     bpe[n], bpe[NP + n], bpe[2 * NP + n], bpe[3 * NP + n]);
+#pragma unroll
+          for (int k = 0; k < 7; k++) {
+            S[k * NP + n] = o.s[k];
+            S[(SH::F_BG + k) * NP + n] = o.bgf[k];
+          }
         } else {
-          prims32<NP, false>(q0, q1, q2, q3, q4, phi, phh, gm1, S, n);
+          prims32<NP>(q0, q1, q2, q3, q4, phi, phh, gm1, S, n);
         }
       } else {
         prims64<NP>(q0, q1, q2, q3, q4, phi, gm1, S, n);
@@ -129,6 +136,7 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
 
   // ---- epilogue: one thread per node -------------------------------------
   const bool rotating = (P.f0 != 0.0) || (P.beta != 0.0);
+  bool bad = false;
   for (int idx = threadIdx.x; idx < EPB * NP; idx += T) {
     const int el2 = idx / NP, n = idx - el2 * NP, e2 = e0 + el2;
     if (e2 >= E) continue;
@@ -142,8 +150,8 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       const size_t qb = (size_t)e2 * 5 * NP + n;
       const double y = rotating ? a.x[((size_t)e2 * 3 + 1) * NP + n] : 0.0;
       float* dq = reinterpret_cast<float*>(a.dq);
-      stage32<NP, BG>(r32, BG ? a.rhs_bg + (size_t)e2 * 3 * NP + n : nullptr, P, y, a.q_in + qb,
-                      dq + qb, dq + qb, a.q_io + qb, a.rkA, a.rkB, a.dt);
+      bad |= stage32<NP, BG>(r32, BG ? a.rhs_bg + (size_t)e2 * 3 * NP + n : nullptr, P, y,
+                             a.q_in + qb, dq + qb, dq + qb, a.q_io + qb, a.rkA, a.rkB, a.dt);
       continue;
     }
     // FP64 stage update: dt is folded into the -1/J scale (r then holds dt rhs)
@@ -180,13 +188,17 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
         double* dq = reinterpret_cast<double*>(a.dq);
 #pragma unroll
         for (int v = 0; v < 5; v++) {
-          const double dv = fma(a.rkA, dq[qb + (size_t)v * NP], r[v]);
+          // first stage (A = 0): the register is not read (see stage32)
+          const double dv = a.rkA == 0.0 ? r[v] : fma(a.rkA, dq[qb + (size_t)v * NP], r[v]);
           dq[qb + (size_t)v * NP] = dv;
-          a.q_io[qb + (size_t)v * NP] = fma(a.rkB, dv, a.q_in[qb + (size_t)v * NP]);
+          const double qn = fma(a.rkB, dv, a.q_in[qb + (size_t)v * NP]);
+          a.q_io[qb + (size_t)v * NP] = qn;
+          bad |= esdg_bad_state(qn, v == 0);
         }
       }
     }
   }
+  if (MODE != 0 && bad && a.status) *a.status = 1;
 }
 
 template <int N, bool MIXED, int MODE, bool BG>

@@ -83,6 +83,30 @@ def test_mixed_full_size_32cubed_N4(lib):
     assert np.all(mixed_errors(s.rhs(qg), o.rhs(qg)) <= 1e-5)
 
 
+def test_mixed_32cubed_N4_100_steps_per_variable(lib):
+    # the benchmark workload at full size (32^3 hexes, N = 4, warped 1000 m cube, 0.5 K
+    # cosine bubble, CFL 0.5): 100 mixed steps against 100 FP64 steps of the GPU path,
+    # whose right-hand side equals the oracle's at this size to 1e-12
+    # (test_rhs_parity_full_size_32cubed_N4); state and flow per variable <= 1e-4
+    K, N = (32, 32, 32), 4
+    out = {}
+    for prec in ("fp64", "mixed"):
+        s = lib.Solver(*K, N, precision=prec, warp=0.05, **CUBE)
+        s.init_bubble()
+        q0 = s.get_state()
+        dt = s.cfl_dt(0.5)
+        s.step(dt, 100)
+        s.sync()
+        out[prec] = (q0, s.get_state(), dt)
+        s.close()
+    (q0, q64, dt64), (q0m, q32, dt32) = out["fp64"], out["mixed"]
+    assert dt64 == dt32 and np.array_equal(q0, q0m)
+    e_state = mixed_errors(q32, q64)
+    e_flow = mixed_errors(q32 - q0, q64 - q0)
+    assert np.all(e_state <= 1e-4), e_state
+    assert np.all(e_flow <= 1e-4), e_flow
+
+
 def test_mixed_channel_with_background(lib):
     m = dict(lo=(0.0, 0.0, 0.0), hi=(40000e3, 6000e3, 30e3), periodic=(1, 0, 0))
     s = lib.Solver(6, 3, 2, 4, precision="mixed", f0=1e-4, **m)

@@ -5,13 +5,16 @@ The slabs' geometry, right-hand sides and LSRK steps equal the whole mesh's bit
 for bit (the same node positions, face geometry and per-face arithmetic; only
 the source of the outside state at a cut changes), in FP64 and in mixed
 precision, with periodic and walled x, ragged and single-layer slabs, a warped
-mesh, and the channel with its Coriolis term.  The whole mesh's own parity with
-the oracle is covered by the other GPU tests.
+mesh, and the channel with its Coriolis term.  Each slab result is also held
+to the CPU oracle directly: right-hand sides to 1e-12 per variable, FP64
+trajectories to 1e-12 or the long-double floor, mixed trajectories to 1e-4 per
+variable (see oracle_checks).
 """
 import numpy as np
 import pytest
 
 import oracle as O
+from oracle_checks import check_fp64, check_mixed, rel_err
 from paper_2605_16684_gb300 import inputs
 from paper_2605_16684_gb300._lib import EsDgError
 
@@ -64,7 +67,10 @@ def test_slab_rhs_equals_whole(lib, K, N, parts, periodic, warp):
     o = O.Oracle(*K, N, **mesh)
     x, _, _ = o.geometry()
     q = inputs.perturb_state(o.bubble(), x, mesh["lo"], mesh["hi"], seed=7)
-    assert np.array_equal(split.rhs(q), whole.rhs(q))
+    r = split.rhs(q)
+    assert np.array_equal(r, whole.rhs(q))
+    err = rel_err(r, o.rhs(q))
+    assert np.all(err <= 1e-12), err
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -73,24 +79,47 @@ def test_slab_steps_equal_whole(lib, K, N, parts, periodic, warp, precision):
     whole, split, _ = pair(lib, K, N, parts, periodic, warp, precision=precision)
     whole.init_bubble(amp=0.8, profile="sharp")
     split.init_bubble(amp=0.8, profile="sharp")
-    assert np.array_equal(split.get_state(), whole.get_state())
+    q_init = split.get_state()
+    assert np.array_equal(q_init, whole.get_state())
     dt = whole.cfl_dt(0.5)
     assert split.cfl_dt(0.5) == dt
     whole.step(dt, 4)
     split.step(dt, 4)
-    assert np.array_equal(split.get_state(), whole.get_state())
+    q = split.get_state()
+    assert np.array_equal(q, whole.get_state())
+    oracle_trajectory(q, q_init, precision, dict(CUBE, periodic=periodic, warp=warp), K, N, dt,
+                      4, lambda o: o.bubble(amp=0.8, profile="sharp"))
+
+
+def oracle_trajectory(q, q_init, precision, mesh, K, N, dt, nsteps, init, channel=False, **phys):
+    """The oracle advanced from its own initial state (which the GPU's must equal to
+    1e-12) with the same step; q checked against it (oracle_checks bars)."""
+    o = O.Oracle(*K, N, **mesh, **phys)
+    q0 = init(o)
+    assert np.abs(q_init - q0).max() <= 1e-12 * np.abs(q0).max()
+    q_plain = o.steps(q0, dt, nsteps)
+    if precision == "fp64":
+        q_long = O.Oracle(*K, N, precision="long", **mesh, **phys).steps(q0, dt, nsteps)
+        check_fp64(q, q_plain, q_long, what=(K, N, mesh))
+    else:
+        check_mixed(q, q0, q_plain, channel=channel, what=(K, N, mesh))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_slab_channel_with_coriolis(lib, precision):
-    kw = dict(mesh=dict(lo=(0.0, 0.0, 0.0), hi=(40000e3, 6000e3, 30e3)), f0=1e-4)
+    box = dict(lo=(0.0, 0.0, 0.0), hi=(40000e3, 6000e3, 30e3))
+    kw = dict(mesh=box, f0=1e-4)
     whole, split, _ = pair(lib, (6, 3, 2), 4, 3, (1, 0, 0), 0.0, precision=precision, **kw)
     whole.init_channel()
     split.init_channel()
+    q_init = split.get_state()
     dt = whole.cfl_dt(0.5)
     whole.step(dt, 3)
     split.step(dt, 3)
-    assert np.array_equal(split.get_state(), whole.get_state())
+    q = split.get_state()
+    assert np.array_equal(q, whole.get_state())
+    oracle_trajectory(q, q_init, precision, dict(box, periodic=(1, 0, 0)), (6, 3, 2), 4, dt, 3,
+                      lambda o: o.channel(), channel=True, f0=1e-4)
 
 
 def test_slab_calls_need_traces(lib):

@@ -1,13 +1,19 @@
 """Batched ensembles and the continuous-batching server on the GPU.
 
-* A batched solve (persistent launches over work tables, CUDA graph) gives the
-  same state as the same solve through the single-handle path.
+* Every served result equals the CPU oracle's trajectory from the same initial
+  state with the same time step (FP64 members to 1e-12 or the long-double
+  floor, mixed members to 1e-4 per variable in the state and the flow), for
+  orders 3, 4 and 7, bubbles, sharp bubbles and channels.
+* A batched solve (persistent launches over work tables, CUDA graph) also gives
+  the same state as the same solve through the single-handle path, bit for bit.
 * A result is the same alone and in a mix of other requests (bit for bit: the
-  members' arithmetic is independent).
+  members' arithmetic is independent), and both equal the oracle's.
 * Admission respects the footprint budget; errors are reported per request.
 """
 import numpy as np
 import pytest
+
+from oracle_checks import check_request_result
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +36,7 @@ def single_handle(lib, req):
         s = lib.Solver(*K, N, lo=(0, 0, 0), hi=(40000e3, 6000e3, 30e3), periodic=(1, 0, 0),
                        precision=req.get("precision", "fp64"), f0=1e-4)
         s.init_channel()
-    dt = s.cfl_dt(0.5)
+    dt = s.cfl_dt(req.get("cfl", 0.4))  # the server's default Courant number
     s.step(dt, req["nsteps"])
     q = s.get_state().reshape(-1)
     s.close()
@@ -45,10 +51,11 @@ MIX = [
     dict(K=(5, 4, 3), N=4, precision="fp64", nsteps=6, centre=(450.0, 520.0, 300.0)),
     dict(K=(3, 2, 2), N=3, precision="mixed", nsteps=7),
     dict(kind="sharp_bubble", K=(3, 3, 3), N=4, precision="mixed", nsteps=4),
+    dict(K=(2, 2, 2), N=7, precision="fp64", nsteps=3, warp=0.05, amp=0.9),
 ]
 
 
-def test_batched_equals_single_handle(lib):
+def test_batched_equals_single_handle_and_oracle(lib):
     srv = lib.Server()
     tickets = [srv.submit(**r) for r in MIX]
     for t, r in zip(tickets, MIX):
@@ -58,6 +65,7 @@ def test_batched_equals_single_handle(lib):
         assert res["dt"] == pytest.approx(dt, rel=0, abs=0)
         assert res["nsteps"] == r["nsteps"]
         assert np.array_equal(res["q"], q_ref), np.abs(res["q"] - q_ref).max()
+        check_request_result(r, res["q"], res["dt"])
     st = srv.stats()
     assert st["finished"] == len(MIX) and st["last_error"] == 0
     srv.close()
@@ -66,17 +74,20 @@ def test_batched_equals_single_handle(lib):
 def test_result_same_alone_and_in_mix(lib):
     target = dict(K=(4, 3, 3), N=4, precision="mixed", nsteps=6, warp=0.05)
     alone = lib.Server()
-    qa = alone.wait(alone.submit(**target))["q"]
+    ra = alone.wait(alone.submit(**target))
     alone.close()
     mix = lib.Server()
     others = [mix.submit(**r) for r in MIX[:3]]
     t = mix.submit(**target)
     later = [mix.submit(**r) for r in MIX[3:]]
-    qm = mix.wait(t)["q"]
+    rm = mix.wait(t)
     for o in others + later:
         assert mix.wait(o)["status"] == 0
     mix.close()
-    assert np.array_equal(qa, qm)
+    assert ra["status"] == 0 and rm["status"] == 0
+    assert np.array_equal(ra["q"], rm["q"])
+    # and both are the oracle's trajectory within the mixed-precision bars
+    check_request_result(target, ra["q"], ra["dt"])
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2])
@@ -95,6 +106,7 @@ def test_every_batched_variant_equals_single_handle(lib, monkeypatch, variant):
         res = srv.wait(t)
         assert res["status"] == 0, srv.stats()["error"]
         assert np.array_equal(res["q"], single_handle(lib, r)[0]), r
+        check_request_result(r, res["q"], res["dt"])
     srv.close()
 
 
@@ -109,6 +121,7 @@ def test_twin_meshes_share_geometry_exactly(lib):
         res = srv.wait(t)
         assert res["status"] == 0, srv.stats()["error"]
         assert np.array_equal(res["q"], single_handle(lib, r)[0])
+        check_request_result(r, res["q"], res["dt"])
     srv.close()
 
 
@@ -136,3 +149,39 @@ def test_errors_and_cancel(lib):
     srv.cancel(t)
     assert srv.wait(t)["status"] in (0, -7)
     srv.close()
+
+
+def test_diverging_member_finishes_alone_with_enan(lib):
+    # host-side injection: one request's time step is far beyond the stability limit
+    # (Courant number 40), so its state overflows within a few steps.  That member
+    # is finished early with ES_DG_ENAN; the members around it are unaffected.
+    good = [dict(K=(3, 3, 3), N=3, precision="fp64", nsteps=40),
+            dict(K=(3, 3, 2), N=4, precision="mixed", nsteps=40, warp=0.05)]
+    bad = dict(K=(3, 3, 3), N=3, precision="mixed", nsteps=400, cfl=40.0)
+    srv = lib.Server()
+    tg = [srv.submit(**good[0]), srv.submit(**bad), srv.submit(**good[1])]
+    res = [srv.wait(t) for t in tg]
+    srv.close()
+    assert res[1]["status"] == -4 and res[1]["q"] is None
+    assert res[1]["nsteps"] < bad["nsteps"]
+    for r, req in zip((res[0], res[2]), good):
+        assert r["status"] == 0
+        assert np.array_equal(r["q"], single_handle(lib, req)[0])
+        check_request_result(req, r["q"], r["dt"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_single_handle_reports_non_finite_state(lib, precision):
+    s = lib.Solver(3, 3, 3, 3, precision=precision)
+    s.init_bubble()
+    q0 = s.get_state()
+    dt = s.cfl_dt(0.5)
+    s.step(80.0 * dt, 60)
+    with pytest.raises(lib.EsDgError) as err:
+        s.sync()
+    assert err.value.code == -4  # ES_DG_ENAN
+    s.set_state(q0)  # the flag was cleared by the failed sync
+    s.step(dt, 2)
+    s.sync()
+    assert np.isfinite(s.get_state()).all()
+    s.close()

@@ -67,6 +67,17 @@ def test_noalloc_integrals_match_handle_path_on_consecutive_calls():
         for got in outs:
             assert np.allclose(got, expected, rtol=1e-12, atol=0), (got, expected)
         assert np.array_equal(outs[0], outs[1])
+        # the property the entry point exists for: a warm call takes no device memory
+        out = torch.empty((3,), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        rc = lib.es_dg_integrals_noalloc(C.byref(mesh), N, None, C.c_void_p(q_dev.data_ptr()),
+                                         C.c_void_p(J_dev.data_ptr()), C.c_void_p(x_dev.data_ptr()),
+                                         C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
+        torch.cuda.synchronize()
+        assert rc == 0
+        assert torch.cuda.mem_get_info()[0] == free_before
+        assert np.array_equal(out.cpu().numpy(), outs[0])
         s.close()
 
 
@@ -79,3 +90,41 @@ def test_noalloc_rejects_meshes_beyond_the_static_scratch():
     dummy = C.c_void_p(16)
     rc = lib.es_dg_integrals_noalloc(C.byref(mesh), 3, None, dummy, dummy, dummy, dummy, None)
     assert rc == -1
+
+
+def _cuda_device_present():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:  # pragma: no cover
+        return False
+
+
+@pytest.mark.skipif(_cuda_device_present(), reason="needs a machine without a CUDA device")
+def test_noalloc_accepts_a_mesh_of_exactly_the_maximum_size():
+    # 64 x 64 x 64 = ES_DG_NOALLOC_MAX_ELEMS elements passes the size check; with no
+    # device present the call then fails at the device query (-ES_DG_ECUDA), not with
+    # -ES_DG_EINVAL for its size
+    from paper_2605_16684_gb300 import _build, _lib
+
+    _build.build()
+    lib = _lib.load()
+    mesh = _mesh(_lib, (64, 64, 64))
+    dummy = C.c_void_p(16)
+    rc = lib.es_dg_integrals_noalloc(C.byref(mesh), 3, None, dummy, dummy, dummy, dummy, None)
+    assert rc == -3  # ES_DG_ECUDA
+
+
+def test_noalloc_rejects_physics_that_create_rejects():
+    from paper_2605_16684_gb300 import _build, _lib
+
+    _build.build()
+    lib = _lib.load()
+    mesh = _mesh(_lib, (2, 2, 2))
+    dummy = C.c_void_p(16)
+    for gamma, R, p0 in ((1.0, 287.0, 1e5), (1.4, 0.0, 1e5), (1.4, 287.0, -1.0),
+                         (float("nan"), 287.0, 1e5)):
+        ph = _lib.es_dg_physics(gamma, 9.81, R, p0, 0.0, 0.0, 0.0, 1)
+        rc = lib.es_dg_integrals_noalloc(C.byref(mesh), 3, C.byref(ph), dummy, dummy, dummy,
+                                         dummy, None)
+        assert rc == -1  # ES_DG_EINVAL, before any CUDA call
