@@ -49,9 +49,9 @@ struct es_dg {
   double* bg;       // [E][3][np] rho_bg, b_bg, p_bg
   double* rhs_bg;   // [E][3][np] FP64 momentum right-hand side of the background at rest
   double* fflux64;  // FP64 face fluxes for evaluating that right-hand side
-  // the mixed volume kernels' copy: bg2 [E][2][np] rho_bg, E_bg; bgp [E][4][np] FP32
+  // the mixed volume kernels' copy: bg3 [E][3][np] rho_bg, E_bg, phi; bgp [E][4][np] FP32
   // rho_bg/4, b_bg/2, 1/b_bg, p_bg; rhs_bg32 [E][3][np] the momentum rhs in FP32
-  double* bg2;
+  double* bg3;
   float* bgp;
   float* rhs_bg32;
   // a partition's trace buffers (caller-owned device memory; [0] low x plane, [1] high)
@@ -155,7 +155,7 @@ EsdgVolArgs vol_args(es_dg_t* h, const double* q_in, double* rhs_out) {
   a.vgeo64 = h->vgeo;
   a.fflux = h->fflux;
   a.x = h->x;
-  a.bg = (h->mixed && h->has_bg) ? h->bg2 : nullptr;
+  a.bg = (h->mixed && h->has_bg) ? h->bg3 : nullptr;
   a.bgp = h->bgp;
   a.rhs_bg = h->rhs_bg32;
   a.rkA = 0.0;
@@ -216,7 +216,7 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
   if (!st && !h->rhs_bg) st = dev_alloc(h, (void**)&h->rhs_bg, E * 3 * np * sizeof(double));
   if (!st && !h->fflux64)
     st = dev_alloc(h, (void**)&h->fflux64, (size_t)h->g.nfaces * 5 * nf2 * sizeof(double));
-  if (!st && !h->bg2) st = dev_alloc(h, (void**)&h->bg2, E * 2 * np * sizeof(double));
+  if (!st && !h->bg3) st = dev_alloc(h, (void**)&h->bg3, E * 3 * np * sizeof(double));
   if (!st && !h->bgp) st = dev_alloc(h, (void**)&h->bgp, E * 4 * np * sizeof(float));
   if (!st && !h->rhs_bg32) st = dev_alloc(h, (void**)&h->rhs_bg32, E * 3 * np * sizeof(float));
   if (st) return st;
@@ -224,7 +224,7 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
   if (q_dev == q0) return ES_DG_EINVAL;
   cudaError_t e = esdg_launch_background(h->g, h->P, h->vgeo, q_dev, h->bg, q0, h->stream);
   if (e == cudaSuccess)
-    e = esdg_launch_background_vol(h->g, h->P, h->vgeo, h->bg, h->bg2, h->bgp, h->stream);
+    e = esdg_launch_background_vol(h->g, h->P, h->vgeo, h->bg, h->bg3, h->bgp, h->stream);
   if (e != cudaSuccess) return cuda_status(e);
   if (is_partition(h)) {
     // the faces of the cut planes need the neighbours' background: evaluated at the

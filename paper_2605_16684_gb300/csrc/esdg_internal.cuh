@@ -306,10 +306,10 @@ cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, co
 // layer's i = N nodes into send_hi (if remote[1]), layout of EsdgTraces.
 cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, const double* bg, int nv,
                                    double* send_lo, double* send_hi, cudaStream_t s);
-// The mixed volume kernels' background copy (bg2: rho_bg, E_bg FP64; bgp:
+// The mixed volume kernels' background copy (bg3: rho_bg, E_bg, phi FP64; bgp:
 // rho_bg/4, b_bg/2, 1/b_bg, p_bg FP32) from the stored background bg.
 cudaError_t esdg_launch_background_vol(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
-                                       const double* bg, double* bg2, float* bgp, cudaStream_t s);
+                                       const double* bg, double* bg3, float* bgp, cudaStream_t s);
 // dst[i] = src[i] rounded to FP32, i < n
 cudaError_t esdg_launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 // The background state at rest from the stored background, per node:
@@ -327,7 +327,7 @@ struct EsdgVolArgs {
   const double* vgeo64;  // [E][11][np] double (geopotential for the pressure recovery)
   const void* fflux;     // face fluxes, double or float
   const double* x;       // coordinates (Coriolis parameter)
-  const double* bg;      // mixed mode with a background: [E][2][np] rho_bg, E_bg (else null)
+  const double* bg;      // mixed mode with a background: [E][3][np] rho_bg, E_bg, phi (else null)
   const float* bgp;      // mixed mode with a background: [E][4][np] rho_bg/4, b_bg/2, 1/b_bg, p_bg
   const float* rhs_bg;   // mixed mode with a background: [E][3][np] momentum rhs of it (FP32)
   double rkA, rkB, dt;

@@ -270,14 +270,15 @@ __global__ void k_background_state(EsdgGrid g, EsdgPhys P, const double* __restr
   o[4 * np + n] = fma(rho, phi, p / (P.gamma - 1.0));
 }
 
-// The mixed volume kernels' copy of the background: bg2 = (rho_bg, E_bg) in
-// FP64, E_bg = p_bg/(gamma - 1) + rho_bg phi the background's total energy at
-// rest (the expression of k_background), for the exact FP64 differences
-// rho - rho_bg and E - E_bg; bgp = (rho_bg/4, b_bg/2, 1/b_bg, p_bg) in FP32, the
+// The mixed volume kernels' copy of the background: bg3 = (rho_bg, E_bg, phi)
+// in FP64, E_bg = p_bg/(gamma - 1) + rho_bg phi the background's total energy
+// at rest (the expression of k_background), for the exact FP64 differences
+// rho - rho_bg and E - E_bg, with the geopotential beside them so that one
+// bulk copy brings all three; bgp = (rho_bg/4, b_bg/2, 1/b_bg, p_bg) in FP32, the
 // background's node fields of the FP32 pair loop, converted once here instead
 // of at every stage.
 __global__ void k_background_vol(EsdgGrid g, EsdgPhys P, const double* __restrict__ vgeo,
-                                 const double* __restrict__ bg, double* __restrict__ bg2,
+                                 const double* __restrict__ bg, double* __restrict__ bg3,
                                  float* __restrict__ bgp) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int np = g.np;
@@ -287,8 +288,9 @@ __global__ void k_background_vol(EsdgGrid g, EsdgPhys P, const double* __restric
   const double phi = vgeo[(e * ESDG_NVGEO + 10) * np + n];
   const double rho = bg[(e * 3 + 0) * np + n], b = bg[(e * 3 + 1) * np + n],
                p = bg[(e * 3 + 2) * np + n];
-  bg2[(e * 2 + 0) * np + n] = rho;
-  bg2[(e * 2 + 1) * np + n] = fma(rho, phi, p / (P.gamma - 1.0));
+  bg3[(e * 3 + 0) * np + n] = rho;
+  bg3[(e * 3 + 1) * np + n] = fma(rho, phi, p / (P.gamma - 1.0));
+  bg3[(e * 3 + 2) * np + n] = phi;
   bgp[(e * 4 + 0) * np + n] = __double2float_rn(0.25 * rho);
   bgp[(e * 4 + 1) * np + n] = __double2float_rn(0.5 * b);
   bgp[(e * 4 + 2) * np + n] = __double2float_rn(1.0 / b);
@@ -303,10 +305,10 @@ __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst
 }  // namespace
 
 cudaError_t esdg_launch_background_vol(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
-                                       const double* bg, double* bg2, float* bgp, cudaStream_t s) {
+                                       const double* bg, double* bg3, float* bgp, cudaStream_t s) {
   const long long nt = (long long)g.E * g.np;
   if (nt == 0) return cudaSuccess;
-  k_background_vol<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, P, vgeo, bg, bg2, bgp);
+  k_background_vol<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, P, vgeo, bg, bg3, bgp);
   return cudaGetLastError();
 }
 

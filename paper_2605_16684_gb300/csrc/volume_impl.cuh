@@ -35,6 +35,7 @@
 #pragma once
 #include "volume_pipe.cuh"
 #include "volume_tile.cuh"
+#include "volume_ws.cuh"
 
 namespace esdg_vol {
 
@@ -49,6 +50,9 @@ cudaError_t launch_volume_t(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys&
     }                                                                          \
     if constexpr (MIXED) {                                                     \
       if (a.bg) {                                                              \
+        if constexpr (WsCfg<NN>::ON && Ws32<NN, 1>::SMEM <= ESDG_PIPE_SMEM_MAX) \
+          return mode ? launch_ws32<NN, 1>(g, P, L, a, s)                      \
+                      : launch_ws32<NN, 0>(g, P, L, a, s);                     \
         if constexpr (Pipe32<NN, 1>::SMEM <= ESDG_PIPE_SMEM_MAX)               \
           return mode ? launch_pipe32<NN, 1>(g, P, L, a, s)                    \
                       : launch_pipe32<NN, 0>(g, P, L, a, s);                   \

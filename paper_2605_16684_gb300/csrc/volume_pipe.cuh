@@ -134,16 +134,19 @@ struct BlockSpan {
   int sh, tail0;            // shift; first element copied with cp.async (n if none)
 };
 __device__ __forceinline__ BlockSpan bc_span(const BlockCopy& c) {
+  // element sizes are 4 or 8 bytes: divisions by them are shifts (a 64-bit
+  // division by a runtime value costs hundreds of cycles on the issuing lane)
+  const unsigned lg = c.esz == 8 ? 3u : 2u;
   const unsigned long long src = reinterpret_cast<unsigned long long>(c.src);
-  const unsigned long long end = src + (unsigned long long)c.n * c.esz;
+  const unsigned long long end = src + ((unsigned long long)c.n << lg);
   const unsigned long long lim = reinterpret_cast<unsigned long long>(c.lim);
   BlockSpan s;
   s.a = src & ~15ull;
-  s.sh = (int)((src - s.a) / (unsigned)c.esz);
+  s.sh = (int)((unsigned)(src - s.a) >> lg);
   const unsigned long long up = (end + 15ull) & ~15ull;
   s.b = up <= lim ? up : (end & ~15ull);
   if (s.b < s.a) s.b = s.a;
-  s.tail0 = s.b >= end ? c.n : (s.b > src ? (int)((s.b - src) / (unsigned)c.esz) : 0);
+  s.tail0 = s.b >= end ? c.n : (s.b > src ? (int)((s.b - src) >> lg) : 0);
   return s;
 }
 
@@ -165,11 +168,15 @@ struct Issuers {
 };
 // phantom: bytes registered but never copied (a test hook that makes the
 // barrier's bounded wait run out; 0 in normal operation)
+// track_cp: every issuing lane also arrives on the barrier (cp.async.mbarrier
+// .arrive.noinc) once its cp.async edge copies have landed, so that threads
+// other than the issuers may wait on the barrier alone; the barrier then
+// expects 1 + ISS::COUNT arrivals per phase.
 template <typename ISS, int MAXB>
 __device__ __forceinline__ void pipe_issue(int tid, const BlockCopy (&bl)[MAXB], int nb,
                                            unsigned long long* bar, unsigned extra = 0,
                                            const void* xsrc = nullptr, void* xdst = nullptr,
-                                           unsigned phantom = 0) {
+                                           unsigned phantom = 0, bool track_cp = false) {
   constexpr int PER = (MAXB + ISS::COUNT - 1) / ISS::COUNT;
   const int il = tid - ISS::FIRST;
   BlockSpan sp[PER];
@@ -203,6 +210,9 @@ __device__ __forceinline__ void pipe_issue(int tid, const BlockCopy (&bl)[MAXB],
       }
     }
   }
+  if (track_cp)
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(esdg_smem_addr(bar))
+                 : "memory");
 }
 
 template <int N, int MODE, bool TABLE>
@@ -438,13 +448,11 @@ struct Pipe32 {
   using SH = PipeShape<N, true>;
   static constexpr int NP = SH::NP, EPB = SH::EPB, P = NP * EPB;
   static constexpr int up16(int b) { return (b + 15) & ~15; }
-  static constexpr int PHS = (NP + 4) & ~1;  // even per-element stride: every target 16-byte aligned
   // byte offsets, 16-byte aligned; copy targets hold 32 extra bytes (the
   // aligned span around each block)
   static constexpr int RAW_Q = 0;                                  // [el][5][NP]  double
-  static constexpr int RAW_PHI = up16(RAW_Q + 8 * (5 * P + 4));    // [el][PHS]    double
-  static constexpr int RAW_BG = up16(RAW_PHI + 8 * EPB * PHS);     // [el][2][NP]  double rho_bg, E_bg
-  static constexpr int RAW_BGP = up16(RAW_BG + 8 * (2 * P + 4));   // [el][4][NP]  float background fields
+  static constexpr int RAW_BG = up16(RAW_Q + 8 * (5 * P + 4));     // [el][3][NP]  double rho_bg, E_bg, phi
+  static constexpr int RAW_BGP = up16(RAW_BG + 8 * (3 * P + 4));   // [el][4][NP]  float background fields
   static constexpr int RAW_G = up16(RAW_BGP + 4 * (4 * P + 8));    // [el][11][NP] float
   static constexpr int S0 = up16(RAW_G + 4 * (ESDG_NVGEO * P + 8));  // [el][NF][NP] float
   static constexpr int EPI_Q = up16(S0 + 4 * SH::NF * P);         // [el][5][NP]  double
@@ -470,7 +478,6 @@ __global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>:
   __shared__ __align__(16) PipeCtl<TABLE> ctl;
   __shared__ float phi0s[EPB];  // each element's reference geopotential
   double* const rawq = reinterpret_cast<double*>(smraw + PP::RAW_Q);
-  double* const rawphi = reinterpret_cast<double*>(smraw + PP::RAW_PHI);
   double* const rawbg = reinterpret_cast<double*>(smraw + PP::RAW_BG);
   float* const rawbgp = reinterpret_cast<float*>(smraw + PP::RAW_BGP);
   float* const rawg = reinterpret_cast<float*>(smraw + PP::RAW_G);
@@ -490,7 +497,6 @@ __global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>:
     const double* bg;
     const float* bgp;
     const float* vg;
-    const double* v64;
     const EsdgMember* Mg;
   };
   auto fetch = [&](int t) {
@@ -503,28 +509,22 @@ __global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>:
     x.bg = x.Mg->a.bg;
     x.bgp = x.Mg->a.bgp;
     x.vg = reinterpret_cast<const float*>(x.Mg->a.vgeo);
-    x.v64 = x.Mg->a.vgeo64;
     return x;
   };
   // issuing lanes: the next tile's (member, e0), descriptor and RAW blocks into slot s
   auto issue_next = [&](const Next& x, int s, unsigned ph = 0) {
     if (tid == ISS::FIRST) ctl.info[s] = x.tr;
     const int e0 = x.tr.y, ne = x.tr.z;
-    const double* v64end = x.v64 + (size_t)x.E * ESDG_NVGEO * NP;
-    BlockCopy bl[4 + EPB];
-    bl[0] = {rawq, x.q + (size_t)e0 * 5 * NP, x.q + (size_t)x.E * 5 * NP, ne * 5 * NP, 8};
-    bl[1] = {rawbg, x.bg + (size_t)e0 * 2 * NP, x.bg + (size_t)x.E * 2 * NP, ne * 2 * NP, 8};
-    bl[2] = {rawbgp, x.bgp + (size_t)e0 * 4 * NP, x.bgp + (size_t)x.E * 4 * NP, ne * 4 * NP, 4};
-    bl[3] = {rawg, x.vg + (size_t)e0 * ESDG_NVGEO * NP, x.vg + (size_t)x.E * ESDG_NVGEO * NP,
-             ne * ESDG_NVGEO * NP, 4};
-#pragma unroll
-    for (int el = 0; el < EPB; el++)
-      bl[4 + el] = {rawphi + (size_t)el * PP::PHS, x.v64 + ((size_t)(e0 + el) * ESDG_NVGEO + 10) * NP,
-                    v64end, el < ne ? NP : 0, 8};
+    const BlockCopy bl[4] = {
+        {rawq, x.q + (size_t)e0 * 5 * NP, x.q + (size_t)x.E * 5 * NP, ne * 5 * NP, 8},
+        {rawbg, x.bg + (size_t)e0 * 3 * NP, x.bg + (size_t)x.E * 3 * NP, ne * 3 * NP, 8},
+        {rawbgp, x.bgp + (size_t)e0 * 4 * NP, x.bgp + (size_t)x.E * 4 * NP, ne * 4 * NP, 4},
+        {rawg, x.vg + (size_t)e0 * ESDG_NVGEO * NP, x.vg + (size_t)x.E * ESDG_NVGEO * NP,
+         ne * ESDG_NVGEO * NP, 4}};
     if constexpr (TABLE)
-      pipe_issue<ISS>(tid, bl, 4 + EPB, &ctl.bars[0], (unsigned)sizeof(EsdgMember), x.Mg, &ctl.desc[s], ph);
+      pipe_issue<ISS>(tid, bl, 4, &ctl.bars[0], (unsigned)sizeof(EsdgMember), x.Mg, &ctl.desc[s], ph);
     else
-      pipe_issue<ISS>(tid, bl, 4 + EPB, &ctl.bars[0], 0, nullptr, nullptr, ph);
+      pipe_issue<ISS>(tid, bl, 4, &ctl.bars[0], 0, nullptr, nullptr, ph);
   };
 
   if (tid == 0) {
@@ -568,9 +568,8 @@ __global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>:
     {
       const float gm1f = esdg_d2f(P.gamma - 1.0);
       const float* vg = reinterpret_cast<const float*>(a.vgeo);
-      const double* v64 = a.vgeo64;
       const double* qr0 = rawq + esdg_block_shift(a.q_in + (size_t)e0 * 5 * NP);
-      const double* br0 = rawbg + esdg_block_shift(a.bg + (size_t)e0 * 2 * NP);
+      const double* br0 = rawbg + esdg_block_shift(a.bg + (size_t)e0 * 3 * NP);
       const float* pr0 = rawbgp + esdg_block_shift(a.bgp + (size_t)e0 * 4 * NP);
       const float* gr0 = rawg + esdg_block_shift(vg + (size_t)e0 * ESDG_NVGEO * NP);
       struct In {
@@ -587,7 +586,7 @@ __global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>:
         x.live = x.any && x.el < ne;
         const int el = x.live ? x.el : 0, n = x.live ? x.n : 0;
         const double* qr = qr0 + (size_t)el * 5 * NP + n;
-        const double* br = br0 + (size_t)el * 2 * NP + n;
+        const double* br = br0 + (size_t)el * 3 * NP + n;
         const float* pr = pr0 + (size_t)el * 4 * NP + n;
         x.q0 = qr[0];
         x.q1 = qr[NP];
@@ -596,12 +595,11 @@ __global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>:
         x.q4 = qr[4 * NP];
         x.rb = br[0];
         x.eb = br[NP];
+        x.phi = br[2 * NP];
         x.b0 = pr[0];
         x.b1 = pr[NP];
         x.b2 = pr[2 * NP];
         x.b3 = pr[3 * NP];
-        x.phi = rawphi[(size_t)el * PP::PHS + n +
-                       esdg_block_shift(v64 + ((size_t)(e0 + el) * ESDG_NVGEO + 10) * NP)];
         x.phh = gr0[((size_t)el * ESDG_NVGEO + 10) * NP + n];
         return x;
       };

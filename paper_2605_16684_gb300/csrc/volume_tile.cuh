@@ -36,7 +36,7 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       if constexpr (MIXED) {
         const float phh = vg[((size_t)e * ESDG_NVGEO + 10) * NP + n];
         if constexpr (BG) {
-          const double* bge = a.bg + (size_t)e * 2 * NP;
+          const double* bge = a.bg + (size_t)e * 3 * NP;
           const float* bpe = a.bgp + (size_t)e * 4 * NP;
           const Prim32 o = prims32bg(q0, q1, q2, q3, q4, phi, phh, gm1f, bge[n], bge[NP + n],
                                      bpe[n], bpe[NP + n], bpe[2 * NP + n], bpe[3 * NP + n]);
