@@ -46,12 +46,18 @@ SAMPLE_K = (8, 8, 8)
 METRIC = "DOF-updates/s per RK stage"
 UNIT = "DOF-updates/s"
 
-# Algorithmic work of the volume kernel (counted from the formulas, FMA = 2):
-# per unordered node pair 100 flops (averages 9, two log means 22, p* 2, u_n 5,
-# F_rho 1, F_m 9, F_E 14, gravity and its partner 13, accumulation into both
-# nodes 26); per node 45 flops (primitive recovery 20, epilogue and RK update 25).
-FLOPS_PER_PAIR = 100
-FLOPS_PER_NODE = 45
+# Algorithmic work of the volume kernel, counted from the oracle's own arithmetic by
+# its counting instantiation (oracle/count_flops.cpp; tests/test_flop_count.py holds
+# these constants to the counts, the same for every order): per unordered node pair of
+# the half sweep 114 flops (both orderings of the oracle's pair term, the symmetric
+# two-point flux, log means and metric average once, the gravity term and the
+# accumulation for each node); per node and stage 56 (primitives 16, and for each of
+# the five values its volume value and stage update).  The kernel itself executes
+# fewer: 100 per pair and 45 per node in its regrouped arithmetic (FMA = 2 flops).
+FLOPS_PER_PAIR = 114
+FLOPS_PER_NODE = 56
+KERNEL_FLOPS_PER_PAIR = 100
+KERNEL_FLOPS_PER_NODE = 45
 # Algorithmic bytes of the interface kernel per face node (FP64): two traces
 # (2 x 40 B), face geometry (40 B) and the flux write (40 B); RK state traffic
 # is fused into the volume kernel.
@@ -117,8 +123,8 @@ def pairs_per_element(N):
     return 3 * Nq * Nq * Nq * (Nq - 1) // 2
 
 
-def volume_flops(E, N):
-    return E * (pairs_per_element(N) * FLOPS_PER_PAIR + (N + 1) ** 3 * FLOPS_PER_NODE)
+def volume_flops(E, N, per_pair=FLOPS_PER_PAIR, per_node=FLOPS_PER_NODE):
+    return E * (pairs_per_element(N) * per_pair + (N + 1) ** 3 * per_node)
 
 
 # ------------------------------------------------------------------ clocks --
@@ -330,7 +336,12 @@ def main_ours(args):
                      "peak_source": f"{dev['sms']} SMs x {DFMA_PER_CLK_SM} DFMA/clk x "
                                     f"{dev['sm_max_mhz']:.0f} MHz ({dev['clock_source']}); the "
                                     "recipe's nominal FP64 rate is 1.25 TFLOP/s",
-                     "flops_per_launch": vflops, "ms_per_launch": r64["t_vol"]},
+                     "flops_per_launch": vflops, "ms_per_launch": r64["t_vol"],
+                     "flop_count": "algorithmic, counted from the oracle: 114 per unordered "
+                                   "node pair, 56 per node and stage",
+                     "kernel_executed_frac": volume_flops(r64["E"], w["N"], KERNEL_FLOPS_PER_PAIR,
+                                                          KERNEL_FLOPS_PER_NODE)
+                     / (r64["t_vol"] * 1e-3) / FP64_PEAK},
         "kernels_ms_per_stage": {"fp64": {"interface": r64["t_face"], "volume_rk": r64["t_vol"]},
                                  "mixed": {"interface": r32["t_face"], "volume_rk": r32["t_vol"]}},
         "mixed": {"value": value32, "unit": UNIT, "dtype": "f32 pairs, f64 state",

@@ -134,6 +134,24 @@ def eigensystem(qm, qp, phi, nhat, gamma=1.4, precision="double"):
     return R, lam, T
 
 
+def count_flops(N: int) -> dict:
+    """Algorithmic flops of the volume term counted from the oracle's own code by
+    its counting instantiation (count_flops.cpp): per unordered node pair of the
+    half sweep (both orderings, shared subexpressions once) and per node and stage
+    (primitives, the volume values and the stage updates)."""
+    with _LOCK:
+        if "count" not in _LIBS:
+            _build.build()
+            lib = C.CDLL(_build.lib_path("liboracle_count.so"))
+            lib.or_count_flops.argtypes = [C.c_int, _D]
+            _LIBS["count"] = lib
+    out = np.zeros(5)
+    if _LIBS["count"].or_count_flops(int(N), _p(out)):
+        raise ValueError("unsupported N")
+    return dict(pair=int(out[0]), node=int(out[1]), primitives=int(out[2]),
+                stage_update=int(out[3]), pair_without_sharing=int(out[4]))
+
+
 def lsrk_coeffs():
     A, B, c = np.zeros(5), np.zeros(5), np.zeros(5)
     _lib().or_lsrk_coeffs(_p(A), _p(B), _p(c))

@@ -543,6 +543,23 @@ static int neighbour(const or_ctx* c, int e, int d, int side) {
   return idx[0] + m->kx * (idx[1] + m->ky * idx[2]);
 }
 
+/* One ordered pair's term of node i's volume sum (Section 4.1): the two-point
+ * flux between node i and its partner l along reference direction d, with the
+ * metric average n = {{Ja^d}}_il and the gravity term of node i, times
+ * Dt_{am} (a, m the two nodes' indices along d). */
+static void volume_pair(const basis_t* B, const real* Ja, int np, int d, int i, int l, int a,
+                        int m, const prim_t* Pi, const prim_t* Pl, real gamma, real* acc) {
+  real n[3], F[NV], G[3];
+  for (int k = 0; k < 3; k++) n[k] = (Ja[(d * 3 + k) * np + i] + Ja[(d * 3 + k) * np + l]) / 2;
+  ec_flux(Pi, Pl, n, gamma, F, G);
+  for (int k = 0; k < 3; k++) F[1 + k] += G[k];
+  for (int v = 0; v < NV; v++) acc[v] += B->Dt[a][m] * F[v];
+}
+
+/* Eq. (nm:semi): the volume part of the right-hand side of one value, -(1/J) times
+ * its flux-differencing sum. */
+static real volume_value(real acc, real J) { return -acc / J; }
+
 int or_rhs_parts(const or_ctx* c, const double* qd, double* vol_out, double* surf_out,
                  double* src_out) {
   const basis_t* B = &c->B;
@@ -573,14 +590,11 @@ int or_rhs_parts(const or_ctx* c, const double* qd, double* vol_out, double* sur
         for (int m = 0; m < Nq; m++) {
           if (m == a) continue;
           int l = node_with(B, i, d, m);
-          real n[3], F[NV], G[3];
-          for (int k = 0; k < 3; k++) n[k] = (Ja[(d * 3 + k) * np + i] + Ja[(d * 3 + k) * np + l]) / 2;
-          ec_flux(&pr[(size_t)e * np + i], &pr[(size_t)e * np + l], n, gamma, F, G);
-          for (int k = 0; k < 3; k++) F[1 + k] += G[k];
-          for (int v = 0; v < NV; v++) acc[v] += B->Dt[a][m] * F[v];
+          volume_pair(B, Ja, np, d, i, l, a, m, &pr[(size_t)e * np + i], &pr[(size_t)e * np + l],
+                      gamma, acc);
         }
       }
-      for (int v = 0; v < NV; v++) vol[((size_t)e * NV + v) * np + i] = -acc[v] / J[i];
+      for (int v = 0; v < NV; v++) vol[((size_t)e * NV + v) * np + i] = volume_value(acc[v], J[i]);
     }
     /* surface term: faces of this element, own metric, neighbour or mirror state */
     for (int d = 0; d < 3; d++)
@@ -731,6 +745,14 @@ void or_lsrk_coeffs(double* A, double* B, double* c) {
   }
 }
 
+/* One value's stage of the 2N-storage scheme: r = the volume, surface and source
+ * parts of its right-hand side; dq <- A_s dq + dt r; q <- q + B_s dq. */
+static void lsrk_value(real v, real s, real h, real A, real Bs, real dt, real* dq, real* q) {
+  real r = v + s + h;
+  *dq = A * *dq + dt * r;
+  *q = *q + Bs * *dq;
+}
+
 /* dq <- A_s dq + dt rhs(q);  q <- q + B_s dq, s = 1..5.  With REAL = long double
  * the state is carried in long double across all steps. */
 int or_lsrk_steps(const or_ctx* c, double* qd, double dt, int nsteps) {
@@ -745,11 +767,9 @@ int or_lsrk_steps(const or_ctx* c, double* qd, double dt, int nsteps) {
     for (int st = 0; st < 5; st++) {
       for (size_t k = 0; k < tot; k++) qs[k] = (double)q[k];
       or_rhs_parts(c, qs, v, s, h);
-      for (size_t k = 0; k < tot; k++) {
-        real r = (real)v[k] + (real)s[k] + (real)h[k];
-        dq[k] = (real)LSRK_A[st] * dq[k] + (real)dt * r;
-        q[k] = q[k] + (real)LSRK_B[st] * dq[k];
-      }
+      for (size_t k = 0; k < tot; k++)
+        lsrk_value((real)v[k], (real)s[k], (real)h[k], (real)LSRK_A[st], (real)LSRK_B[st],
+                   (real)dt, &dq[k], &q[k]);
     }
   for (size_t k = 0; k < tot; k++) qd[k] = (double)q[k];
   free(q);

@@ -89,8 +89,8 @@ MUTATIONS = [
     ("surface term sign",
      "surf[((size_t)e * NV + v) * np + i] -= s / (J[i] * B->w[own_end]) * Fs[v];",
      "surf[((size_t)e * NV + v) * np + i] += s / (J[i] * B->w[own_end]) * Fs[v];"),
-    ("volume term sign", "vol[((size_t)e * NV + v) * np + i] = -acc[v] / J[i];",
-     "vol[((size_t)e * NV + v) * np + i] = acc[v] / J[i];"),
+    ("volume term sign", "static real volume_value(real acc, real J) { return -acc / J; }",
+     "static real volume_value(real acc, real J) { return acc / J; }"),
     ("warp amplitude doubled in x", "out[0] += a * L[0] * s1 * s2;",
      "out[0] += 2 * a * L[0] * s1 * s2;"),
     ("smooth bubble profile", "(real)amp * (1 + cos(pi * r / (real)radius)) / 2",
