@@ -526,7 +526,8 @@ def run_channel(args):
     right-hand sides to the CPU oracle; the oracle itself would need ~2 h for 500 steps of
     this mesh).  Reports per-variable relative errors of the state and of the flow (state
     minus initial state, momentum as one vector), relative drift of mass and total energy
-    for both precisions, and DOF-updates/s per RK stage."""
+    for both precisions, and DOF-updates/s per RK stage; the mixed path twice, with the
+    channel state at rest as background and with the balanced jet as a moving background."""
     import numpy as np
     import torch
     from paper_2605_16684_gb300 import _build, _lib
@@ -534,10 +535,11 @@ def run_channel(args):
     c = CHANNEL
     res = {}
     dt = None
-    for prec in ("fp64", "mixed"):
+    for case in ("fp64", "mixed", "jet"):
+        prec = "fp64" if case == "fp64" else "mixed"
         s = _lib.Solver(*c["K"], c["N"], lo=c["lo"], hi=c["hi"], periodic=c["periodic"],
                         precision=prec, f0=c["f0"])
-        s.init_channel()
+        s.init_channel(background="jet" if case == "jet" else "rest")
         q0 = s.get_state()
         if dt is None:
             dt = s.cfl_dt(c["cfl"])
@@ -551,16 +553,23 @@ def run_channel(args):
         el = time.perf_counter() - t
         i1 = s.integrals()
         q = s.get_state()
-        res[prec] = dict(q=q, q0=q0, s=el, ndof=s.E * s.np,
+        res[case] = dict(q=q, q0=q0, s=el, ndof=s.E * s.np,
                          drift=[float((i1[k] - i0[k]) / abs(i0[k])) for k in (0, 1)])
         s.close()
-    q64, q32, q0 = res["fp64"]["q"], res["mixed"]["q"], res["fp64"]["q0"]
-    state_err = [float(np.linalg.norm(q32[:, v] - q64[:, v]) / np.linalg.norm(q64[:, v]))
-                 for v in range(5)]
-    f64, f32 = q64 - q0, q32 - q0
+    q64, q0 = res["fp64"]["q"], res["fp64"]["q0"]
+    f64 = q64 - q0
     mom = np.sqrt(sum(np.linalg.norm(f64[:, v]) ** 2 for v in (1, 2, 3)))
-    flow_err = [float(np.linalg.norm(f32[:, v] - f64[:, v]) /
+
+    def errors(q32):
+        state = [float(np.linalg.norm(q32[:, v] - q64[:, v]) / np.linalg.norm(q64[:, v]))
+                 for v in range(5)]
+        f32 = q32 - q0
+        flow = [float(np.linalg.norm(f32[:, v] - f64[:, v]) /
                       (mom if v in (1, 2, 3) else np.linalg.norm(f64[:, v]))) for v in range(5)]
+        return state, flow
+
+    state_err, flow_err = errors(res["mixed"]["q"])
+    state_jet, flow_jet = errors(res["jet"]["q"])
     out = {"metric": "channel: mixed vs FP64 per-variable error, conservation drift, "
                      "DOF-updates/s per RK stage",
            "unit": "relative / DOF-updates/s", "n_gpus": 1, "steps": args.steps, "dt_s": dt,
@@ -571,6 +580,10 @@ def run_channel(args):
                       "reference": "FP64 GPU path (RHS parity with the CPU oracle <= 1e-12)"},
            "state_rel_err_rho_rhou_rhov_rhow_E": state_err,
            "flow_rel_err_rho_rhou_rhov_rhow_E": flow_err,
+           "jet_background": {"state_rel_err_rho_rhou_rhov_rhow_E": state_jet,
+                              "flow_rel_err_rho_rhou_rhov_rhow_E": flow_jet,
+                              "mass_energy_drift": res["jet"]["drift"],
+                              "value": res["jet"]["ndof"] * 5 * args.steps / res["jet"]["s"]},
            "mass_energy_drift_fp64": res["fp64"]["drift"],
            "mass_energy_drift_mixed": res["mixed"]["drift"],
            "fp64_value": res["fp64"]["ndof"] * 5 * args.steps / res["fp64"]["s"],

@@ -124,8 +124,17 @@ int es_dg_init_bubble_profile(es_dg_t* h, double theta0, double amp, const doubl
  * 3000 km)/600 km)), rho = p/(g H), zonal wind in geostrophic balance
  * u = -g z H'(y)/(f H) with f = f0 + beta (y - y0), plus the perturbation
  * 1 m/s exp(-((x - 2000 km)^2 + (y - 2500 km)^2)/(600 km)^2); v = w = 0.
- * Needs f != 0 somewhere (ES_DG_EINVAL when f0 = beta = 0). */
+ * Needs f != 0 somewhere (ES_DG_EINVAL when f0 = beta = 0).  A mixed handle gets
+ * the channel state at rest as its background (es_dg_set_background). */
 int es_dg_init_channel(es_dg_t* h);
+/* The channel state with the perturbation's amplitude amp (m/s; 1 in
+ * es_dg_init_channel, 0 the balanced jet alone) and the mixed path's background
+ * chosen: ES_DG_BACKGROUND_REST as es_dg_init_channel, ES_DG_BACKGROUND_JET the
+ * balanced jet itself, carried with its flow (es_dg_set_moving_background; whole
+ * meshes only, ES_DG_EINVAL on a partition).  No background in FP64 mode.
+ * ES_DG_EINVAL: amp not finite, another background value, f0 = beta = 0. */
+enum { ES_DG_BACKGROUND_REST = 0, ES_DG_BACKGROUND_JET = 1 };
+int es_dg_init_channel_ex(es_dg_t* h, double amp, int background);
 
 /* Hydrostatic background of the mixed-precision path (the perturbation-variable
  * formulation the paper suggests for 32-bit runs, Section 5.2).  From q_bg the
@@ -139,6 +148,20 @@ int es_dg_init_channel(es_dg_t* h);
  * channel state at rest as background automatically.  No effect in FP64 mode.
  * Synchronous when on_device = 0.  es_dg_clear_background returns to plain FP32. */
 int es_dg_set_background(es_dg_t* h, const double* q_bg, int on_device);
+/* A moving background: q_bg itself, flow included (Section 5.2's perturbation
+ * formulation extended to a background that carries a flow, e.g. the channel's
+ * balanced jet, whose density and energy right-hand sides cancel convective
+ * fluxes far larger than themselves).  The library evaluates rhs(q_bg) once in
+ * FP64 (every component, the Coriolis force of its momentum included) and forms
+ * every flux of the FP32 bracket rhs(q) - rhs(q_bg) as an exact difference in
+ * perturbation variables (rho', m', E', u', p', b'), so FP32 rounding is relative
+ * to q - q_bg.  Requirements of the formulation: q_bg continuous across faces and
+ * tangential at walls (u_bg . n = 0 there), as a state given per node of one
+ * mesh is when it comes from a smooth field of position with that property.
+ * Whole meshes only (ES_DG_EINVAL on a partition; the server's batched kernels
+ * carry only a background at rest).  No effect in FP64 mode.  Synchronous when
+ * on_device = 0; q_bg (nelem*5*np doubles) is copied. */
+int es_dg_set_moving_background(es_dg_t* h, const double* q_bg, int on_device);
 int es_dg_clear_background(es_dg_t* h);
 
 /* One evaluation of the right-hand side dq/dt of Eq. (nm:semi) at state q

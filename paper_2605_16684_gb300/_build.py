@@ -14,8 +14,8 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(BUILD, "libesdg.so")
 
-SOURCES = ["volume64.cu", "volume32.cu", "surface.cu", "geometry.cu", "reduce.cu", "api.cu",
-           "serve.cu", "checks.cu", "lgl.cpp"]
+SOURCES = ["volume64.cu", "volume32.cu", "volume32m.cu", "surface.cu", "geometry.cu", "reduce.cu",
+           "api.cu", "serve.cu", "checks.cu", "lgl.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -83,8 +83,10 @@ SIGNATURES = {
     "es_dg_init_bubble_profile": (C.c_int, [_VP, C.c_double, C.c_double, _DP, C.c_double,
                                             C.c_int]),
     "es_dg_init_channel": (C.c_int, [_VP]),
+    "es_dg_init_channel_ex": (C.c_int, [_VP, C.c_double, C.c_int]),
     "es_dg_rhs": (C.c_int, [_VP, _VP, _VP, C.c_int]),
     "es_dg_set_background": (C.c_int, [_VP, _VP, C.c_int]),
+    "es_dg_set_moving_background": (C.c_int, [_VP, _VP, C.c_int]),
     "es_dg_clear_background": (C.c_int, [_VP]),
     "es_dg_cfl_dt": (C.c_int, [_VP, C.c_double, _DP]),
     "es_dg_step": (C.c_int, [_VP, C.c_double, C.c_int]),
@@ -289,12 +291,27 @@ class Solver:
         check(self.lib.es_dg_init_bubble_profile(self.h, theta0, amp, c, radius, k),
               "es_dg_init_bubble_profile")
 
-    def init_channel(self):
-        check(self.lib.es_dg_init_channel(self.h), "es_dg_init_channel")
+    def init_channel(self, amp=None, background=None):
+        """The channel state; with amp (m/s) or background ("rest" or "jet") given,
+        es_dg_init_channel_ex, else es_dg_init_channel (amp 1, background at rest)."""
+        if amp is None and background is None:
+            check(self.lib.es_dg_init_channel(self.h), "es_dg_init_channel")
+            return
+        kinds = {"rest": 0, "jet": 1}
+        if (background or "rest") not in kinds:
+            raise ValueError("background: 'rest' or 'jet'")
+        check(self.lib.es_dg_init_channel_ex(self.h, float(1.0 if amp is None else amp),
+                                             kinds[background or "rest"]),
+              "es_dg_init_channel_ex")
 
     def set_background(self, q_bg):
         check(self.lib.es_dg_set_background(self.h, C.c_void_p(_ptr(q_bg)), _on_device(q_bg)),
               "es_dg_set_background")
+
+    def set_moving_background(self, q_bg):
+        check(self.lib.es_dg_set_moving_background(self.h, C.c_void_p(_ptr(q_bg)),
+                                                   _on_device(q_bg)),
+              "es_dg_set_moving_background")
 
     def clear_background(self):
         check(self.lib.es_dg_clear_background(self.h), "es_dg_clear_background")
@@ -390,9 +407,9 @@ class PartitionedSolver:
         for s in self.parts:
             s.init_bubble(**kw)
 
-    def init_channel(self):
+    def init_channel(self, amp=None, background=None):
         for s in self.parts:
-            s.init_channel()
+            s.init_channel(amp, background)
 
     def exchange(self):
         check(self.lib.es_dg_partitions_exchange(self._arr, len(self.parts)),

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/es_dg.h: handle management, buffers and launch
 // sequences.  All arithmetic happens in the kernels; this file only validates
 // arguments, owns device memory and orders launches on the handle's stream.
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -54,6 +55,13 @@ struct es_dg {
   double* bg3;
   float* bgp;
   float* rhs_bg32;
+  // a moving background (carries a flow; whole meshes only): its state bgq
+  // [E][5][np], u_bg in FP32 bgu [E][3][np], its full right-hand side in FP32
+  // rhs_bgm32 [E][5][np]
+  int bg_moving;
+  double* bgq;
+  float* bgu;
+  float* rhs_bgm32;
   // a partition's trace buffers (caller-owned device memory; [0] low x plane, [1] high)
   double* tr_send[2];
   double* tr_recv[2];
@@ -158,6 +166,10 @@ EsdgVolArgs vol_args(es_dg_t* h, const double* q_in, double* rhs_out) {
   a.bg = (h->mixed && h->has_bg) ? h->bg3 : nullptr;
   a.bgp = h->bgp;
   a.rhs_bg = h->rhs_bg32;
+  const bool moving = h->mixed && h->has_bg && h->bg_moving;
+  a.bgq = moving ? h->bgq : nullptr;
+  a.bgu = moving ? h->bgu : nullptr;
+  a.rhs_bgm = moving ? h->rhs_bgm32 : nullptr;
   a.rkA = 0.0;
   a.rkB = 0.0;
   a.dt = 0.0;
@@ -195,8 +207,10 @@ int launch_stage(es_dg_t* h, const double* q_in, int mode, double* rhs_out, doub
     const int st = resolve_background(h);
     if (st) return st;
   }
+  const bool moving = h->mixed && h->has_bg && h->bg_moving;
   cudaError_t e = esdg_launch_face(h->g, h->P, h->mixed, q_in, h->fgeo, h->fflux, h->stream,
-                                   (h->mixed && h->has_bg) ? h->bg : nullptr, traces_of(h));
+                                   (h->mixed && h->has_bg) ? h->bg : nullptr, traces_of(h),
+                                   moving ? h->bgq : nullptr);
   if (e != cudaSuccess) return cuda_status(e);
   EsdgVolArgs a = vol_args(h, q_in, rhs_out);
   a.rkA = A;
@@ -222,6 +236,7 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
   if (st) return st;
   double* q0 = h->qtmp;
   if (q_dev == q0) return ES_DG_EINVAL;
+  h->bg_moving = 0;
   cudaError_t e = esdg_launch_background(h->g, h->P, h->vgeo, q_dev, h->bg, q0, h->stream);
   if (e == cudaSuccess)
     e = esdg_launch_background_vol(h->g, h->P, h->vgeo, h->bg, h->bg3, h->bgp, h->stream);
@@ -248,6 +263,50 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
   if (e == cudaSuccess) e = esdg_launch_to_f32(h->rhs_bg, h->rhs_bg32, (long long)E * 3 * np, h->stream);
   if (e != cudaSuccess) return cuda_status(e);
   h->has_bg = 1;
+  h->bg_moving = 0;
+  return ES_DG_OK;
+}
+
+// Set a moving background from state q_dev (device; whole meshes only): the
+// state itself with its flow, its rho_bg, b_bg, p_bg and FP32 fields as for a
+// background at rest, u_bg in FP32, and its full right-hand side evaluated
+// once with the FP64 kernels (every component: a moving background's density
+// and energy fluxes do not vanish).
+int set_moving_background_dev(es_dg_t* h, const double* q_dev) {
+  if (is_partition(h)) return ES_DG_EINVAL;
+  const size_t E = h->g.E, np = h->g.np, nf2 = (size_t)h->g.Nq * h->g.Nq;
+  int st = ensure_rhs_buffers(h);
+  if (!st && !h->bg) st = dev_alloc(h, (void**)&h->bg, E * 3 * np * sizeof(double));
+  if (!st && !h->fflux64)
+    st = dev_alloc(h, (void**)&h->fflux64, (size_t)h->g.nfaces * 5 * nf2 * sizeof(double));
+  if (!st && !h->bg3) st = dev_alloc(h, (void**)&h->bg3, E * 3 * np * sizeof(double));
+  if (!st && !h->bgp) st = dev_alloc(h, (void**)&h->bgp, E * 4 * np * sizeof(float));
+  if (!st && !h->bgq) st = dev_alloc(h, (void**)&h->bgq, E * 5 * np * sizeof(double));
+  if (!st && !h->bgu) st = dev_alloc(h, (void**)&h->bgu, E * 3 * np * sizeof(float));
+  if (!st && !h->rhs_bgm32) st = dev_alloc(h, (void**)&h->rhs_bgm32, E * 5 * np * sizeof(float));
+  if (st) return st;
+  if (q_dev == h->qtmp) return ES_DG_EINVAL;
+  h->has_bg = 0;  // until the new background is complete
+  cudaError_t e = cudaMemcpyAsync(h->bgq, q_dev, E * 5 * np * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = esdg_launch_background(h->g, h->P, h->vgeo, h->bgq, h->bg, h->qtmp, h->stream);
+  if (e == cudaSuccess)
+    e = esdg_launch_background_vol(h->g, h->P, h->vgeo, h->bg, h->bg3, h->bgp, h->stream);
+  if (e == cudaSuccess) e = esdg_launch_background_velocity(h->g, h->bgq, h->bgu, h->stream);
+  if (e == cudaSuccess) e = esdg_launch_face(h->g, h->P, 0, h->bgq, h->fgeo, h->fflux64, h->stream);
+  if (e == cudaSuccess) {
+    EsdgVolArgs a = vol_args(h, h->bgq, h->rhs);
+    a.vgeo = h->vgeo;
+    a.fflux = h->fflux64;
+    a.bg = nullptr;
+    a.bgq = nullptr;
+    e = esdg_launch_volume(h->g, h->L, h->P, 0, 0, a, h->stream);
+  }
+  if (e == cudaSuccess) e = esdg_launch_to_f32(h->rhs, h->rhs_bgm32, (long long)E * 5 * np, h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  h->has_bg = 1;
+  h->bg_moving = 1;
   return ES_DG_OK;
 }
 
@@ -302,6 +361,7 @@ int esdg_take_status(es_dg_t* h) {
 int esdg_member_descriptor(es_dg_t* h, double dt, EsdgMember* out, EsdgLGL* L, int* mixed) {
   if (!h || !out) return ES_DG_EINVAL;
   if (h->mixed && !h->has_bg) return ES_DG_EINVAL;
+  if (h->mixed && h->bg_moving) return ES_DG_EINVAL;  // batched kernels: a background at rest
   if (is_partition(h)) return ES_DG_EINVAL;  // batched members are whole meshes
   std::memset(out, 0, sizeof(*out));
   out->g = h->g;
@@ -523,11 +583,29 @@ int es_dg_init_bubble_profile(es_dg_t* h, double theta0, double amp, const doubl
 }
 
 int es_dg_init_channel(es_dg_t* h) {
-  if (!h) return ES_DG_EINVAL;
+  return es_dg_init_channel_ex(h, 1.0, ES_DG_BACKGROUND_REST);
+}
+
+int es_dg_init_channel_ex(es_dg_t* h, double amp, int background) {
+  if (!h || !std::isfinite(amp)) return ES_DG_EINVAL;
+  if (background != ES_DG_BACKGROUND_REST && background != ES_DG_BACKGROUND_JET)
+    return ES_DG_EINVAL;
   if (h->P.f0 == 0.0 && h->P.beta == 0.0) return ES_DG_EINVAL;  // geostrophic balance needs f
-  cudaError_t e = esdg_launch_channel(h->g, h->P, h->x, h->q, h->stream);
+  if (h->mixed && background == ES_DG_BACKGROUND_JET && is_partition(h)) return ES_DG_EINVAL;
+  cudaError_t e;
+  if (h->mixed && background == ES_DG_BACKGROUND_JET) {
+    // the balanced jet alone (no perturbation), carried with its velocity
+    int st = ensure_rhs_buffers(h);
+    if (st) return st;
+    e = esdg_launch_channel(h->g, h->P, h->x, h->q, 0.0, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    st = set_moving_background_dev(h, h->q);
+    if (st) return st;
+  }
+  e = esdg_launch_channel(h->g, h->P, h->x, h->q, amp, h->stream);
   if (e != cudaSuccess) return cuda_status(e);
-  if (h->mixed) return set_background_dev(h, h->q);  // the jump-free state at rest
+  if (h->mixed && background == ES_DG_BACKGROUND_REST)
+    return set_background_dev(h, h->q);  // the state at rest
   return ES_DG_OK;
 }
 
@@ -546,10 +624,26 @@ int es_dg_set_background(es_dg_t* h, const double* q_bg, int on_device) {
   return st;
 }
 
+int es_dg_set_moving_background(es_dg_t* h, const double* q_bg, int on_device) {
+  if (!h || !q_bg) return ES_DG_EINVAL;
+  if (!h->mixed) return ES_DG_OK;  // the FP64 path needs no background
+  if (is_partition(h)) return ES_DG_EINVAL;
+  const size_t bytes = (size_t)h->g.E * 5 * h->g.np * sizeof(double);
+  int st = ensure_rhs_buffers(h);
+  if (st) return st;
+  cudaError_t e = cudaMemcpyAsync(h->rhs, q_bg, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                                 : cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  st = set_moving_background_dev(h, h->rhs);
+  if (!st && !on_device) st = cuda_status(cudaStreamSynchronize(h->stream));
+  return st;
+}
+
 int es_dg_clear_background(es_dg_t* h) {
   if (!h) return ES_DG_EINVAL;
   h->has_bg = 0;
   h->bg_pending = 0;
+  h->bg_moving = 0;
   return ES_DG_OK;
 }
 
@@ -644,8 +738,9 @@ int es_dg_launch(es_dg_t* h, int which, int stage, double dt) {
   }
   if (which == 0)
     return cuda_status(esdg_launch_face(h->g, h->P, h->mixed, h->q, h->fgeo, h->fflux, h->stream,
-                                        (h->mixed && h->has_bg) ? h->bg : nullptr,
-                                        traces_of(h)));
+                                        (h->mixed && h->has_bg) ? h->bg : nullptr, traces_of(h),
+                                        (h->mixed && h->has_bg && h->bg_moving) ? h->bgq
+                                                                                : nullptr));
   if (which == 1) {
     int st = ensure_rhs_buffers(h);
     if (st) return st;

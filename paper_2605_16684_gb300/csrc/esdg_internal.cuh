@@ -293,14 +293,17 @@ cudaError_t esdg_launch_geometry(const EsdgGrid& g, const EsdgLGL& L, double* x,
 cudaError_t esdg_launch_bubble(const EsdgGrid& g, const EsdgPhys& P, const double* x, double theta0,
                                double amp, const double* centre, double radius, int sharp,
                                double* q, cudaStream_t s);
+// amp: amplitude of the Gaussian wind perturbation (m/s); 0 gives the balanced jet alone
 cudaError_t esdg_launch_channel(const EsdgGrid& g, const EsdgPhys& P, const double* x, double* q,
-                                cudaStream_t s);
+                                double amp, cudaStream_t s);
 cudaError_t esdg_launch_background(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
                                    const double* q, double* bg, double* q0, cudaStream_t s);
+// bgq: a moving background's state [E][5][np] (mixed with bg only; null at rest)
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
                              const double* fgeo, void* fflux, cudaStream_t s,
                              const double* bg = nullptr,
-                             EsdgTraces tr = EsdgTraces{nullptr, nullptr, 5, 0});
+                             EsdgTraces tr = EsdgTraces{nullptr, nullptr, 5, 0},
+                             const double* bgq = nullptr);
 // Pack a partition's own traces for its neighbours: the state of the first
 // element layer's i = 0 nodes into send_lo (if remote[0]) and of the last
 // layer's i = N nodes into send_hi (if remote[1]), layout of EsdgTraces.
@@ -310,6 +313,10 @@ cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, const dou
 // rho_bg/4, b_bg/2, 1/b_bg, p_bg FP32) from the stored background bg.
 cudaError_t esdg_launch_background_vol(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
                                        const double* bg, double* bg3, float* bgp, cudaStream_t s);
+// A moving background's FP32 velocity u_bg = m_bg/rho_bg from its state bgq
+// ([E][5][np]) into bgu ([E][3][np]).
+cudaError_t esdg_launch_background_velocity(const EsdgGrid& g, const double* bgq, float* bgu,
+                                            cudaStream_t s);
 // dst[i] = src[i] rounded to FP32, i < n
 cudaError_t esdg_launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 // The background state at rest from the stored background, per node:
@@ -330,10 +337,18 @@ struct EsdgVolArgs {
   const double* bg;      // mixed mode with a background: [E][3][np] rho_bg, E_bg, phi (else null)
   const float* bgp;      // mixed mode with a background: [E][4][np] rho_bg/4, b_bg/2, 1/b_bg, p_bg
   const float* rhs_bg;   // mixed mode with a background: [E][3][np] momentum rhs of it (FP32)
+  // a moving background (one that carries a flow, e.g. a balanced jet); null at rest:
+  const double* bgq;     // [E][5][np] the background state itself (rho_bg, m_bg, E_bg)
+  const float* bgu;      // [E][3][np] u_bg in FP32
+  const float* rhs_bgm;  // [E][5][np] the background's full right-hand side (FP32)
   double rkA, rkB, dt;
   int* status;           // mode 1: set to 1 when an updated state value is not finite or a
                          // density is not positive (null: not checked)
 };
+// The mixed volume kernel with a moving background (per-tile kernel; its own
+// translation unit): mode 0 writes rhs, mode 1 applies the LSRK stage.
+cudaError_t esdg_launch_volume_mixed_moving(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys& P,
+                                            int mode, const EsdgVolArgs& a, cudaStream_t s);
 // One mesh of a batch: everything its kernels need, read by the persistent
 // batched kernels from a device array (one entry per resident solve).
 struct EsdgMember {
@@ -342,7 +357,7 @@ struct EsdgMember {
   EsdgVolArgs a;       // q_in == q_io: the member's state; dq, geometry, face fluxes, dt
   const double* fgeo;  // face geometry
   const double* bg;    // mixed background (rho_bg, b_bg, p_bg, for the faces) or null
-  long long pad;
+  // (sizeof a multiple of 16 bytes: the pipelined kernels bulk-copy descriptors)
 };
 
 // Batched persistent launches over device work tables (tiles: int2 (member,

@@ -199,16 +199,17 @@ __global__ void k_bubble(EsdgGrid g, EsdgPhys P, const double* __restrict__ x, d
 }
 
 // Synthetic channel: ln p = ln p0 - z/H(y), H = H0 + dH (1 - tanh((y - yc)/delta))/2,
-// rho = p/(g H), geostrophic u = -g z H'(y)/(f H), plus a 1 m/s Gaussian in u.
+// rho = p/(g H), geostrophic u = -g z H'(y)/(f H), plus a Gaussian of amplitude up in u
+// (1 m/s in the channel workload; 0 gives the balanced jet alone).
 __global__ void k_channel(EsdgGrid g, EsdgPhys P, const double* __restrict__ x,
-                          double* __restrict__ q) {
+                          double* __restrict__ q, double up) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int np = g.np;
   if (tid >= (long long)g.E * np) return;
   const long long e = tid / np;
   const int n = (int)(tid - e * np);
   const double H0 = 7500.0, dH = 120.0, delta = 600e3, yc = 3000e3;
-  const double xp = 2000e3, yp = 2500e3, Lp = 600e3, up = 1.0;
+  const double xp = 2000e3, yp = 2500e3, Lp = 600e3;
   const double X = x[(e * 3 + 0) * np + n], Y = x[(e * 3 + 1) * np + n], Z = x[(e * 3 + 2) * np + n];
   const double th = tanh((Y - yc) / delta);
   const double H = H0 + dH * 0.5 * (1.0 - th);
@@ -297,6 +298,19 @@ __global__ void k_background_vol(EsdgGrid g, EsdgPhys P, const double* __restric
   bgp[(e * 4 + 3) * np + n] = __double2float_rn(p);
 }
 
+// u_bg = m_bg / rho_bg of a moving background, rounded to FP32
+__global__ void k_background_velocity(EsdgGrid g, const double* __restrict__ bgq,
+                                      float* __restrict__ bgu) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int np = g.np;
+  if (tid >= (long long)g.E * np) return;
+  const long long e = tid / np;
+  const int n = (int)(tid - e * np);
+  const double* qe = bgq + e * 5 * np;
+  const double ir = 1.0 / qe[n];
+  for (int d = 0; d < 3; d++) bgu[(e * 3 + d) * np + n] = __double2float_rn(qe[(1 + d) * np + n] * ir);
+}
+
 __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = __double2float_rn(src[i]);
@@ -309,6 +323,14 @@ cudaError_t esdg_launch_background_vol(const EsdgGrid& g, const EsdgPhys& P, con
   const long long nt = (long long)g.E * g.np;
   if (nt == 0) return cudaSuccess;
   k_background_vol<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, P, vgeo, bg, bg3, bgp);
+  return cudaGetLastError();
+}
+
+cudaError_t esdg_launch_background_velocity(const EsdgGrid& g, const double* bgq, float* bgu,
+                                            cudaStream_t s) {
+  const long long nt = (long long)g.E * g.np;
+  if (nt == 0) return cudaSuccess;
+  k_background_velocity<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, bgq, bgu);
   return cudaGetLastError();
 }
 
@@ -363,8 +385,8 @@ cudaError_t esdg_launch_bubble(const EsdgGrid& g, const EsdgPhys& P, const doubl
 }
 
 cudaError_t esdg_launch_channel(const EsdgGrid& g, const EsdgPhys& P, const double* x, double* q,
-                                cudaStream_t s) {
+                                double amp, cudaStream_t s) {
   const long long nt = (long long)g.E * g.np;
-  k_channel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, P, x, q);
+  k_channel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(g, P, x, q, amp);
   return cudaGetLastError();
 }

@@ -197,22 +197,63 @@ __device__ __forceinline__ void face_flux(const Side<R>& M, const Side<R>& Pp, R
   F[4] = fma((R)-0.5, dE, F[4]);
 }
 
-// Mixed precision relative to a hydrostatic background (u_bg = 0, continuous
-// across faces): the face flux's background part is the Euler flux
-// (0, p_bg nhat, 0), so the kernel stores F* - (0, p_bg nhat, 0).  Its momentum
-// pressure p* - p_bg and the jumps feeding the dissipation ([[rho]], [[b]],
-// [[b u]], [[b |u|^2]]) come in from FP64 differences, so FP32 rounding is
-// relative to the perturbations and jumps, not to the state.
+// Jumps and pressure mean of a face node relative to a background, formed from
+// FP64 differences (see face_node): [[rho]], [[b]], [[b u]], [[b |u|^2]] and
+// p* - p_bg, each with its FP32 rounding relative to the perturbations and jumps.
 struct BgFace {
   float dr, db, dbu0, dbu1, dbu2, dbuu, ptp;
 };
 
+// The matrix dissipation of the face flux from the jumps J (FP32, relative to
+// the perturbations) and the averaged state: F -= 1/2 R |Lambda| T R^T [[v]].
+__device__ __forceinline__ void dissipate_bg(float phi, float n0, float n1, float n2, float gamma,
+                                             float igm1, float igamma, const BgFace& J,
+                                             bool r_small, float rsr, float ur, float lnr_jump,
+                                             float lnb_jump, float rho_log, float pt, float u0,
+                                             float u1, float u2, float un, float* F) {
+  using Mth = FaceMath<float>;
+  const float gm1 = gamma - 1.0f;
+  const float half = 0.5f;
+  const float dr = J.dr, db = J.db;
+  const float jv1 = lnr_jump + lnb_jump * igm1 - J.dbuu + 2.0f * phi * db;
+  const float jm0 = 2.0f * J.dbu0, jm1 = 2.0f * J.dbu1, jm2 = 2.0f * J.dbu2;
+  const float jv5 = -2.0f * db;
+  const float irh = r_small ? 2.0f * rsr * Mth::A(ur) : lnr_jump / dr;
+  const float a2 = gamma * pt * irh;
+  const float a = sqrtf(a2);
+  const float k2 = half * (u0 * u0 + u1 * u1 + u2 * u2) + phi;
+  const float a2g = a2 * igm1;
+  const float H = a2g + k2;
+  const float njm = n0 * jm0 + n1 * jm1 + n2 * jm2;
+  const float w2 = jv1 + u0 * jm0 + u1 * jm1 + u2 * jm2 + k2 * jv5;
+  const float ac = a2g * jv5;
+  const float w1 = w2 - a * njm + ac - a * un * jv5;
+  const float w5 = w2 + a * njm + ac + a * un * jv5;
+  const float c1 = fabsf(un - a) * rho_log * half * igamma * w1;
+  const float c2 = fabsf(un) * rho_log * gm1 * igamma * w2;
+  const float c5 = fabsf(un + a) * rho_log * half * igamma * w5;
+  const float ls = fabsf(un) * pt;
+  const float y0 = jm0 + u0 * jv5, y1 = jm1 + u1 * jv5, y2 = jm2 + u2 * jv5;
+  const float yn = y0 * n0 + y1 * n1 + y2 * n2;
+  const float t0 = y0 - yn * n0, t1 = y1 - yn * n1, t2 = y2 - yn * n2;
+  const float csum = c1 + c2 + c5, cdif = c5 - c1;
+  F[0] -= half * csum;
+  F[1] -= half * (csum * u0 + a * cdif * n0 + ls * t0);
+  F[2] -= half * (csum * u1 + a * cdif * n1 + ls * t1);
+  F[3] -= half * (csum * u2 + a * cdif * n2 + ls * t2);
+  F[4] -= half * ((c1 + c5) * H + a * un * cdif + c2 * k2 + ls * (u0 * t0 + u1 * t1 + u2 * t2));
+}
+
+// Mixed precision relative to a hydrostatic background (u_bg = 0, continuous
+// across faces): the face flux's background part is the Euler flux
+// (0, p_bg nhat, 0), so the kernel stores F* - (0, p_bg nhat, 0).  Its momentum
+// pressure p* - p_bg and the jumps feeding the dissipation come in from BgFace,
+// so FP32 rounding is relative to the perturbations and jumps, not to the state.
 __device__ __forceinline__ void face_flux_bg(const Side<float>& M, const Side<float>& Pp, float phi,
                                              float n0, float n1, float n2, float gamma, float igm1,
                                              float igamma, int dissipation, const BgFace& J,
                                              float* F) {
   using Mth = FaceMath<float>;
-  const float gm1 = gamma - 1.0f;
   const float half = 0.5f;
   const float sr = Pp.rho + M.rho, dr = J.dr;
   const float sb = Pp.b + M.b, db = J.db;
@@ -247,41 +288,95 @@ __device__ __forceinline__ void face_flux_bg(const Side<float>& M, const Side<fl
   F[3] = Fr * u2 + ptp * n2;
   F[4] = Fr * (iblog * half * igm1 + half * uu + phi) + pt * un;
   if (!dissipation) return;
-  const float jv1 = lnr_jump + lnb_jump * igm1 - J.dbuu + 2.0f * phi * db;
-  const float jm0 = 2.0f * J.dbu0, jm1 = 2.0f * J.dbu1, jm2 = 2.0f * J.dbu2;
-  const float jv5 = -2.0f * db;
-  const float irh = Mth::small(ur) ? 2.0f * rsr * Mth::A(ur) : lnr_jump / dr;
-  const float a2 = gamma * pt * irh;
-  const float a = sqrtf(a2);
-  const float k2 = half * (u0 * u0 + u1 * u1 + u2 * u2) + phi;
-  const float a2g = a2 * igm1;
-  const float H = a2g + k2;
-  const float njm = n0 * jm0 + n1 * jm1 + n2 * jm2;
-  const float w2 = jv1 + u0 * jm0 + u1 * jm1 + u2 * jm2 + k2 * jv5;
-  const float ac = a2g * jv5;
-  const float w1 = w2 - a * njm + ac - a * un * jv5;
-  const float w5 = w2 + a * njm + ac + a * un * jv5;
-  const float c1 = fabsf(un - a) * rho_log * half * igamma * w1;
-  const float c2 = fabsf(un) * rho_log * gm1 * igamma * w2;
-  const float c5 = fabsf(un + a) * rho_log * half * igamma * w5;
-  const float ls = fabsf(un) * pt;
-  const float y0 = jm0 + u0 * jv5, y1 = jm1 + u1 * jv5, y2 = jm2 + u2 * jv5;
-  const float yn = y0 * n0 + y1 * n1 + y2 * n2;
-  const float t0 = y0 - yn * n0, t1 = y1 - yn * n1, t2 = y2 - yn * n2;
-  const float csum = c1 + c2 + c5, cdif = c5 - c1;
-  F[0] -= half * csum;
-  F[1] -= half * (csum * u0 + a * cdif * n0 + ls * t0);
-  F[2] -= half * (csum * u1 + a * cdif * n1 + ls * t1);
-  F[3] -= half * (csum * u2 + a * cdif * n2 + ls * t2);
-  F[4] -= half * ((c1 + c5) * H + a * un * cdif + c2 * k2 + ls * (u0 * t0 + u1 * t1 + u2 * t2));
+  dissipate_bg(phi, n0, n1, n2, gamma, igm1, igamma, J, Mth::small(ur), rsr, ur, lnr_jump,
+               lnb_jump, rho_log, pt, u0, u1, u2, un, F);
 }
 
-// One face node (global face-node index tid) of one mesh.
-template <typename R, int N, bool BG>
+// A moving background (a flow carried by the background, continuous across
+// faces and tangential at walls): the face flux's background part is the
+// Euler flux f(q_bg).n, so the kernel stores F* - f(q_bg).n.  With primes for
+// state minus background, {{.}} the two-side average and un = {{u}}.n:
+//   F^rho - f^rho_bg = (<rho>_log - rho_bg) un + rho_bg {{u'}}.n,
+//     <rho>_log - rho_bg = {{rho'}} Q(u) + rho_bg (Q(u) - 1)   (series branch),
+//   F^m - f^m_bg     = (F^rho - f^rho_bg) {{u}} + f^rho_bg {{u'}} + (p* - p_bg) n,
+//   F^E - f^E_bg     = (F^rho - f^rho_bg) W + f^rho_bg W' + (p* - p_bg) un + p_bg {{u'}}.n,
+// W = 1/(2 (gamma-1) <b>_log) + u-.u+/2 + phi, W' = (1/<b>_log - 1/b_bg)/(2 (gamma-1))
+// + (u-'.u+ + u_bg.u+')/2 and 1/<b>_log - 1/b_bg = ((A(u) - 1) - {{b'}}/b_bg)/{{b}}
+// (series branch).  The dissipation is that of face_flux_bg (jumps only).
+struct BgMove {
+  float rb, ibb, pb;                   // background rho, 1/b, p at the node
+  float ub0, ub1, ub2;                 // background velocity
+  float vm0, vm1, vm2, vp0, vp1, vp2;  // u' = u - u_bg on the two sides
+  float rpbar, bpbar;                  // {{rho'}}, {{b'}}
+};
+
+__device__ __forceinline__ void face_flux_bgm(const Side<float>& M, const Side<float>& Pp,
+                                              float phi, float n0, float n1, float n2, float gamma,
+                                              float igm1, float igamma, int dissipation,
+                                              const BgFace& J, const BgMove& G, float* F) {
+  using Mth = FaceMath<float>;
+  const float half = 0.5f;
+  const float sr = Pp.rho + M.rho, dr = J.dr;
+  const float sb = Pp.b + M.b, db = J.db;
+  const float rsr = Mth::rcp(sr), rsb = Mth::rcp(sb);
+  const float fr = dr * rsr, ur = fr * fr;
+  const float fb = db * rsb, ub = fb * fb;
+  float rho_log, lnr_jump, iblog, lnb_jump, rlp, ibp;
+  if (Mth::small(ur)) {
+    const float Qr = Mth::Q(ur);
+    rho_log = half * sr * Qr;
+    lnr_jump = 2.0f * fr * Mth::A(ur);
+    // Q(u) - 1 = u (-1/3 - 4u/45 - 44u^2/945)
+    const float qm1 = ur * fmaf(ur, fmaf(ur, -44.0f / 945.0f, -4.0f / 45.0f), -1.0f / 3.0f);
+    rlp = fmaf(G.rpbar, Qr, G.rb * qm1);
+  } else {
+    lnr_jump = Mth::ljump(Pp.rho, M.rho, dr);
+    rho_log = dr / lnr_jump;
+    rlp = rho_log - G.rb;
+  }
+  if (Mth::small(ub)) {
+    const float Ab = Mth::A(ub);
+    iblog = 2.0f * rsb * Ab;
+    lnb_jump = 2.0f * fb * Ab;
+    // A(u) - 1 = u (1/3 + u/5 + u^2/7)
+    const float am1 = ub * fmaf(ub, fmaf(ub, 1.0f / 7.0f, 0.2f), 1.0f / 3.0f);
+    ibp = 2.0f * rsb * fmaf(-G.bpbar, G.ibb, am1);
+  } else {
+    lnb_jump = Mth::ljump(Pp.b, M.b, db);
+    iblog = lnb_jump / db;
+    ibp = iblog - G.ibb;
+  }
+  const float u0 = half * (M.u0 + Pp.u0), u1 = half * (M.u1 + Pp.u1), u2 = half * (M.u2 + Pp.u2);
+  const float v0 = half * (G.vm0 + G.vp0), v1 = half * (G.vm1 + G.vp1), v2 = half * (G.vm2 + G.vp2);
+  const float un = u0 * n0 + u1 * n1 + u2 * n2;
+  const float unp = v0 * n0 + v1 * n1 + v2 * n2;
+  const float unb = G.ub0 * n0 + G.ub1 * n1 + G.ub2 * n2;
+  const float pt = sr * rsb * half;
+  const float ptp = J.ptp;
+  const float uu = M.u0 * Pp.u0 + M.u1 * Pp.u1 + M.u2 * Pp.u2;
+  const float uup = G.vm0 * Pp.u0 + G.vm1 * Pp.u1 + G.vm2 * Pp.u2 +
+                    (G.ub0 * G.vp0 + G.ub1 * G.vp1 + G.ub2 * G.vp2);
+  const float Frp = rlp * un + G.rb * unp;
+  const float Frb = G.rb * unb;
+  F[0] = Frp;
+  F[1] = Frp * u0 + Frb * v0 + ptp * n0;
+  F[2] = Frp * u1 + Frb * v1 + ptp * n1;
+  F[3] = Frp * u2 + Frb * v2 + ptp * n2;
+  F[4] = Frp * (iblog * half * igm1 + half * uu + phi) + Frb * (ibp * half * igm1 + half * uup) +
+         ptp * un + G.pb * unp;
+  if (!dissipation) return;
+  dissipate_bg(phi, n0, n1, n2, gamma, igm1, igamma, J, Mth::small(ur), rsr, ur, lnr_jump,
+               lnb_jump, rho_log, pt, u0, u1, u2, un, F);
+}
+
+// One face node (global face-node index tid) of one mesh.  BG: 0 none, 1 a
+// background at rest (bg), 2 a moving background (bg and its state bgq).
+template <typename R, int N, int BG>
 __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
                                           const double* __restrict__ q,
                                           const double* __restrict__ fgeo, R* __restrict__ fflux,
-                                          const double* __restrict__ bg, const double* tr_lo,
+                                          const double* __restrict__ bg,
+                                          const double* __restrict__ bgq, const double* tr_lo,
                                           const double* tr_hi, int tr_nv, int tr_bg,
                                           long long tid) {
   constexpr int Nq = N + 1, NF2 = Nq * Nq, NP = Nq * Nq * Nq;
@@ -363,7 +458,92 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
   }
   const double gm1 = P.gamma - 1.0;
   R F[5];
-  if constexpr (BG) {
+  if constexpr (BG == 2) {
+    // FP64 only where the state cancels: per side rho' = rho - rho_bg,
+    // m' = m - m_bg, e' = E - E_bg - phi rho' against the background at this
+    // node (one element's value: the background is a function of position),
+    // and the jumps of rho and rho u.  Then in FP32 per side (as prims32bgm)
+    //   u' = (m' - rho' u_bg)/rho, u = u_bg + u', p' = (gamma-1)(e' - (m'.u + rho_bg u_bg.u')/2),
+    //   b' = (rho' p_bg - rho_bg p')/(2 p p_bg),
+    // and the jumps and pressure mean by the identities of the branch below,
+    // [[p]] = [[p']] and {{p}} - p_bg = {{p'}}.
+    const int eb = em >= 0 ? em : ep, nb = em >= 0 ? nm : npn;
+    const double* Qb = bgq + (size_t)eb * 5 * NP + nb;
+    const double rbd = Qb[0], ebd = Qb[4 * NP];
+    const double mbd[3] = {Qb[NP], Qb[2 * NP], Qb[3 * NP]};
+    const float rbf = esdg_d2f(rbd), pbf = esdg_d2f(pbg);
+    const float ibbf = esdg_rcpf(esdg_d2f(bg[((size_t)eb * 3 + 1) * NP + nb]));
+    const float irb = esdg_rcpf(rbf);
+    const float ubv[3] = {esdg_d2f(mbd[0]) * irb, esdg_d2f(mbd[1]) * irb, esdg_d2f(mbd[2]) * irb};
+    const float gm1f = esdg_d2f(gm1);
+    float rho[2], ir[2], v[2][3], u[2][3], pp[2], pf[2], rpf[2];
+#pragma unroll
+    for (int sd2 = 0; sd2 < 2; sd2++) {
+      const double* qs = sd2 ? qp : qm;
+      const double rp = qs[0] - rbd;
+      const double ep = fma(-phi, rp, qs[4] - ebd);
+      rpf[sd2] = esdg_d2f(rp);
+      const float epf = esdg_d2f(ep);
+      rho[sd2] = esdg_d2f(qs[0]);
+      ir[sd2] = esdg_rcpf(rho[sd2]);
+      float mf[3];
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        mf[c] = esdg_d2f(qs[1 + c] - mbd[c]);
+        v[sd2][c] = fmaf(-rpf[sd2], ubv[c], mf[c]) * ir[sd2];
+        u[sd2][c] = ubv[c] + v[sd2][c];
+      }
+      const float kb = rbf * fmaf(ubv[2], v[sd2][2], fmaf(ubv[1], v[sd2][1], ubv[0] * v[sd2][0]));
+      const float kep = 0.5f * fmaf(mf[2], u[sd2][2], fmaf(mf[1], u[sd2][1], fmaf(mf[0], u[sd2][0], kb)));
+      pp[sd2] = gm1f * (epf - kep);
+      pf[sd2] = pbf + pp[sd2];
+    }
+    const Side<float> M{rho[0], u[0][0], u[0][1], u[0][2], 0.5f * rho[0] * esdg_rcpf(pf[0])};
+    const Side<float> Pp{rho[1], u[1][0], u[1][1], u[1][2], 0.5f * rho[1] * esdg_rcpf(pf[1])};
+    const float dr = esdg_d2f(qp[0] - qm[0]);
+    const float dm0 = esdg_d2f(qp[1] - qm[1]), dm1 = esdg_d2f(qp[2] - qm[2]),
+                dm2 = esdg_d2f(qp[3] - qm[3]);
+    const float dp = pp[1] - pp[0];
+    const float rbar = 0.5f * (Pp.rho + M.rho), pbar = 0.5f * (pf[1] + pf[0]);
+    const float X = fmaf(dr, pbar, -rbar * dp);  // rho+ p- - rho- p+
+    BgFace J;
+    J.dr = dr;
+    J.db = X * esdg_rcpf(2.0f * pf[1] * pf[0]);
+    const float irbar = 0.5f * (ir[1] + ir[0]), dirr = dr * ir[1] * ir[0];
+    const float du0 = fmaf(dm0, irbar, -0.5f * (Pp.rho * Pp.u0 + M.rho * M.u0) * dirr);
+    const float du1 = fmaf(dm1, irbar, -0.5f * (Pp.rho * Pp.u1 + M.rho * M.u1) * dirr);
+    const float du2 = fmaf(dm2, irbar, -0.5f * (Pp.rho * Pp.u2 + M.rho * M.u2) * dirr);
+    const float ub0 = 0.5f * (Pp.u0 + M.u0), ub1 = 0.5f * (Pp.u1 + M.u1), ub2 = 0.5f * (Pp.u2 + M.u2);
+    const float bbar = 0.5f * (Pp.b + M.b);
+    J.dbu0 = fmaf(J.db, ub0, bbar * du0);
+    J.dbu1 = fmaf(J.db, ub1, bbar * du1);
+    J.dbu2 = fmaf(J.db, ub2, bbar * du2);
+    const float bu0 = 0.5f * (Pp.b * Pp.u0 + M.b * M.u0), bu1 = 0.5f * (Pp.b * Pp.u1 + M.b * M.u1),
+                bu2 = 0.5f * (Pp.b * Pp.u2 + M.b * M.u2);
+    J.dbuu = fmaf(J.dbu0, ub0, fmaf(J.dbu1, ub1, fmaf(J.dbu2, ub2,
+                  fmaf(bu0, du0, fmaf(bu1, du1, bu2 * du2)))));
+    const float D = fmaf(2.0f * rbar, pbar, -0.5f * dr * dp);
+    J.ptp = fmaf(dp * X, esdg_rcpf(2.0f * D), 0.5f * (pp[1] + pp[0]));
+    BgMove Gm;
+    Gm.rb = rbf;
+    Gm.ibb = ibbf;
+    Gm.pb = pbf;
+    Gm.ub0 = ubv[0];
+    Gm.ub1 = ubv[1];
+    Gm.ub2 = ubv[2];
+    Gm.vm0 = v[0][0];
+    Gm.vm1 = v[0][1];
+    Gm.vm2 = v[0][2];
+    Gm.vp0 = v[1][0];
+    Gm.vp1 = v[1][1];
+    Gm.vp2 = v[1][2];
+    Gm.rpbar = 0.5f * (rpf[0] + rpf[1]);
+    const float bpm = fmaf(rpf[0], pbf, -rbf * pp[0]) * esdg_rcpf(2.0f * pf[0] * pbf);
+    const float bpp = fmaf(rpf[1], pbf, -rbf * pp[1]) * esdg_rcpf(2.0f * pf[1] * pbf);
+    Gm.bpbar = 0.5f * (bpm + bpp);
+    face_flux_bgm(M, Pp, esdg_d2f(phi), esdg_d2f(n0), esdg_d2f(n1), esdg_d2f(n2),
+                  esdg_d2f(P.gamma), esdg_d2f(P.igm1), esdg_d2f(P.igamma), P.dissipation, J, Gm, F);
+  } else if constexpr (BG) {
     // FP64 only where the state cancels (13 instructions): each side's pressure
     // E - rho phi - KE (KE in FP32), and the jumps of rho, rho u and p.  The
     // jumps of b, b u, b |u|^2 and the pressure mean follow from them by exact
@@ -428,12 +608,13 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
   for (int v = 0; v < 5; v++) out[v * NF2 + fn] = sc * F[v];
 }
 
-template <typename R, int N, bool BG>
+template <typename R, int N, int BG>
 __global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const double* __restrict__ q,
                                               const double* __restrict__ fgeo,
                                               R* __restrict__ fflux,
-                                              const double* __restrict__ bg, EsdgTraces tr) {
-  face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, tr.lo, tr.hi, tr.nv, tr.bgmode,
+                                              const double* __restrict__ bg, EsdgTraces tr,
+                                              const double* __restrict__ bgq) {
+  face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, bgq, tr.lo, tr.hi, tr.nv, tr.bgmode,
                       (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -481,26 +662,27 @@ __global__ void __launch_bounds__(256) k_face_batch(const EsdgMember* __restrict
         dst[k] = src[k];
     }
     __syncthreads();
-    face_node<R, N, BG>(mb.g, mb.P, mb.a.q_in, mb.fgeo, (R*)mb.a.fflux, mb.bg,
+    face_node<R, N, BG>(mb.g, mb.P, mb.a.q_in, mb.fgeo, (R*)mb.a.fflux, mb.bg, nullptr,
                         nullptr, nullptr, 5, 0, (long long)tile.y + threadIdx.x);
     __syncthreads();
   }
 }
 
-template <typename R, bool BG>
+template <typename R, int BG>
 cudaError_t launch_face_t(const EsdgGrid& g, const EsdgPhys& P, const double* q, const double* fgeo,
-                          R* fflux, const double* bg, EsdgTraces tr, cudaStream_t s) {
+                          R* fflux, const double* bg, EsdgTraces tr, cudaStream_t s,
+                          const double* bgq = nullptr) {
   const long long nt = g.nfaces * g.Nq * g.Nq;
   if (nt == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((nt + 255) / 256);
   switch (g.N) {
-    case 1: k_face<R, 1, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
-    case 2: k_face<R, 2, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
-    case 3: k_face<R, 3, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
-    case 4: k_face<R, 4, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
-    case 5: k_face<R, 5, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
-    case 6: k_face<R, 6, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
-    case 7: k_face<R, 7, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr); break;
+    case 1: k_face<R, 1, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
+    case 2: k_face<R, 2, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
+    case 3: k_face<R, 3, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
+    case 4: k_face<R, 4, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
+    case 5: k_face<R, 5, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
+    case 6: k_face<R, 6, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
+    case 7: k_face<R, 7, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -526,10 +708,12 @@ cudaError_t esdg_launch_face_batch(int N, int mixed, int bg, const EsdgMember* m
 
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
                              const double* fgeo, void* fflux, cudaStream_t s, const double* bg,
-                             EsdgTraces tr) {
-  if (mixed && bg) return launch_face_t<float, true>(g, P, q, fgeo, (float*)fflux, bg, tr, s);
-  if (mixed) return launch_face_t<float, false>(g, P, q, fgeo, (float*)fflux, nullptr, tr, s);
-  return launch_face_t<double, false>(g, P, q, fgeo, (double*)fflux, nullptr, tr, s);
+                             EsdgTraces tr, const double* bgq) {
+  if (mixed && bg && bgq)
+    return launch_face_t<float, 2>(g, P, q, fgeo, (float*)fflux, bg, tr, s, bgq);
+  if (mixed && bg) return launch_face_t<float, 1>(g, P, q, fgeo, (float*)fflux, bg, tr, s);
+  if (mixed) return launch_face_t<float, 0>(g, P, q, fgeo, (float*)fflux, nullptr, tr, s);
+  return launch_face_t<double, 0>(g, P, q, fgeo, (double*)fflux, nullptr, tr, s);
 }
 
 cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, const double* bg, int nv,

@@ -49,6 +49,7 @@ cudaError_t launch_volume_t(const EsdgGrid& g, const EsdgLGL& L, const EsdgPhys&
                   : launch_pipe64<NN, 0>(g, P, L, a, s);                       \
     }                                                                          \
     if constexpr (MIXED) {                                                     \
+      if (a.bg && a.bgq) return esdg_launch_volume_mixed_moving(g, L, P, mode, a, s); \
       if (a.bg) {                                                              \
         if constexpr (WsCfg<NN>::ON && Ws32<NN, 1>::SMEM <= ESDG_PIPE_SMEM_MAX) \
           return mode ? launch_ws32<NN, 1>(g, P, L, a, s)                      \

@@ -31,18 +31,21 @@ template <> struct Cfg<5, true> { static constexpr int EPB = 3; };
 template <> struct Cfg<6, true> { static constexpr int EPB = 2; };
 template <> struct Cfg<7, true> { static constexpr int EPB = 2; };
 
-template <int N, bool MIXED, bool BG = false, int EPB_ = 0>
+// BG: 0 no background, 1 a background at rest (hydrostatic), 2 a moving
+// background (one that carries a flow; mixed mode only)
+template <int N, bool MIXED, int BG = 0, int EPB_ = 0>
 struct Shape {
   static constexpr int Nq = N + 1, NP = Nq * Nq * Nq, NPEN = Nq * Nq;
   static constexpr int EPB = EPB_ > 0 ? EPB_ : Cfg<N, MIXED>::EPB;  // elements per CTA (tile)
   static constexpr int PENCILS = 3 * NPEN * EPB;
   static constexpr int THREADS = ((PENCILS + 31) / 32) * 32;
   // node fields: rq=rho/4, bh=b/2, ib=1/b, uh=u/2 (3), ph=phi/2, [lr, lb], nh=Ja/2 (9),
-  // [background: rq'=rho'/4, bh'=b'/2, rq_bg, bh_bg, 1/b_bg, p_bg, p'=p-p_bg]
+  // [background: rq'=rho'/4, bh'=b'/2, rq_bg, bh_bg, 1/b_bg, p_bg, p'=p-p_bg,
+  //  moving background: u'/2 = (u - u_bg)/2 (3)]
   static constexpr int F_LR = 7, F_LB = 8;
   static constexpr int F_NH = MIXED ? 7 : 9;
   static constexpr int F_BG = F_NH + 9;
-  static constexpr int NF = F_NH + 9 + (BG ? 7 : 0);
+  static constexpr int NF = F_NH + 9 + (BG ? 7 : 0) + (BG == 2 ? 3 : 0);
   using R = typename std::conditional<MIXED, float, double>::type;
   static constexpr size_t SMEM = sizeof(R) * (size_t)NF * NP * EPB;
 };
@@ -51,9 +54,10 @@ template <typename R>
 struct Node {
   R rq, bh, ib, u0, u1, u2, ph, n0, n1, n2, lr, lb;
   R rqp, bhp, rqb, bhb, ibb, pb, pp;  // perturbation and background (mixed mode with a background)
+  R up0, up1, up2;                    // u'/2 (a moving background)
 };
 
-template <typename R, bool LOGS, int F_NH, int NP, bool BG = false>
+template <typename R, bool LOGS, int F_NH, int NP, int BG = 0>
 __device__ __forceinline__ Node<R> load_node(const R* __restrict__ S, int n, int d) {
   Node<R> a;
   a.rq = S[0 * NP + n];
@@ -82,6 +86,12 @@ __device__ __forceinline__ Node<R> load_node(const R* __restrict__ S, int n, int
     a.ibb = b[4 * NP + n];
     a.pb = b[5 * NP + n];
     a.pp = b[6 * NP + n];
+  }
+  if (BG == 2) {
+    const R* b = S + (F_NH + 16) * NP;
+    a.up0 = b[0 * NP + n];
+    a.up1 = b[1 * NP + n];
+    a.up2 = b[2 * NP + n];
   }
   return a;
 }
@@ -194,6 +204,26 @@ __device__ __forceinline__ void pair32(const Node<float>& A, const Node<float>& 
   al[4] = fmaf(dli, FE, al[4]);
 }
 
+// Log branch of a log-mean difference relative to a background, for field
+// values x = x_bg + x' at the pair's nodes A, B (the density's quarter or b's
+// half: the mean is 4 d/L, 1/<b>_log is L/(2 d)).  With d = x_A - x_B =
+// d_bg + d', L = ln(x_A/x_B) = L_bg + l and l = log1p(x'_A/x_bg,A) -
+// log1p(x'_B/x_bg,B):
+//   d/L - d_bg/L_bg = (d' L_bg - d_bg l) / (L_bg (L_bg + l)),
+//   L/d - L_bg/d_bg = (l d_bg - L_bg d') / (d_bg d),
+// each term carrying a perturbation factor, where the plain difference of the
+// two means would round relative to the means themselves (a strongly
+// stratified background, e.g. a scale height of a few kilometres across one
+// element, takes every vertical pair to the log branch).  Needs L_bg and d_bg
+// away from zero (the background's own u at or above the series threshold).
+struct LogDiff {
+  float L, l;  // L_bg, l
+};
+__device__ __forceinline__ LogDiff esdg_logdiff(float xa, float xb, float pa, float pb) {
+  return LogDiff{log1pf((xa - xb) * esdg_rcpf(xb)),
+                 log1pf(pa * esdg_rcpf(xa)) - log1pf(pb * esdg_rcpf(xb))};
+}
+
 // The FP32 pair relative to a hydrostatic background (u_bg = 0): the
 // momentum flux's pressure and gravity parts are formed as exact differences
 // H - H_bg in perturbation variables rho' = rho - rho_bg, b' = b - b_bg, so
@@ -257,9 +287,16 @@ __device__ __forceinline__ void pair32bg(const Node<float>& A, const Node<float>
                                  : (4.0f * dr) / log1pf(dr * esdg_rcpf(B.rq));
     iblog = (ub < ESDG_LOG_EPS32) ? rsb * esdg_Af(ub)
                                   : log1pf(db * esdg_rcpf(B.bh)) / (2.0f * db);
-    const float rlogb = (urb < ESDG_LOG_EPS32) ? srb * esdg_Q2f(urb)
-                                               : (4.0f * drb) / log1pf(drb * esdg_rcpf(B.rqb));
-    rlogp = rlog - rlogb;
+    if (urb < ESDG_LOG_EPS32 || ur < ESDG_LOG_EPS32) {
+      // a near-uniform background or a perturbation that cancels its ratio: the
+      // plain difference is relative to the perturbation already
+      const float rlogb = (urb < ESDG_LOG_EPS32) ? srb * esdg_Q2f(urb)
+                                                 : (4.0f * drb) / log1pf(drb * esdg_rcpf(B.rqb));
+      rlogp = rlog - rlogb;
+    } else {
+      const LogDiff g = esdg_logdiff(A.rqb, B.rqb, A.rqp, B.rqp);
+      rlogp = 4.0f * fmaf(A.rqp - B.rqp, g.L, -drb * g.l) / (g.L * (g.L + g.l));
+    }
   }
   const float n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;
   const float u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;
@@ -289,8 +326,131 @@ __device__ __forceinline__ void pair32bg(const Node<float>& A, const Node<float>
   al[4] = fmaf(dli, FE, al[4]);
 }
 
+// The FP32 pair relative to a moving background (u_bg != 0, e.g. a balanced
+// jet, whose convective fluxes are far larger than their divergence): every
+// flux is formed as H - H_bg.  With primes for state minus background, sums
+// over the pair of the halved node fields ({{u}} = u_i/2 + u_l/2) and
+// un = {{u}}.n, un' = {{u'}}.n:
+//   Fr - Fr_bg = (<rho>_log - <rho_bg>_log) un + <rho_bg>_log un',
+//   M - M_bg   = (Fr - Fr_bg) {{u}} + Fr_bg {{u'}} + (p* - p*_bg) n,
+//   FE - FE_bg = (Fr - Fr_bg) W + Fr_bg W' + (p* - p*_bg) un + p*_bg un',
+// Fr_bg = <rho_bg>_log {{u_bg}}.n, W = ce/<b>_log + u_i.u_l/2 + {{phi}} and
+// W' = ce (1/<b>_log - 1/<b_bg>_log) + (u'_i.u_l + u_bg,i.u'_l)/2.  Both
+// log-mean differences come from divided differences of their series (the
+// density's as in pair32bg; 1/<b>_log = A(u_b)/{{b}} with A(u) = 1 + u/3 +
+// u^2/5 + u^3/7, so its difference is A(u_b)(1/{{b}} - 1/{{b_bg}}) +
+// (A(u_b) - A(u_b,bg))/{{b_bg}}), so every term carries a perturbation
+// factor.  The pressure mean and the gravity parts are those of pair32bg.
+template <bool LOGS>
+__device__ __forceinline__ void pair32bgm(const Node<float>& A, const Node<float>& B, float dil,
+                                          float dli, float ce, float* ai, float* al) {
+  const float sr = A.rq + B.rq;
+  const float sb = A.bh + B.bh;
+  const float rsb = esdg_rcpf(sb);
+  const float pt = sr * rsb;
+  const float dr = A.rq - B.rq, db = A.bh - B.bh;
+  const float rsr = esdg_rcpf(sr);
+  const float fr = dr * rsr, ur = fr * fr;
+  const float fb = db * rsb, ub = fb * fb;
+  const float srb = A.rqb + B.rqb, sbb = A.bhb + B.bhb;
+  const float srp = A.rqp + B.rqp;
+  float ptp;
+  {
+    const float ri = 4.0f * A.rqb, rl = 4.0f * B.rqb, rpi = 4.0f * A.rqp, rpl = 4.0f * B.rqp;
+    const float dpb = A.pb - B.pb, dpp = A.pp - B.pp;
+    const float Cb = ri * B.pb - rl * A.pb;
+    const float Db = fmaf(ri, B.pb, rl * A.pb);
+    const float x1 = fmaf(ri, B.pp, fmaf(rpi, B.pb, rpi * B.pp));
+    const float x2 = fmaf(rl, A.pp, fmaf(rpl, A.pb, rpl * A.pp));
+    const float Cp = x1 - x2, Dp = x1 + x2;
+    const float C = Cb + Cp, D = Db + Dp;
+    const float num = fmaf(dpp * C, Db, dpb * fmaf(Cp, Db, -Cb * Dp));
+    ptp = fmaf(0.5f, A.pp + B.pp, num * esdg_rcpf(2.0f * D * Db));
+  }
+  const float drb = A.rqb - B.rqb, dbb = A.bhb - B.bhb;
+  const float rsrb = esdg_rcpf(srb), rsbb = esdg_rcpf(sbb);
+  const float frb = drb * rsrb, urb = frb * frb;
+  const float fbb = dbb * rsbb, ubb = fbb * fbb;
+  float rlog, iblog, rlogp, iblogp;
+  if (!LOGS || (ur < ESDG_LOG_EPS32 && ub < ESDG_LOG_EPS32 && urb < ESDG_LOG_EPS32 &&
+                ubb < ESDG_LOG_EPS32)) {
+    const float q2 = esdg_Q2f(ur);
+    rlog = sr * q2;
+    const float ab = esdg_Af(ub);
+    iblog = rsb * ab;
+    const float fdiff = 2.0f * (A.rqp * B.rqb - B.rqp * A.rqb) * rsr * rsrb;
+    const float udiff = fdiff * (fr + frb);
+    const float s2 = fmaf(-88.0f / 945.0f, fmaf(ur, ur, fmaf(ur, urb, urb * urb)),
+                          fmaf(-8.0f / 45.0f, ur + urb, -2.0f / 3.0f));
+    rlogp = fmaf(srp, q2, srb * udiff * s2);
+    const float sbp = A.bhp + B.bhp;
+    const float gdiff = 2.0f * (A.bhp * B.bhb - B.bhp * A.bhb) * rsb * rsbb;
+    const float vdiff = gdiff * (fb + fbb);
+    // divided difference of A(u) = 1 + u/3 + u^2/5 + u^3/7
+    const float sa = fmaf(1.0f / 7.0f, fmaf(ub, ub, fmaf(ub, ubb, ubb * ubb)),
+                          fmaf(0.2f, ub + ubb, 1.0f / 3.0f));
+    iblogp = fmaf(-ab * sbp, rsb * rsbb, rsbb * vdiff * sa);
+  } else {
+    rlog = (ur < ESDG_LOG_EPS32) ? sr * esdg_Q2f(ur)
+                                 : (4.0f * dr) / log1pf(dr * esdg_rcpf(B.rq));
+    iblog = (ub < ESDG_LOG_EPS32) ? rsb * esdg_Af(ub)
+                                  : log1pf(db * esdg_rcpf(B.bh)) / (2.0f * db);
+    if (urb < ESDG_LOG_EPS32 || ur < ESDG_LOG_EPS32) {
+      const float rlogb = (urb < ESDG_LOG_EPS32) ? srb * esdg_Q2f(urb)
+                                                 : (4.0f * drb) / log1pf(drb * esdg_rcpf(B.rqb));
+      rlogp = rlog - rlogb;
+    } else {
+      const LogDiff g = esdg_logdiff(A.rqb, B.rqb, A.rqp, B.rqp);
+      rlogp = 4.0f * fmaf(A.rqp - B.rqp, g.L, -drb * g.l) / (g.L * (g.L + g.l));
+    }
+    if (ubb < ESDG_LOG_EPS32 || ub < ESDG_LOG_EPS32) {
+      const float iblogb = (ubb < ESDG_LOG_EPS32) ? rsbb * esdg_Af(ubb)
+                                                  : log1pf(dbb * esdg_rcpf(B.bhb)) / (2.0f * dbb);
+      iblogp = iblog - iblogb;
+    } else {
+      const LogDiff g = esdg_logdiff(A.bhb, B.bhb, A.bhp, B.bhp);
+      iblogp = fmaf(g.l, dbb, -g.L * (A.bhp - B.bhp)) / (2.0f * dbb * db);
+    }
+  }
+  const float rlogb = rlog - rlogp;
+  const float n0 = A.n0 + B.n0, n1 = A.n1 + B.n1, n2 = A.n2 + B.n2;
+  const float u0 = A.u0 + B.u0, u1 = A.u1 + B.u1, u2 = A.u2 + B.u2;
+  const float v0 = A.up0 + B.up0, v1 = A.up1 + B.up1, v2 = A.up2 + B.up2;  // {{u'}}
+  const float un = fmaf(u2, n2, fmaf(u1, n1, u0 * n0));
+  const float unp = fmaf(v2, n2, fmaf(v1, n1, v0 * n0));
+  const float Frp = fmaf(rlogp, un, rlogb * unp);  // Fr - Fr_bg
+  const float Frb = rlogb * (un - unp);            // Fr_bg
+  const float m0 = fmaf(Frp, u0, fmaf(Frb, v0, ptp * n0));
+  const float m1 = fmaf(Frp, u1, fmaf(Frb, v1, ptp * n1));
+  const float m2 = fmaf(Frp, u2, fmaf(Frb, v2, ptp * n2));
+  const float uu = fmaf(A.u2, B.u2, fmaf(A.u1, B.u1, A.u0 * B.u0));
+  const float t = fmaf(2.0f, uu, A.ph + B.ph);
+  // (u'_i.u_l + u_bg,i.u'_l)/2 from the halved fields, u_bg,i/2 = u_i/2 - u'_i/2
+  const float c0 = A.u0 - A.up0, c1 = A.u1 - A.up1, c2 = A.u2 - A.up2;
+  const float tp = 2.0f * fmaf(A.up2, B.u2, fmaf(A.up1, B.u1, fmaf(A.up0, B.u0,
+                              fmaf(c2, B.up2, fmaf(c1, B.up1, c0 * B.up0)))));
+  const float FE = fmaf(Frp, fmaf(iblog, ce, t),
+                        fmaf(Frb, fmaf(iblogp, ce, tp), fmaf(ptp, un, (pt - ptp) * unp)));
+  // gravity perturbation (as pair32bg)
+  const float dph = B.ph - A.ph;
+  const float dYi = 2.0f * (B.bhp * A.bhb - B.bhb * A.bhp) * A.ib * A.ibb;
+  const float dYl = 2.0f * (A.bhp * B.bhb - A.bhb * B.bhp) * B.ib * B.ibb;
+  const float gi = dph * fmaf(dYi, rlog, sbb * A.ibb * rlogp);
+  const float gl = -dph * fmaf(dYl, rlog, sbb * B.ibb * rlogp);
+  ai[0] = fmaf(dil, Frp, ai[0]);
+  ai[1] = fmaf(dil, fmaf(gi, n0, m0), ai[1]);
+  ai[2] = fmaf(dil, fmaf(gi, n1, m1), ai[2]);
+  ai[3] = fmaf(dil, fmaf(gi, n2, m2), ai[3]);
+  ai[4] = fmaf(dil, FE, ai[4]);
+  al[0] = fmaf(dli, Frp, al[0]);
+  al[1] = fmaf(dli, fmaf(gl, n0, m0), al[1]);
+  al[2] = fmaf(dli, fmaf(gl, n1, m1), al[2]);
+  al[3] = fmaf(dli, fmaf(gl, n2, m2), al[3]);
+  al[4] = fmaf(dli, FE, al[4]);
+}
+
 // ce: 1/(2(gamma - 1)) as float (mixed) or as the scaled series (FP64)
-template <int N, bool MIXED, bool LOGS, bool BG, typename CE>
+template <int N, bool MIXED, bool LOGS, int BG, typename CE>
 __device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED, BG>::R* __restrict__ S,
                                             int d, int base, int stride, const EsdgLGL& L,
                                             const CE& ce,
@@ -304,7 +464,9 @@ __device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED, BG>::
 #pragma unroll
     for (int l = i + 1; l < Nq; l++) {
       const Node<R> B = load_node<R, LOGS, SH::F_NH, SH::NP, BG>(S, base + l * stride, d);
-      if constexpr (MIXED && BG)
+      if constexpr (MIXED && BG == 2)
+        pair32bgm<LOGS>(A, B, L.Dtf[i][l], L.Dtf[l][i], ce, acc[i], acc[l]);
+      else if constexpr (MIXED && BG)
         pair32bg<LOGS>(A, B, L.Dtf[i][l], L.Dtf[l][i], ce, acc[i], acc[l]);
       else if constexpr (MIXED)
         pair32<LOGS>(A, B, L.Dtf[i][l], L.Dtf[l][i], ce, acc[i], acc[l]);
@@ -456,27 +618,90 @@ __device__ __forceinline__ Prim32 prims32bg(double q0, double q1, double q2, dou
   return o;
 }
 
+// The node fields relative to a moving background: those of prims32bg plus
+// up[0..2] = u'/2, u' = u - u_bg.  FP64 where the state cancels against the
+// background, six instructions: rho' = rho - rho_bg, m' = m - m_bg (3),
+// E' = E - E_bg, e' = E' - phi rho' (E_bg the background's total energy,
+// kinetic part included); then in FP32, each rounding relative to the
+// perturbation:
+//   u' = (m' - rho' u_bg)/rho,  u = u_bg + u',
+//   p' = (gamma - 1)(e' - KE'),  KE' = (m'.u + rho_bg u_bg.u')/2
+// (KE' = m.u/2 - m_bg.u_bg/2 exactly), p = p_bg + p', b' as in prims32bg.
+struct Prim32m {
+  float s[7], bgf[7], up[3];
+};
+__device__ __forceinline__ Prim32m prims32bgm(double q0, double q1, double q2, double q3,
+                                              double q4, double phi, float phh, float gm1f,
+                                              double rb, double mb0, double mb1, double mb2,
+                                              double eb, float rqb, float bhb, float ibb,
+                                              float pbf, float ub0, float ub1, float ub2) {
+  const double rp = q0 - rb;
+  const double mp0 = q1 - mb0, mp1 = q2 - mb1, mp2 = q3 - mb2;
+  const double ep = fma(-phi, rp, q4 - eb);
+  const float rpf = esdg_d2f(rp), epf = esdg_d2f(ep);
+  const float m0 = esdg_d2f(mp0), m1 = esdg_d2f(mp1), m2 = esdg_d2f(mp2);
+  const float q0f = esdg_d2f(q0);
+  const float irf = esdg_rcpf(q0f);
+  const float v0 = fmaf(-rpf, ub0, m0) * irf, v1 = fmaf(-rpf, ub1, m1) * irf,
+              v2 = fmaf(-rpf, ub2, m2) * irf;  // u'
+  const float u0 = ub0 + v0, u1 = ub1 + v1, u2 = ub2 + v2;
+  const float kb = (4.0f * rqb) * fmaf(ub2, v2, fmaf(ub1, v1, ub0 * v0));
+  const float kep = 0.5f * fmaf(m2, u2, fmaf(m1, u1, fmaf(m0, u0, kb)));
+  const float ppf = gm1f * (epf - kep);
+  const float pf = pbf + ppf;
+  const float rq = 0.25f * q0f;
+  Prim32m o;
+  o.s[0] = rq;
+  o.s[1] = rq * esdg_rcpf(pf);
+  o.s[2] = 2.0f * pf * irf;
+  o.s[3] = 0.5f * u0;
+  o.s[4] = 0.5f * u1;
+  o.s[5] = 0.5f * u2;
+  o.s[6] = phh;
+  o.bgf[0] = 0.25f * rpf;
+  o.bgf[1] = fmaf(rpf, pbf, -4.0f * rqb * ppf) * esdg_rcpf(4.0f * pf * pbf);  // b'/2
+  o.bgf[2] = rqb;
+  o.bgf[3] = bhb;
+  o.bgf[4] = ibb;
+  o.bgf[5] = pbf;
+  o.bgf[6] = ppf;
+  o.up[0] = 0.5f * v0;
+  o.up[1] = 0.5f * v1;
+  o.up[2] = 0.5f * v2;
+  return o;
+}
+
 // Mixed-precision stage update of one node: r = -(1/J) (volume + lifts) in
 // FP32, plus the background's right-hand side (stored in FP32) and the
 // Coriolis source, all in FP32 (they join an FP32 increment); FP64 only in
 // q += B dq.  Arrays are per node with stride NP between variables: rbg (3,
-// background momentum rhs), qin (5),
+// background momentum rhs; 5, the full rhs of a moving background), qin (5),
 // dqold (5) may be in shared or global memory; dq and qio are the node's
-// global locations.  Returns true if the updated state is not finite or its
-// density is not positive.
-template <int NP, bool BG>
+// global locations; qbg (5) the moving background's state (its Coriolis force
+// is part of its rhs, so the source here acts on m - m_bg).  Returns true if
+// the updated state is not finite or its density is not positive.
+template <int NP, int BG>
 __device__ __forceinline__ bool stage32(float (&r)[5], const float* rbg, const EsdgPhys& P,
                                         double y, const double* qin, const float* dqold, float* dq,
-                                        double* qio, double rkA, double rkB, double dt) {
-  if constexpr (BG) {
+                                        double* qio, double rkA, double rkB, double dt,
+                                        const double* qbg = nullptr) {
+  if constexpr (BG == 2) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) r[v] += rbg[v * NP];
+  } else if constexpr (BG) {
     r[1] += rbg[0];
     r[2] += rbg[NP];
     r[3] += rbg[2 * NP];
   }
   if ((P.f0 != 0.0) || (P.beta != 0.0)) {
     const float f = esdg_d2f(P.f0 + P.beta * (y - P.y0));
-    r[1] = fmaf(f, esdg_d2f(qin[2 * NP]), r[1]);
-    r[2] = fmaf(-f, esdg_d2f(qin[NP]), r[2]);
+    if constexpr (BG == 2) {
+      r[1] = fmaf(f, esdg_d2f(qin[2 * NP] - qbg[2 * NP]), r[1]);
+      r[2] = fmaf(-f, esdg_d2f(qin[NP] - qbg[NP]), r[2]);
+    } else {
+      r[1] = fmaf(f, esdg_d2f(qin[2 * NP]), r[1]);
+      r[2] = fmaf(-f, esdg_d2f(qin[NP]), r[2]);
+    }
   }
   const float A = esdg_d2f(rkA), B = esdg_d2f(rkB), dtf = esdg_d2f(dt);
   bool bad = false;

@@ -1,8 +1,8 @@
 // volume_tile.cuh -- the per-tile volume kernel: one CTA per tile of EPB
 // elements (k_volume), its persistent batched form over a device work table
 // (k_volume_batch), and their launchers.  Used for the mixed path without a
-// background, for tiles whose pipelined form exceeds shared memory, and as the
-// autotuner's alternative batch variants.
+// background or with a moving one, for tiles whose pipelined form exceeds
+// shared memory, and as the autotuner's alternative batch variants.
 #pragma once
 #include "volume_pairs.cuh"
 
@@ -10,7 +10,7 @@ namespace esdg_vol {
 
 // One tile: elements e0 .. e0 + EPB - 1 of one mesh, processed by a CTA of
 // SH::THREADS threads with SH::SMEM bytes of shared memory at smraw.
-template <int N, bool MIXED, int MODE, bool BG, int EPB_ = 0>
+template <int N, bool MIXED, int MODE, int BG, int EPB_ = 0>
 __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
                                             const EsdgVolArgs& a, int e0, unsigned char* smraw) {
   using SH = Shape<N, MIXED, BG, EPB_>;
@@ -35,7 +35,21 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       const double phi = a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP + n];
       if constexpr (MIXED) {
         const float phh = vg[((size_t)e * ESDG_NVGEO + 10) * NP + n];
-        if constexpr (BG) {
+        if constexpr (BG == 2) {
+          const double* bq = a.bgq + (size_t)e * 5 * NP + n;
+          const float* bpe = a.bgp + (size_t)e * 4 * NP + n;
+          const float* bu = a.bgu + (size_t)e * 3 * NP + n;
+          const Prim32m o = prims32bgm(q0, q1, q2, q3, q4, phi, phh, gm1f, bq[0], bq[NP],
+                                       bq[2 * NP], bq[3 * NP], bq[4 * NP], bpe[0], bpe[NP],
+                                       bpe[2 * NP], bpe[3 * NP], bu[0], bu[NP], bu[2 * NP]);
+#pragma unroll
+          for (int k = 0; k < 7; k++) {
+            S[k * NP + n] = o.s[k];
+            S[(SH::F_BG + k) * NP + n] = o.bgf[k];
+          }
+#pragma unroll
+          for (int k = 0; k < 3; k++) S[(SH::F_BG + 7 + k) * NP + n] = o.up[k];
+        } else if constexpr (BG) {
           const double* bge = a.bg + (size_t)e * 3 * NP;
           const float* bpe = a.bgp + (size_t)e * 4 * NP;
           const Prim32 o = prims32bg(q0, q1, q2, q3, q4, phi, phh, gm1f, bge[n], bge[NP + n],
@@ -150,8 +164,9 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       const size_t qb = (size_t)e2 * 5 * NP + n;
       const double y = rotating ? a.x[((size_t)e2 * 3 + 1) * NP + n] : 0.0;
       float* dq = reinterpret_cast<float*>(a.dq);
-      bad |= stage32<NP, BG>(r32, BG ? a.rhs_bg + (size_t)e2 * 3 * NP + n : nullptr, P, y,
-                             a.q_in + qb, dq + qb, dq + qb, a.q_io + qb, a.rkA, a.rkB, a.dt);
+      const float* rbg = BG == 2 ? a.rhs_bgm + qb : (BG ? a.rhs_bg + (size_t)e2 * 3 * NP + n : nullptr);
+      bad |= stage32<NP, BG>(r32, rbg, P, y, a.q_in + qb, dq + qb, dq + qb, a.q_io + qb, a.rkA,
+                             a.rkB, a.dt, BG == 2 ? a.bgq + qb : nullptr);
       continue;
     }
     // FP64 stage update: dt is folded into the -1/J scale (r then holds dt rhs)
@@ -166,7 +181,10 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       else r[v] = rv;
     }
     const size_t qb = (size_t)e2 * 5 * NP + n;
-    if constexpr (BG) {  // the background's own FP64 momentum right-hand side
+    if constexpr (BG == 2) {  // the moving background's own right-hand side
+#pragma unroll
+      for (int v = 0; v < 5; v++) r[v] += a.rhs_bgm[qb + (size_t)v * NP];
+    } else if constexpr (BG) {  // the background's own momentum right-hand side
       r[1] += a.rhs_bg[((size_t)e2 * 3 + 0) * NP + n];
       r[2] += a.rhs_bg[((size_t)e2 * 3 + 1) * NP + n];
       r[3] += a.rhs_bg[((size_t)e2 * 3 + 2) * NP + n];
@@ -175,8 +193,11 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       const double y = a.x[((size_t)e2 * 3 + 1) * NP + n];
       double f = P.f0 + P.beta * (y - P.y0);
       if constexpr (DT_IN_R) f *= a.dt;
-      r[1] = fma(f, a.q_in[qb + 2 * NP], r[1]);
-      r[2] = fma(-f, a.q_in[qb + NP], r[2]);
+      // with a moving background its Coriolis force is part of its rhs
+      const double my = BG == 2 ? a.q_in[qb + 2 * NP] - a.bgq[qb + 2 * NP] : a.q_in[qb + 2 * NP];
+      const double mx = BG == 2 ? a.q_in[qb + NP] - a.bgq[qb + NP] : a.q_in[qb + NP];
+      r[1] = fma(f, my, r[1]);
+      r[2] = fma(-f, mx, r[2]);
     }
     if constexpr (MODE == 0) {
 #pragma unroll
@@ -201,7 +222,7 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
   if (MODE != 0 && bad && a.status) *a.status = 1;
 }
 
-template <int N, bool MIXED, int MODE, bool BG>
+template <int N, bool MIXED, int MODE, int BG>
 __global__ void __launch_bounds__(Shape<N, MIXED, BG>::THREADS)
     k_volume(EsdgGrid g, EsdgPhys P, EsdgLGL L, EsdgVolArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -238,7 +259,7 @@ __global__ void __launch_bounds__(Shape<N, MIXED, BG, EPB_>::THREADS)
   }
 }
 
-template <int N, bool MIXED, int MODE, bool BG>
+template <int N, bool MIXED, int MODE, int BG>
 cudaError_t launch_one(const EsdgGrid& g, const EsdgPhys& P, const EsdgLGL& L,
                        const EsdgVolArgs& a, cudaStream_t s) {
   using SH = Shape<N, MIXED, BG>;
