@@ -91,7 +91,7 @@ def test_slab_steps_equal_whole(lib, K, N, parts, periodic, warp, precision):
                       4, lambda o: o.bubble(amp=0.8, profile="sharp"))
 
 
-def oracle_trajectory(q, q_init, precision, mesh, K, N, dt, nsteps, init, channel=False, **phys):
+def oracle_trajectory(q, q_init, precision, mesh, K, N, dt, nsteps, init, **phys):
     """The oracle advanced from its own initial state (which the GPU's must equal to
     1e-12) with the same step; q checked against it (oracle_checks bars)."""
     o = O.Oracle(*K, N, **mesh, **phys)
@@ -102,7 +102,7 @@ def oracle_trajectory(q, q_init, precision, mesh, K, N, dt, nsteps, init, channe
         q_long = O.Oracle(*K, N, precision="long", **mesh, **phys).steps(q0, dt, nsteps)
         check_fp64(q, q_plain, q_long, what=(K, N, mesh))
     else:
-        check_mixed(q, q0, q_plain, channel=channel, what=(K, N, mesh))
+        check_mixed(q, q0, q_plain, what=(K, N, mesh))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -119,7 +119,7 @@ def test_slab_channel_with_coriolis(lib, precision):
     q = split.get_state()
     assert np.array_equal(q, whole.get_state())
     oracle_trajectory(q, q_init, precision, dict(box, periodic=(1, 0, 0)), (6, 3, 2), 4, dt, 3,
-                      lambda o: o.channel(), channel=True, f0=1e-4)
+                      lambda o: o.channel(), f0=1e-4)
 
 
 def test_slab_calls_need_traces(lib):
