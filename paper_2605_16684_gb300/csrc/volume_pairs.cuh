@@ -479,12 +479,13 @@ __device__ __forceinline__ void pencil_pass(const typename Shape<N, MIXED, BG>::
 // Interface terms of one pencil: the element is the "+" side of plane e_d
 // (its first node receives -(s/w) F*) and the "-" side of plane e_d + 1 (its
 // last node receives +(s/w) F*); fn is the pencil's node index on those faces.
-// INIT: the terms are the accumulators' initial value (FP64: they are then
-// loaded long before their first use), else they are added at the end (mixed:
-// after the element's reference geopotential is restored in the pair sums).
-template <bool INIT, int N, typename R>
-__device__ __forceinline__ void face_lift(const EsdgGrid& g, const EsdgVolArgs& a, int e, int d,
-                                          int fn, R (&acc)[N + 1][5]) {
+template <typename R>
+struct FaceTerms {
+  R m[5], p[5];  // (s/w) F* of the pencil's lower and upper face
+};
+template <int N, typename R>
+__device__ __forceinline__ FaceTerms<R> face_fetch(const EsdgGrid& g, const EsdgVolArgs& a, int e,
+                                                   int d, int fn) {
   constexpr int NPEN = (N + 1) * (N + 1);
   // element indices selected without dynamic array indexing (no local memory)
   const int i0 = e % g.K[0], i1 = (e / g.K[0]) % g.K[1], i2 = e / (g.K[0] * g.K[1]);
@@ -498,16 +499,39 @@ __device__ __forceinline__ void face_lift(const EsdgGrid& g, const EsdgVolArgs& 
   const long long fm = esdg_face_id(g, d, Pm, ia, ib);
   const long long fp = esdg_face_id(g, d, Pp, ia, ib);
   const R* ff = reinterpret_cast<const R*>(a.fflux);
+  FaceTerms<R> t;
 #pragma unroll
   for (int v = 0; v < 5; v++) {
-    const R m = ff[((size_t)fm * 5 + v) * NPEN + fn], p = ff[((size_t)fp * 5 + v) * NPEN + fn];
-    if (INIT) {
-      acc[0][v] = -m;
-      acc[N][v] = p;
-    } else {
-      acc[0][v] -= m;
-      acc[N][v] += p;
+    t.m[v] = ff[((size_t)fm * 5 + v) * NPEN + fn];
+    t.p[v] = ff[((size_t)fp * 5 + v) * NPEN + fn];
+  }
+  return t;
+}
+// Mixed path: the terms are added after the pair sums (once the element's
+// reference geopotential is restored in them); fetched before the pair pass,
+// their gathers' latency hides behind it.
+template <int N, typename R>
+__device__ __forceinline__ void face_add(const FaceTerms<R>& t, R (&acc)[N + 1][5]) {
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    acc[0][v] -= t.m[v];
+    acc[N][v] += t.p[v];
+  }
+}
+// INIT: the terms are the accumulators' initial value (FP64: they are then
+// loaded long before their first use), else they are added at once.
+template <bool INIT, int N, typename R>
+__device__ __forceinline__ void face_lift(const EsdgGrid& g, const EsdgVolArgs& a, int e, int d,
+                                          int fn, R (&acc)[N + 1][5]) {
+  const FaceTerms<R> t = face_fetch<N, R>(g, a, e, d, fn);
+  if (INIT) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      acc[0][v] = -t.m[v];
+      acc[N][v] = t.p[v];
     }
+  } else {
+    face_add<N, R>(t, acc);
   }
 }
 

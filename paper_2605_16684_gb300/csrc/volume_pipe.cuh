@@ -672,6 +672,7 @@ __global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>:
 #pragma unroll
       for (int v = 0; v < 5; v++) acc[i][v] = 0.0f;
     if (active && el < ne) {
+      const FaceTerms<float> ft = face_fetch<N, float>(g, a, e, d, ps + Nq * pt);
       const float* S = sm + (size_t)el * NF * NP;
       const float ce = esdg_d2f(0.5 * P.igm1);
       if (need_logs)
@@ -681,7 +682,7 @@ __global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>:
       const float phi0 = phi0s[el];
 #pragma unroll
       for (int i = 0; i < Nq; i++) acc[i][4] = fmaf(phi0, acc[i][0], acc[i][4]);
-      face_lift<false, N, float>(g, a, e, d, ps + Nq * pt, acc);
+      face_add<N, float>(ft, acc);
     }
     __syncthreads();
     if (active && el < ne) {

@@ -121,6 +121,14 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
   if constexpr (!MIXED)
     if (active && e < E) face_lift<true, N, R>(g, a, e, d, s + Nq * t, acc);
   if (active && e < E) {
+    // mixed: the face terms and the element's reference geopotential are
+    // fetched ahead of the pair pass and applied after it
+    FaceTerms<R> ft{};
+    R phi0 = (R)0;
+    if constexpr (MIXED) {
+      ft = face_fetch<N, R>(g, a, e, d, s + Nq * t);
+      phi0 = esdg_d2f(a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP]);
+    }
     const R* S = sm + (size_t)el * NF * NP;
     const auto ce = [&] {
       if constexpr (MIXED) return esdg_d2f(0.5 * P.igm1);
@@ -132,10 +140,9 @@ __device__ __forceinline__ void volume_tile(const EsdgGrid& g, const EsdgPhys& P
       pencil_pass<N, MIXED, false, BG>(S, d, base, stride, L, ce, acc);
     if constexpr (MIXED) {
       // restore the element's reference geopotential in the energy flux
-      const R phi0 = esdg_d2f(a.vgeo64[((size_t)e * ESDG_NVGEO + 10) * NP]);
 #pragma unroll
       for (int i = 0; i < Nq; i++) acc[i][4] = fmaf(phi0, acc[i][0], acc[i][4]);
-      face_lift<false, N, R>(g, a, e, d, s + Nq * t, acc);
+      face_add<N, R>(ft, acc);
     }
   }
   __syncthreads();

@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(Ws32<N, MODE>::T, 1)
 #pragma unroll
         for (int v = 0; v < 5; v++) acc[i][v] = 0.0f;
       if (active && el < ne) {
+        const FaceTerms<float> ft = face_fetch<N, float>(g, a, e0 + el, d, ps + Nq * pt);
         const float* S = Sb + (size_t)el * NF * NP;
         if (need_logs)
           pencil_pass<N, true, true, true>(S, d, base, stride, L, ce, acc);
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(Ws32<N, MODE>::T, 1)
         const float phi0 = c.phi0[b][el];
 #pragma unroll
         for (int i = 0; i < Nq; i++) acc[i][4] = fmaf(phi0, acc[i][0], acc[i][4]);
-        face_lift<false, N, float>(g, a, e0 + el, d, ps + Nq * pt, acc);
+        face_add<N, float>(ft, acc);
       }
       ws_bar(CBAR, CT);  // every node field of the buffer read
       if (active && el < ne) {
