@@ -739,7 +739,9 @@ def run_slabs(args):
     out = {"metric": "domain decomposition on one GPU: DOF-updates/s per RK stage by slab count",
            "unit": "DOF-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "config": {"workload": WORKLOAD_NAME + "_x_slabs", "slabs": "x element layers",
-                      "exchange": "pack kernel + one device copy per cut plane and stage"},
+                      "exchange": "pack kernel + one device copy per cut plane and stage; "
+                                  "one stream per slab ordered by events, one LSRK step "
+                                  "captured as a CUDA graph and replayed"},
            "fp64": res["fp64"], "mixed": res["mixed"]}
     print(json.dumps(out))
 

@@ -68,9 +68,29 @@ struct es_dg {
   // a mixed partition evaluates its background's right-hand side at its first stage,
   // once its neighbours' background values have arrived with the traces
   int bg_pending;
+  // es_dg_partitions_step: this partition's own stream and the events ordering it
+  // against its neighbours (created on first use)
+  cudaStream_t pstream;
+  cudaEvent_t ev_packed, ev_sent, ev_faced, ev_join;
+  // configuration generation (unique across handles): renewed whenever what a
+  // captured step launches could change (traces, background)
+  long long gen;
+  // the captured LSRK step of the partitions this handle leads (parts[0]), its
+  // time step and the partitions and generations it was captured for
+  cudaGraphExec_t pexec;
+  double pexec_dt;
+  std::vector<es_dg_t*> pexec_parts;
+  std::vector<long long> pexec_gens;
 };
 
 namespace {
+
+long long next_gen() {
+  static std::atomic<long long> counter{0};
+  return ++counter;
+}
+
+void touch(es_dg_t* h) { h->gen = next_gen(); }
 
 int dev_alloc(es_dg_t* h, void** p, size_t bytes) {
   *p = nullptr;
@@ -236,6 +256,7 @@ int set_background_dev(es_dg_t* h, const double* q_dev) {
   if (st) return st;
   double* q0 = h->qtmp;
   if (q_dev == q0) return ES_DG_EINVAL;
+  touch(h);
   h->bg_moving = 0;
   cudaError_t e = esdg_launch_background(h->g, h->P, h->vgeo, q_dev, h->bg, q0, h->stream);
   if (e == cudaSuccess)
@@ -286,6 +307,7 @@ int set_moving_background_dev(es_dg_t* h, const double* q_dev) {
   if (!st && !h->rhs_bgm32) st = dev_alloc(h, (void**)&h->rhs_bgm32, E * 5 * np * sizeof(float));
   if (st) return st;
   if (q_dev == h->qtmp) return ES_DG_EINVAL;
+  touch(h);
   h->has_bg = 0;  // until the new background is complete
   cudaError_t e = cudaMemcpyAsync(h->bgq, q_dev, E * 5 * np * sizeof(double),
                                   cudaMemcpyDeviceToDevice, h->stream);
@@ -336,6 +358,7 @@ int resolve_background(es_dg_t* h) {
   if (e == cudaSuccess) e = esdg_launch_to_f32(h->rhs_bg, h->rhs_bg32, (long long)E * 3 * np, h->stream);
   if (e != cudaSuccess) return cuda_status(e);
   h->bg_pending = 0;
+  touch(h);
   return ES_DG_OK;
 }
 
@@ -400,6 +423,7 @@ int create_impl(const es_dg_mesh* mesh, int N, es_dg_precision precision,
   if (st) return st;
   es_dg_t* h = new (std::nothrow) es_dg();
   if (!h) return ES_DG_ENOMEM;
+  touch(h);
   h->g = g;
   if (esdg_lgl_build(N, &h->L)) {
     delete h;
@@ -516,6 +540,15 @@ int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,
 void es_dg_destroy(es_dg_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->pexec) cudaGraphExecDestroy(h->pexec);
+  if (h->pstream) {
+    cudaStreamSynchronize(h->pstream);
+    cudaEventDestroy(h->ev_packed);
+    cudaEventDestroy(h->ev_sent);
+    cudaEventDestroy(h->ev_faced);
+    cudaEventDestroy(h->ev_join);
+    cudaStreamDestroy(h->pstream);
+  }
   for (void* p : h->blocks) {
     if (h->has_alloc) h->alloc.free(p, h->alloc.ctx);
     else cudaFree(p);
@@ -641,6 +674,7 @@ int es_dg_set_moving_background(es_dg_t* h, const double* q_bg, int on_device) {
 
 int es_dg_clear_background(es_dg_t* h) {
   if (!h) return ES_DG_EINVAL;
+  touch(h);
   h->has_bg = 0;
   h->bg_pending = 0;
   h->bg_moving = 0;
@@ -788,6 +822,7 @@ int es_dg_set_traces(es_dg_t* h, double* send_lo, double* send_hi, double* recv_
   for (const void* p : {(const void*)send_lo, (const void*)send_hi, (const void*)recv_lo,
                         (const void*)recv_hi})
     if (reinterpret_cast<uintptr_t>(p) % sizeof(double)) return ES_DG_EINVAL;
+  touch(h);
   h->tr_send[0] = h->g.remote[0] ? send_lo : nullptr;
   h->tr_send[1] = h->g.remote[1] ? send_hi : nullptr;
   h->tr_recv[0] = h->g.remote[0] ? recv_lo : nullptr;
@@ -899,17 +934,185 @@ int es_dg_partitions_exchange(es_dg_t* const* parts, int P) {
   return st;
 }
 
+namespace {
+
+int ensure_part_streams(es_dg_t* h) {
+  if (h->pstream) return ES_DG_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->pstream, cudaStreamNonBlocking);
+  cudaEvent_t* evs[4] = {&h->ev_packed, &h->ev_sent, &h->ev_faced, &h->ev_join};
+  for (int k = 0; k < 4 && e == cudaSuccess; k++)
+    e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
+  return cuda_status(e);
+}
+
+// One LSRK step of all partitions, each on its own stream (h->stream is the
+// partition's pstream meanwhile), ordered by events instead of one stream:
+//   A1  every partition packs its traces (after its previous stage);
+//   A2  partition p copies the pair of traces across its high plane into the
+//       receive buffers of p and q = hi_of[p], after q's pack and after q's
+//       previous face pass (which read the buffer being overwritten);
+//   B   each partition runs its faces once its low neighbour's copies have
+//       landed, then its volume kernel with the stage update.
+// The host issues the phases in this order for every stage, so each wait
+// names an event already recorded for this stage (A1 -> A2 -> B) or the
+// previous one (B -> A2): the dependency graph has no cycle.  Partitions'
+// kernels overlap where their dependencies allow (one slab's volume kernel
+// with a neighbour's faces and copies) instead of running one after another.
+// captured: the step is being captured into a graph whose launches follow one
+// another, so its first stage needs (and may name) no event of the step before.
+int issue_partition_step(es_dg_t* const* parts, int P, const std::vector<int>& lo_of,
+                         const std::vector<int>& hi_of, double dt, bool captured) {
+  for (int s = 0; s < 5; s++) {
+    for (int p = 0; p < P; p++) {
+      int st = es_dg_pack_traces(parts[p], ES_DG_TRACE_STATE);
+      if (st) return st;
+      if (cudaEventRecord(parts[p]->ev_packed, parts[p]->stream) != cudaSuccess) return ES_DG_ECUDA;
+    }
+    for (int p = 0; p < P; p++) {
+      es_dg_t* h = parts[p];
+      const int q = hi_of[p];
+      if (q < 0) continue;
+      cudaError_t e = cudaStreamWaitEvent(h->stream, parts[q]->ev_packed, 0);
+      if (e == cudaSuccess && q != p && !(captured && s == 0))
+        e = cudaStreamWaitEvent(h->stream, parts[q]->ev_faced, 0);
+      const size_t bytes = trace_doubles(h) * sizeof(double);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(parts[q]->tr_recv[0], h->tr_send[1], bytes, cudaMemcpyDeviceToDevice,
+                            h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->tr_recv[1], parts[q]->tr_send[0], bytes, cudaMemcpyDeviceToDevice,
+                            h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_sent, h->stream);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    for (int p = 0; p < P; p++) {
+      es_dg_t* h = parts[p];
+      if (lo_of[p] >= 0 && lo_of[p] != p &&
+          cudaStreamWaitEvent(h->stream, parts[lo_of[p]]->ev_sent, 0) != cudaSuccess)
+        return ES_DG_ECUDA;
+      const bool moving = h->mixed && h->has_bg && h->bg_moving;
+      if (h->bg_pending) {
+        const int st = resolve_background(h);
+        if (st) return st;
+      }
+      cudaError_t e = esdg_launch_face(h->g, h->P, h->mixed, h->q, h->fgeo, h->fflux, h->stream,
+                                       (h->mixed && h->has_bg) ? h->bg : nullptr, traces_of(h),
+                                       moving ? h->bgq : nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_faced, h->stream);
+      if (e != cudaSuccess) return cuda_status(e);
+      EsdgVolArgs a = vol_args(h, h->q, nullptr);
+      a.rkA = kRkA[s];
+      a.rkB = kRkB[s];
+      a.dt = dt;
+      e = esdg_launch_volume(h->g, h->L, h->P, h->mixed, 1, a, h->stream);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
+  return ES_DG_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// The captured step of parts (led by parts[0]) is valid for this call: same time
+// step, same partitions, none of them reconfigured since, no background pending.
+bool step_graph_valid(es_dg_t* const* parts, int P, double dt) {
+  const es_dg_t* h0 = parts[0];
+  if (!h0->pexec || h0->pexec_dt != dt || (int)h0->pexec_parts.size() != P) return false;
+  for (int p = 0; p < P; p++)
+    if (h0->pexec_parts[p] != parts[p] || h0->pexec_gens[p] != parts[p]->gen ||
+        parts[p]->bg_pending)
+      return false;
+  return true;
+}
+
+// Capture one LSRK step of parts on the first partition's stream (every other
+// partition stream joined into the capture) and keep it in parts[0].
+int capture_step_graph(es_dg_t* const* parts, int P, const std::vector<int>& lo_of,
+                       const std::vector<int>& hi_of, double dt) {
+  es_dg_t* h0 = parts[0];
+  cudaStream_t o = h0->pstream;
+  if (h0->pexec) {
+    cudaGraphExecDestroy(h0->pexec);
+    h0->pexec = nullptr;
+  }
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(o, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaEventRecord(h0->ev_join, o);
+  for (int p = 1; p < P && e == cudaSuccess; p++)
+    e = cudaStreamWaitEvent(parts[p]->stream, h0->ev_join, 0);
+  int st = e == cudaSuccess ? issue_partition_step(parts, P, lo_of, hi_of, dt, true) : ES_DG_ECUDA;
+  for (int p = 1; p < P && !st; p++)
+    if (cudaEventRecord(parts[p]->ev_join, parts[p]->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(o, parts[p]->ev_join, 0) != cudaSuccess)
+      st = ES_DG_ECUDA;
+  e = cudaStreamEndCapture(o, &gr);
+  if (!st && e != cudaSuccess) st = cuda_status(e);
+  if (!st) st = cuda_status(cudaGraphInstantiate(&h0->pexec, gr, 0));
+  if (gr) cudaGraphDestroy(gr);
+  if (st) {
+    cudaGetLastError();
+    h0->pexec = nullptr;
+    return st;
+  }
+  h0->pexec_dt = dt;
+  h0->pexec_parts.assign(parts, parts + P);
+  h0->pexec_gens.resize(P);
+  for (int p = 0; p < P; p++) h0->pexec_gens[p] = parts[p]->gen;
+  return ES_DG_OK;
+}
+
+}  // namespace
+
 int es_dg_partitions_step(es_dg_t* const* parts, int P, double dt, int nsteps) {
   if (nsteps < 0 || !(dt > 0.0)) return ES_DG_EINVAL;
   std::vector<int> lo_of, hi_of;
   int st = check_partitions(parts, P, lo_of, hi_of);
-  for (int n = 0; n < nsteps && !st; n++)
-    for (int s = 0; s < 5 && !st; s++) {
-      for (int p = 0; p < P && !st; p++) st = es_dg_pack_traces(parts[p], ES_DG_TRACE_STATE);
-      if (!st) st = exchange_traces(parts, P, hi_of, false);
-      for (int p = 0; p < P && !st; p++)
-        st = launch_stage(parts[p], parts[p]->q, 1, nullptr, kRkA[s], kRkB[s], dt);
+  if (st || nsteps == 0) return st;
+  for (int p = 0; p < P && !st; p++) st = ensure_part_streams(parts[p]);
+  if (st) return st;
+  cudaStream_t user = parts[0]->stream;
+  es_dg_t* h0 = parts[0];
+  cudaStream_t o = h0->pstream;
+  // fork: every partition stream after the work already queued on the caller's stream
+  cudaError_t e = cudaEventRecord(h0->ev_join, user);
+  for (int p = 0; p < P && e == cudaSuccess; p++) e = cudaStreamWaitEvent(parts[p]->pstream, h0->ev_join, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int p = 0; p < P; p++) parts[p]->stream = parts[p]->pstream;
+  // Steps replay the captured step graph of these partitions.  Without a valid
+  // one, the first step runs as issued (it resolves a mixed partition's
+  // background and configures each kernel once, outside any capture) and the
+  // step is captured for the others and for later calls.
+  int n = 0;
+  if (!step_graph_valid(parts, P, dt)) {
+    st = issue_partition_step(parts, P, lo_of, hi_of, dt, false);
+    n = 1;
+    // the graph runs on the first partition's stream: after every partition's first step
+    for (int p = 1; p < P && !st; p++)
+      if (cudaEventRecord(parts[p]->ev_join, parts[p]->stream) != cudaSuccess ||
+          cudaStreamWaitEvent(o, parts[p]->ev_join, 0) != cudaSuccess)
+        st = ES_DG_ECUDA;
+    if (!st && capture_step_graph(parts, P, lo_of, hi_of, dt) != ES_DG_OK) {
+      // no graph: issue the remaining steps directly
+      for (; n < nsteps && !st; n++) st = issue_partition_step(parts, P, lo_of, hi_of, dt, false);
     }
+  }
+  for (; n < nsteps && !st; n++) st = cuda_status(cudaGraphLaunch(h0->pexec, o));
+  // join: the caller's stream after every partition stream.  The ordering events
+  // are recorded again outside any capture, so that none names a node of the
+  // captured graph when the next call waits on it.
+  for (int p = 0; p < P; p++) {
+    es_dg_t* h = parts[p];
+    h->stream = user;
+    cudaError_t ej = cudaEventRecord(h->ev_packed, h->pstream);
+    if (ej == cudaSuccess) ej = cudaEventRecord(h->ev_sent, h->pstream);
+    if (ej == cudaSuccess) ej = cudaEventRecord(h->ev_faced, h->pstream);
+    if (ej == cudaSuccess) ej = cudaEventRecord(h->ev_join, h->pstream);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(user, h->ev_join, 0);
+    if (ej != cudaSuccess && !st) st = cuda_status(ej);
+  }
   return st;
 }
 

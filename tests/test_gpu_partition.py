@@ -84,7 +84,10 @@ def test_slab_steps_equal_whole(lib, K, N, parts, periodic, warp, precision):
     dt = whole.cfl_dt(0.5)
     assert split.cfl_dt(0.5) == dt
     whole.step(dt, 4)
-    split.step(dt, 4)
+    # one call of one step (issued directly), then a call of three (the first issued,
+    # two replays of the captured step): consecutive calls reuse the ordering events
+    split.step(dt, 1)
+    split.step(dt, 3)
     q = split.get_state()
     assert np.array_equal(q, whole.get_state())
     oracle_trajectory(q, q_init, precision, dict(CUBE, periodic=periodic, warp=warp), K, N, dt,
@@ -115,11 +118,32 @@ def test_slab_channel_with_coriolis(lib, precision):
     q_init = split.get_state()
     dt = whole.cfl_dt(0.5)
     whole.step(dt, 3)
-    split.step(dt, 3)
+    split.step(dt, 2)
+    split.step(dt, 1)
     q = split.get_state()
     assert np.array_equal(q, whole.get_state())
     oracle_trajectory(q, q_init, precision, dict(box, periodic=(1, 0, 0)), (6, 3, 2), 4, dt, 3,
                       lambda o: o.channel(), f0=1e-4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_slab_step_graph_follows_dt_and_reconfiguration(lib, precision):
+    # the captured step is replayed only for the time step and configuration it was
+    # captured for: a new dt, a new background and new states all match the whole mesh
+    K, N, parts, periodic, warp = CASES[1]
+    whole, split, _ = pair(lib, K, N, parts, periodic, warp, precision=precision)
+    for s in (whole, split):
+        s.init_bubble(amp=0.8)
+    dt = whole.cfl_dt(0.5)
+    for s in (whole, split):
+        s.step(dt, 2)
+        s.step(dt, 2)
+        s.step(0.5 * dt, 3)
+    assert np.array_equal(split.get_state(), whole.get_state())
+    for s in (whole, split):
+        s.init_bubble(amp=0.3, profile="sharp")  # new state and background
+        s.step(dt, 3)
+    assert np.array_equal(split.get_state(), whole.get_state())
 
 
 def test_slab_calls_need_traces(lib):
