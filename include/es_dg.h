@@ -230,9 +230,13 @@ int es_dg_integrals(es_dg_t* h, double out[3]);
  * Any pointer may be NULL.  Synchronous when on_device = 0. */
 int es_dg_geometry(es_dg_t* h, double* x, double* J, double* Ja, int on_device);
 
-/* Launch a single kernel of the right-hand side on the handle's state, for
- * timing: which = 0 interface flux, 1 volume (writes the rhs buffer), 2 volume
- * with the fused RK update at stage `stage` (0..4) and step dt. */
+/* Launch a single kernel of the right-hand side on the handle's state: which =
+ * 0 interface flux (every face), 1 volume (writes the rhs buffer), 2 volume with
+ * the fused RK update at stage `stage` (0..4) and step dt; on a partition also
+ * 3 the interface flux of every face whose outside state needs no trace, and 4
+ * that of the faces of its remote planes (3 then 4 equals 0: a caller can run 3
+ * while the traces are in flight, Section 4.3's overlap of the exchange with
+ * the work that does not depend on it).  ES_DG_EINVAL for another value. */
 int es_dg_launch(es_dg_t* h, int which, int stage, double dt);
 
 /* ---- Domain decomposition (Section 4.3: elements split among processes, face

@@ -219,6 +219,35 @@ EsdgTraces traces_of(const es_dg_t* h) {
 
 int resolve_background(es_dg_t* h);
 
+// The interface fluxes of one class of faces for state q_in: 0 every face, 1 the
+// faces whose outside state needs no trace, 2 the faces of the remote planes.
+// x faces come first, plane by plane (plane 0 is a partition's low cut, the last
+// x plane its high cut), then the y and z faces.
+enum { FACES_ALL = 0, FACES_INTERIOR = 1, FACES_CUT = 2 };
+int launch_faces(es_dg_t* h, const double* q_in, int which) {
+  const bool moving = h->mixed && h->has_bg && h->bg_moving;
+  const double* bg = (h->mixed && h->has_bg) ? h->bg : nullptr;
+  const EsdgTraces tr = traces_of(h);
+  auto run = [&](long long f0, long long f1) {
+    return esdg_launch_face(h->g, h->P, h->mixed, q_in, h->fgeo, h->fflux, h->stream, bg, tr,
+                            moving ? h->bgq : nullptr, f0, f1);
+  };
+  const long long plane = (long long)h->g.K[1] * h->g.K[2];
+  const long long x0 = h->g.face_off[0], x1 = h->g.face_off[1];
+  const long long lo = h->g.remote[0] ? plane : 0, hi = h->g.remote[1] ? plane : 0;
+  cudaError_t e = cudaSuccess;
+  if (which == FACES_ALL) {
+    e = run(0, -1);
+  } else if (which == FACES_INTERIOR) {
+    e = run(x0 + lo, x1 - hi);
+    if (e == cudaSuccess) e = run(x1, -1);
+  } else {
+    if (lo) e = run(x0, x0 + lo);
+    if (e == cudaSuccess && hi) e = run(x1 - hi, x1);
+  }
+  return cuda_status(e);
+}
+
 // face fluxes then volume (+ lift, source, optional RK update) for state q_in
 int launch_stage(es_dg_t* h, const double* q_in, int mode, double* rhs_out, double A, double B,
                  double dt) {
@@ -227,16 +256,13 @@ int launch_stage(es_dg_t* h, const double* q_in, int mode, double* rhs_out, doub
     const int st = resolve_background(h);
     if (st) return st;
   }
-  const bool moving = h->mixed && h->has_bg && h->bg_moving;
-  cudaError_t e = esdg_launch_face(h->g, h->P, h->mixed, q_in, h->fgeo, h->fflux, h->stream,
-                                   (h->mixed && h->has_bg) ? h->bg : nullptr, traces_of(h),
-                                   moving ? h->bgq : nullptr);
-  if (e != cudaSuccess) return cuda_status(e);
+  const int stf = launch_faces(h, q_in, FACES_ALL);
+  if (stf) return stf;
   EsdgVolArgs a = vol_args(h, q_in, rhs_out);
   a.rkA = A;
   a.rkB = B;
   a.dt = dt;
-  e = esdg_launch_volume(h->g, h->L, h->P, h->mixed, mode, a, h->stream);
+  const cudaError_t e = esdg_launch_volume(h->g, h->L, h->P, h->mixed, mode, a, h->stream);
   return cuda_status(e);
 }
 
@@ -766,15 +792,15 @@ int es_dg_geometry(es_dg_t* h, double* x, double* J, double* Ja, int on_device) 
 int es_dg_launch(es_dg_t* h, int which, int stage, double dt) {
   if (!h || stage < 0 || stage > 4) return ES_DG_EINVAL;
   if (!traces_ready(h)) return ES_DG_EINVAL;
-  if (h->bg_pending) {
+  // the faces that need no trace may run before the traces arrive; everything
+  // else first completes a pending background (which reads them)
+  if (h->bg_pending && which != 3) {
     const int st = resolve_background(h);
     if (st) return st;
   }
-  if (which == 0)
-    return cuda_status(esdg_launch_face(h->g, h->P, h->mixed, h->q, h->fgeo, h->fflux, h->stream,
-                                        (h->mixed && h->has_bg) ? h->bg : nullptr, traces_of(h),
-                                        (h->mixed && h->has_bg && h->bg_moving) ? h->bgq
-                                                                                : nullptr));
+  if (which == 0) return launch_faces(h, h->q, FACES_ALL);
+  if (which == 3) return launch_faces(h, h->q, FACES_INTERIOR);
+  if (which == 4) return launch_faces(h, h->q, FACES_CUT);
   if (which == 1) {
     int st = ensure_rhs_buffers(h);
     if (st) return st;
@@ -987,18 +1013,20 @@ int issue_partition_step(es_dg_t* const* parts, int P, const std::vector<int>& l
     }
     for (int p = 0; p < P; p++) {
       es_dg_t* h = parts[p];
+      // one face launch once the traces are in: on one GPU the copies are short,
+      // and splitting off the faces that need no trace (as a process per slab
+      // does, es_dg_launch 3 and 4) costs more launches than it overlaps
       if (lo_of[p] >= 0 && lo_of[p] != p &&
           cudaStreamWaitEvent(h->stream, parts[lo_of[p]]->ev_sent, 0) != cudaSuccess)
         return ES_DG_ECUDA;
-      const bool moving = h->mixed && h->has_bg && h->bg_moving;
+      int st = ES_DG_OK;
       if (h->bg_pending) {
-        const int st = resolve_background(h);
+        st = resolve_background(h);
         if (st) return st;
       }
-      cudaError_t e = esdg_launch_face(h->g, h->P, h->mixed, h->q, h->fgeo, h->fflux, h->stream,
-                                       (h->mixed && h->has_bg) ? h->bg : nullptr, traces_of(h),
-                                       moving ? h->bgq : nullptr);
-      if (e == cudaSuccess) e = cudaEventRecord(h->ev_faced, h->stream);
+      st = launch_faces(h, h->q, FACES_ALL);
+      if (st) return st;
+      cudaError_t e = cudaEventRecord(h->ev_faced, h->stream);
       if (e != cudaSuccess) return cuda_status(e);
       EsdgVolArgs a = vol_args(h, h->q, nullptr);
       a.rkA = kRkA[s];

@@ -298,12 +298,13 @@ cudaError_t esdg_launch_channel(const EsdgGrid& g, const EsdgPhys& P, const doub
                                 double amp, cudaStream_t s);
 cudaError_t esdg_launch_background(const EsdgGrid& g, const EsdgPhys& P, const double* vgeo,
                                    const double* q, double* bg, double* q0, cudaStream_t s);
-// bgq: a moving background's state [E][5][np] (mixed with bg only; null at rest)
+// bgq: a moving background's state [E][5][np] (mixed with bg only; null at rest).
+// Faces f0 .. f1 - 1 only (global face ids; f1 < 0: to the last face).
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
                              const double* fgeo, void* fflux, cudaStream_t s,
                              const double* bg = nullptr,
                              EsdgTraces tr = EsdgTraces{nullptr, nullptr, 5, 0},
-                             const double* bgq = nullptr);
+                             const double* bgq = nullptr, long long f0 = 0, long long f1 = -1);
 // Pack a partition's own traces for its neighbours: the state of the first
 // element layer's i = 0 nodes into send_lo (if remote[0]) and of the last
 // layer's i = N nodes into send_hi (if remote[1]), layout of EsdgTraces.

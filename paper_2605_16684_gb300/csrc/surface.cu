@@ -613,9 +613,12 @@ __global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const doub
                                               const double* __restrict__ fgeo,
                                               R* __restrict__ fflux,
                                               const double* __restrict__ bg, EsdgTraces tr,
-                                              const double* __restrict__ bgq) {
-  face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, bgq, tr.lo, tr.hi, tr.nv, tr.bgmode,
-                      (long long)blockIdx.x * blockDim.x + threadIdx.x);
+                                              const double* __restrict__ bgq, long long t0,
+                                              long long t1) {
+  // face nodes t0 .. t1 - 1 (global face-node indices)
+  const long long tid = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= t1) return;
+  face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, bgq, tr.lo, tr.hi, tr.nv, tr.bgmode, tid);
 }
 
 // A partition's traces: one thread per (side, face of the plane, face node);
@@ -671,18 +674,21 @@ __global__ void __launch_bounds__(256) k_face_batch(const EsdgMember* __restrict
 template <typename R, int BG>
 cudaError_t launch_face_t(const EsdgGrid& g, const EsdgPhys& P, const double* q, const double* fgeo,
                           R* fflux, const double* bg, EsdgTraces tr, cudaStream_t s,
-                          const double* bgq = nullptr) {
-  const long long nt = g.nfaces * g.Nq * g.Nq;
-  if (nt == 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((nt + 255) / 256);
+                          const double* bgq, long long f0, long long f1) {
+  const long long nf2 = (long long)g.Nq * g.Nq;
+  if (f1 < 0 || f1 > g.nfaces) f1 = g.nfaces;
+  if (f0 < 0) f0 = 0;
+  if (f1 <= f0) return cudaSuccess;
+  const long long t0 = f0 * nf2, t1 = f1 * nf2;
+  const unsigned blocks = (unsigned)((t1 - t0 + 255) / 256);
   switch (g.N) {
-    case 1: k_face<R, 1, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
-    case 2: k_face<R, 2, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
-    case 3: k_face<R, 3, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
-    case 4: k_face<R, 4, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
-    case 5: k_face<R, 5, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
-    case 6: k_face<R, 6, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
-    case 7: k_face<R, 7, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq); break;
+    case 1: k_face<R, 1, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq, t0, t1); break;
+    case 2: k_face<R, 2, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq, t0, t1); break;
+    case 3: k_face<R, 3, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq, t0, t1); break;
+    case 4: k_face<R, 4, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq, t0, t1); break;
+    case 5: k_face<R, 5, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq, t0, t1); break;
+    case 6: k_face<R, 6, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq, t0, t1); break;
+    case 7: k_face<R, 7, BG><<<blocks, 256, 0, s>>>(g, P, q, fgeo, fflux, bg, tr, bgq, t0, t1); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -708,12 +714,14 @@ cudaError_t esdg_launch_face_batch(int N, int mixed, int bg, const EsdgMember* m
 
 cudaError_t esdg_launch_face(const EsdgGrid& g, const EsdgPhys& P, int mixed, const double* q,
                              const double* fgeo, void* fflux, cudaStream_t s, const double* bg,
-                             EsdgTraces tr, const double* bgq) {
+                             EsdgTraces tr, const double* bgq, long long f0, long long f1) {
   if (mixed && bg && bgq)
-    return launch_face_t<float, 2>(g, P, q, fgeo, (float*)fflux, bg, tr, s, bgq);
-  if (mixed && bg) return launch_face_t<float, 1>(g, P, q, fgeo, (float*)fflux, bg, tr, s);
-  if (mixed) return launch_face_t<float, 0>(g, P, q, fgeo, (float*)fflux, nullptr, tr, s);
-  return launch_face_t<double, 0>(g, P, q, fgeo, (double*)fflux, nullptr, tr, s);
+    return launch_face_t<float, 2>(g, P, q, fgeo, (float*)fflux, bg, tr, s, bgq, f0, f1);
+  if (mixed && bg)
+    return launch_face_t<float, 1>(g, P, q, fgeo, (float*)fflux, bg, tr, s, nullptr, f0, f1);
+  if (mixed)
+    return launch_face_t<float, 0>(g, P, q, fgeo, (float*)fflux, nullptr, tr, s, nullptr, f0, f1);
+  return launch_face_t<double, 0>(g, P, q, fgeo, (double*)fflux, nullptr, tr, s, nullptr, f0, f1);
 }
 
 cudaError_t esdg_launch_trace_pack(const EsdgGrid& g, const double* q, const double* bg, int nv,

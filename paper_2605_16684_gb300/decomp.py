@@ -7,9 +7,11 @@ trace received from the neighbouring slab.  All slabs on one GPU are stepped by
 the library itself (`_lib.PartitionedSolver`, device-to-device copies).  Across
 processes, `DistributedSlab` runs one slab per rank and moves the traces with
 torch.distributed point-to-point messages (NCCL between GPUs, gloo on CPU) before
-every stage: pack (kernel), exchange, interface kernel, volume kernel with the
-RK update.  The exchange is the only communication; there is no collective on
-the data path.
+every stage: pack (kernel), exchange posted, the interface kernel on the faces
+that need no trace while the messages are in flight (Section 4.3's overlap), the
+faces of the cut planes once they have landed, volume kernel with the RK
+update.  The exchange is the only communication; there is no collective on the
+data path.
 """
 from __future__ import annotations
 
@@ -50,6 +52,21 @@ def exchange(send_lo, send_hi, recv_lo, recv_hi, rank: int, world: int, periodic
     its low neighbour.  directions="up" moves only the high-to-low-plane half (the
     face geometry hand-over).  Tensors of a plane without a neighbour may be None.
     Blocks until every message of this rank has completed."""
+    exchange_finish(exchange_start(send_lo, send_hi, recv_lo, recv_hi, rank, world, periodic,
+                                   group, directions))
+
+
+def exchange_finish(works) -> None:
+    """Wait for the messages posted by exchange_start."""
+    for w in works:
+        w.wait()
+
+
+def exchange_start(send_lo, send_hi, recv_lo, recv_hi, rank: int, world: int, periodic: bool,
+                   group=None, directions: str = "both") -> list:
+    """Post one stage's trace messages (as exchange) and return their handles
+    without waiting: work that needs no trace can run while they are in flight
+    (Section 4.3), and exchange_finish waits for them."""
     import torch.distributed as dist
     lo, hi = neighbours(rank, world, periodic)
     ops = []
@@ -63,9 +80,7 @@ def exchange(send_lo, send_hi, recv_lo, recv_hi, rank: int, world: int, periodic
         ops.append(dist.P2POp(dist.irecv, recv_lo, lo, group, TAG_TO_LO_PLANE))
     if hi is not None and directions == "both":
         ops.append(dist.P2POp(dist.irecv, recv_hi, hi, group, TAG_TO_HI_PLANE))
-    if ops:
-        for w in dist.batch_isend_irecv(ops):
-            w.wait()
+    return dist.batch_isend_irecv(ops) if ops else []
 
 
 class DistributedSlab:
@@ -91,10 +106,18 @@ class DistributedSlab:
         self.s.set_traces(*self.t)
 
     def _exchange(self, directions="both"):
+        self._exchange_finish(self._exchange_start(directions))
+
+    def _exchange_start(self, directions="both"):
         import torch
-        torch.cuda.current_stream().wait_stream(self.s.stream)
-        exchange(*self.t, self.rank, self.world, self.periodic_x, self.group, directions)
-        self.s.stream.wait_stream(torch.cuda.current_stream())
+        torch.cuda.current_stream().wait_stream(self.s.stream)  # the traces are packed
+        return exchange_start(*self.t, self.rank, self.world, self.periodic_x, self.group,
+                              directions)
+
+    def _exchange_finish(self, works):
+        import torch
+        exchange_finish(works)
+        self.s.stream.wait_stream(torch.cuda.current_stream())  # the traces have landed
 
     def connect(self):
         """Hand the high planes' face geometry to the high neighbours (once)."""
@@ -104,9 +127,13 @@ class DistributedSlab:
         self.s.sync()
 
     def step(self, dt: float, nsteps: int = 1):
+        """LSRK steps with Section 4.3's overlap: the faces that need no trace run
+        while the stage's traces are in flight, those of the cut planes after."""
         for _ in range(nsteps):
             for stage in range(5):
                 self.s.pack_traces()
-                self._exchange()
-                self.s.launch(0, stage, dt)  # interface fluxes with the received traces
+                works = self._exchange_start()
+                self.s.launch(3, stage, dt)  # interface fluxes that need no trace
+                self._exchange_finish(works)
+                self.s.launch(4, stage, dt)  # those of the cut planes, with the traces
                 self.s.launch(2, stage, dt)  # volume, lifts, source and the RK update

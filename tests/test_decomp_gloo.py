@@ -54,9 +54,17 @@ def _rank(rank, world, port, periodic, directions, out):
         send_hi = _trace(rank, "hi") if hi is not None else None
         recv_lo = torch.full((37,), -1.0, dtype=torch.float64) if lo is not None else None
         recv_hi = torch.full((37,), -1.0, dtype=torch.float64) if hi is not None else None
-        for _ in range(3):  # several stages in a row
-            decomp.exchange(send_lo, send_hi, recv_lo, recv_hi, rank, world, periodic,
-                            directions=directions)
+        for k in range(3):  # several stages in a row
+            if k == 1:
+                # posted, other work while in flight, then waited for (Section 4.3)
+                works = decomp.exchange_start(send_lo, send_hi, recv_lo, recv_hi, rank, world,
+                                              periodic, directions=directions)
+                busy = torch.arange(1000, dtype=torch.float64).sum()
+                decomp.exchange_finish(works)
+                assert float(busy) == 499500.0
+            else:
+                decomp.exchange(send_lo, send_hi, recv_lo, recv_hi, rank, world, periodic,
+                                directions=directions)
         out[rank] = (None if recv_lo is None else recv_lo.tolist(),
                      None if recv_hi is None else recv_hi.tolist())
         dist.barrier()

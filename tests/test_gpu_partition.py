@@ -146,6 +146,28 @@ def test_slab_step_graph_follows_dt_and_reconfiguration(lib, precision):
     assert np.array_equal(split.get_state(), whole.get_state())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_split_face_launches_equal_the_stage(lib, precision):
+    # the transport-agnostic sequence a process-per-slab caller runs (pack and
+    # exchange, the faces that need no trace, the cut planes' faces, the volume
+    # kernel with the stage update) equals the library's partitioned steps bitwise
+    K, N, parts, periodic, warp = CASES[1]
+    _, a, _ = pair(lib, K, N, parts, periodic, warp, precision=precision)
+    _, b, _ = pair(lib, K, N, parts, periodic, warp, precision=precision)
+    for s in (a, b):
+        s.init_bubble(amp=0.8)
+    dt = a.cfl_dt(0.5)
+    a.step(dt, 2)
+    for _ in range(2):
+        for stage in range(5):
+            b.exchange()
+            for s in b.parts:
+                s.launch(3, stage, dt)
+                s.launch(4, stage, dt)
+                s.launch(2, stage, dt)
+    assert np.array_equal(a.get_state(), b.get_state())
+
+
 def test_slab_calls_need_traces(lib):
     m = dict(CUBE, periodic=(1, 1, 0))
     s = lib.Solver(4, 2, 2, 3, part=(1, 3), **m)
