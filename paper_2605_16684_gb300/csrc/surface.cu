@@ -608,6 +608,33 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
   for (int v = 0; v < 5; v++) out[v * NF2 + fn] = sc * F[v];
 }
 
+// Face of work item w when a launch covers every face: layer by layer in z
+// (element layer k: its x faces, its y faces, then the z plane below it; the
+// z planes past the last layer at the end), so that the few megabytes of
+// state a layer's faces read stay in L2 for all three directions instead of
+// streaming the whole state through L2 once per direction (the face ids,
+// and with them the flux layout, are unchanged).
+__device__ __forceinline__ long long face_layered(const EsdgGrid& g, long long w) {
+  const long long K0 = g.K[0], K1 = g.K[1], K2 = g.K[2];
+  const long long nx = (long long)g.nplanes[0] * K1, ny = (long long)g.nplanes[1] * K0;
+  const long long L = nx + ny + K0 * K1;
+  if (w >= K2 * L) return g.face_off[2] + K2 * K1 * K0 + (w - K2 * L);
+  const long long k = w / L;
+  long long r = w - k * L;
+  if (r < nx) {
+    const long long P = r / K1;
+    return g.face_off[0] + (P * K2 + k) * K1 + (r - P * K1);
+  }
+  r -= nx;
+  if (r < ny) {
+    const long long P = r / K0;
+    return g.face_off[1] + (P * K2 + k) * K0 + (r - P * K0);
+  }
+  r -= ny;
+  const long long b = r / K0;
+  return g.face_off[2] + (k * K1 + b) * K0 + (r - b * K0);
+}
+
 template <typename R, int N, int BG>
 __global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const double* __restrict__ q,
                                               const double* __restrict__ fgeo,
@@ -615,9 +642,15 @@ __global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const doub
                                               const double* __restrict__ bg, EsdgTraces tr,
                                               const double* __restrict__ bgq, long long t0,
                                               long long t1) {
-  // face nodes t0 .. t1 - 1 (global face-node indices)
-  const long long tid = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // face nodes t0 .. t1 - 1 (global face-node indices); a launch over every
+  // face takes them in the layered order
+  constexpr long long NF2 = (N + 1) * (N + 1);
+  long long tid = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= t1) return;
+  if (t0 == 0 && t1 == g.nfaces * NF2) {
+    const long long w = tid / NF2;
+    tid = face_layered(g, w) * NF2 + (tid - w * NF2);
+  }
   face_node<R, N, BG>(g, P, q, fgeo, fflux, bg, bgq, tr.lo, tr.hi, tr.nv, tr.bgmode, tid);
 }
 
