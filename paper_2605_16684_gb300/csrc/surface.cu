@@ -698,8 +698,15 @@ __global__ void __launch_bounds__(256) k_face_batch(const EsdgMember* __restrict
         dst[k] = src[k];
     }
     __syncthreads();
+    // the member's faces in the layered order (a table covers all of them)
+    constexpr long long NF2 = (N + 1) * (N + 1);
+    long long tid = (long long)tile.y + threadIdx.x;
+    if (tid < mb.g.nfaces * NF2) {
+      const long long w = tid / NF2;
+      tid = face_layered(mb.g, w) * NF2 + (tid - w * NF2);
+    }
     face_node<R, N, BG>(mb.g, mb.P, mb.a.q_in, mb.fgeo, (R*)mb.a.fflux, mb.bg, nullptr,
-                        nullptr, nullptr, 5, 0, (long long)tile.y + threadIdx.x);
+                        nullptr, nullptr, 5, 0, tid);
     __syncthreads();
   }
 }
