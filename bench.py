@@ -62,6 +62,14 @@ KERNEL_FLOPS_PER_NODE = 45
 # (2 x 40 B), face geometry (40 B) and the flux write (40 B); RK state traffic
 # is fused into the volume kernel.
 FACE_BYTES_PER_NODE = {"fp64": 160, "mixed": 140}
+# Algorithmic bytes of the mixed volume kernel per node: FP64 state in and out
+# (2 x 40 B), FP32 increment in and out (2 x 20 B), FP32 geometry (11 x 4 B), the
+# background (3 FP64 + 4 FP32 values) and its FP32 momentum rhs (3 x 4 B), and
+# the FP32 face fluxes of the element's six faces (6 x 5 x 4 B per face node,
+# i.e. 6 N_q^2 / N_q^3 of them per node).
+def mixed_volume_bytes_per_node(N):
+    nq = N + 1
+    return 2 * 40 + 2 * 20 + 11 * 4 + (3 * 8 + 4 * 4) + 3 * 4 + 6 * 5 * 4 * nq * nq / nq ** 3
 
 # DRAM traffic of one FP64 volume launch (k_volume_pipe64<4, 1, 0>): ncu capture of the same
 # kernel on the 24^3 case (dram__bytes_read.sum + dram__bytes_write.sum = 332.80 MB +
@@ -90,6 +98,19 @@ def device_peaks(device=0):
     hz = mhz * 1e6
     return {"sms": sms, "sm_max_mhz": mhz, "clock_source": src,
             "fp64": sms * hz * DFMA_PER_CLK_SM * 2, "fp32": sms * hz * FFMA_PER_CLK_SM * 2}
+
+
+def hbm_block(r64, r32, N, hbm_gbs):
+    """Achieved HBM bandwidth of the memory-side kernels from their algorithmic bytes
+    (the interface kernels per face node, the mixed volume kernel per node) over their
+    CUDA-event durations, against the measured copy bandwidth."""
+    def entry(nbytes, ms):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"gbs": gbs, "frac": gbs / hbm_gbs, "bytes": nbytes, "ms": ms}
+    return {"peak_gbs": hbm_gbs, "unit": "GB/s (algorithmic bytes / event time)",
+            "interface_fp64": entry(r64["face_nodes"] * FACE_BYTES_PER_NODE["fp64"], r64["t_face"]),
+            "interface_mixed": entry(r32["face_nodes"] * FACE_BYTES_PER_NODE["mixed"], r32["t_face"]),
+            "volume_mixed": entry(r32["ndof"] * mixed_volume_bytes_per_node(N), r32["t_vol"])}
 
 
 def measured_peaks():
@@ -248,7 +269,8 @@ def run_gpu_arm(args, rank, world, dist):
         ndof = info.ndof
         results[prec] = dict(ms=ms, t_face=t_face, t_vol=t_vol, ndof=ndof, dt=dt,
                              e2e_s=te, e2e_steps=e2e_steps, clocks=clocks, finite=finite,
-                             state_bytes=ndof * 5 * 8, E=info.nelem)
+                             state_bytes=ndof * 5 * 8, E=info.nelem,
+                             face_nodes=info.nfaces * info.Nq * info.Nq)
         s.close()
         del qh
     return results
@@ -344,6 +366,7 @@ def main_ours(args):
                      / (r64["t_vol"] * 1e-3) / FP64_PEAK},
         "kernels_ms_per_stage": {"fp64": {"interface": r64["t_face"], "volume_rk": r64["t_vol"]},
                                  "mixed": {"interface": r32["t_face"], "volume_rk": r32["t_vol"]}},
+        "hbm": hbm_block(r64, r32, w["N"], float(peaks.get("hbm_gbs", 6800.0))),
         "mixed": {"value": value32, "unit": UNIT, "dtype": "f32 pairs, f64 state",
                   "ms_per_step": r32["ms"] / args.steps,
                   "volume_fp32_tflops": vflops / (r32["t_vol"] * 1e-3) / 1e12,
