@@ -635,11 +635,18 @@ __global__ void __launch_bounds__(PipeShape<N, true>::THREADS, PipeCfg<N, true>:
         return prims32bg(x.q0, x.q1, x.q2, x.q3, x.q4, x.phi, x.phh, gm1f, x.rb, x.eb, x.b0, x.b1,
                          x.b2, x.b3);
       };
+      // two nodes per thread and round; a warp whose second slots all lie
+      // past the tile (warp-uniform test on its first lane) converts one
       for (int i0 = tid; i0 < NN; i0 += 2 * T) {
-        const In x0 = load(i0), x1 = load(i0 + T);
-        const Prim32 o0 = prim(x0), o1 = prim(x1);
-        store(x0, o0);
-        store(x1, o1);
+        if (i0 - (tid & 31) + T < NN) {
+          const In x0 = load(i0), x1 = load(i0 + T);
+          const Prim32 o0 = prim(x0), o1 = prim(x1);
+          store(x0, o0);
+          store(x1, o1);
+        } else {
+          const In x0 = load(i0);
+          store(x0, prim(x0));
+        }
       }
     }
     __syncthreads();  // RAW consumed

@@ -59,10 +59,17 @@ struct WsCfg {
   static constexpr bool ON = false;
   static constexpr int EPB = 1, PW = 1;
 };
+#ifndef ESDG_WS4_EPB
+#define ESDG_WS4_EPB 4
+#endif
+#ifndef ESDG_WS4_PW
+#define ESDG_WS4_PW 5
+#endif
 template <>
 struct WsCfg<4> {
   static constexpr bool ON = true;
-  static constexpr int EPB = 4, PW = 5;  // 300 pencils in 10 warps, 5 producer warps, 1 copy warp
+  // 300 pencils in 10 warps, 5 producer warps, 1 copy warp
+  static constexpr int EPB = ESDG_WS4_EPB, PW = ESDG_WS4_PW;
 };
 
 template <int N, int MODE>
@@ -291,11 +298,18 @@ __global__ void __launch_bounds__(Ws32<N, MODE>::T, 1)
           return prims32bg(x.q0, x.q1, x.q2, x.q3, x.q4, x.phi, x.phh, gm1f, x.rb, x.eb, x.b0,
                            x.b1, x.b2, x.b3);
         };
+        // two nodes per thread and round; a warp whose second slots all lie
+        // past the tile (warp-uniform test on its first lane) converts one
         for (int i0 = p; i0 < NN; i0 += 2 * PT) {
-          const In x0 = load(i0), x1 = load(i0 + PT);
-          const Prim32 o0 = prim(x0), o1 = prim(x1);
-          store(x0, o0);
-          store(x1, o1);
+          if (i0 - (p & 31) + PT < NN) {
+            const In x0 = load(i0), x1 = load(i0 + PT);
+            const Prim32 o0 = prim(x0), o1 = prim(x1);
+            store(x0, o0);
+            store(x1, o1);
+          } else {
+            const In x0 = load(i0);
+            store(x0, prim(x0));
+          }
         }
         ws_bar(PBAR, PT);  // node fields written; RAW consumed
         if (p == 0) ws_arrive(&c.rawfree);
