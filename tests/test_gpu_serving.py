@@ -110,6 +110,22 @@ def test_every_batched_variant_equals_single_handle(lib, monkeypatch, variant):
     srv.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_equals_single_handle_several_tiles_per_cta(lib, precision):
+    # 15 x 16 x 13 elements at N = 4: the single-mesh kernels (the warp-specialised
+    # mixed kernel, the pipelined FP64 kernel) walk several tiles per CTA through their
+    # double-buffered hand-overs, with a partial last round; the batched kernels walk
+    # the work table.  Bitwise the same state.
+    r = dict(K=(15, 16, 13), N=4, precision=precision, nsteps=2, warp=0.05, amp=0.8)
+    srv = lib.Server()
+    res = srv.wait(srv.submit(**r))
+    srv.close()
+    assert res["status"] == 0
+    q_ref, dt = single_handle(lib, r)
+    assert res["dt"] == dt
+    assert np.array_equal(res["q"], q_ref), np.abs(res["q"] - q_ref).max()
+
+
 def test_twin_meshes_share_geometry_exactly(lib):
     # members with the same mesh and order copy the first one's geometry at
     # admission; every result still equals its own single-handle solve bit for bit
