@@ -395,14 +395,17 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
   const int so1 = (d == 0) ? K0 : 1, so2 = (d == 2) ? K0 : K0 * K1;
   const int nd = (d == 0) ? 1 : ((d == 1) ? Nq : NF2);
   const int no1 = (d == 0) ? Nq : 1, no2 = (d == 2) ? Nq : NF2;
-  long long r = f - g.face_off[d];
-  const int a = (int)(r % Ko1);
-  r /= Ko1;
-  const int b = (int)(r % Ko2);
-  const int Pl = (int)(r / Ko2);
+  // the face within its direction as (a, b, plane); 32-bit unsigned divisions
+  // (fewer than 2^32 faces)
+  const unsigned r = (unsigned)(f - g.face_off[d]);
+  const unsigned r1 = r / (unsigned)Ko1;
+  const int a = (int)(r - r1 * (unsigned)Ko1);
+  const unsigned r2 = r1 / (unsigned)Ko2;
+  const int b = (int)(r1 - r2 * (unsigned)Ko2);
+  const int Pl = (int)r2;
   // elements below and above the plane (-1 at a wall or a partition's cut)
   const int et = a * so1 + b * so2;
-  const int em = (Pl > 0 || per) ? et + ((Pl - 1 + Kd) % Kd) * sd : -1;
+  const int em = (Pl > 0 || per) ? et + (Pl > 0 ? Pl - 1 : Kd - 1) * sd : -1;
   const int ep = (Pl < Kd) ? et + Pl * sd : -1;
   const int nt = (fn % Nq) * no1 + (fn / Nq) * no2;
   const int nm = nt + N * nd, npn = nt;
@@ -614,29 +617,35 @@ __device__ __forceinline__ void face_node(const EsdgGrid& g, const EsdgPhys& P,
 // state a layer's faces read stay in L2 for all three directions instead of
 // streaming the whole state through L2 once per direction (the face ids,
 // and with them the flux layout, are unchanged).
-__device__ __forceinline__ long long face_layered(const EsdgGrid& g, long long w) {
-  const long long K0 = g.K[0], K1 = g.K[1], K2 = g.K[2];
-  const long long nx = (long long)g.nplanes[0] * K1, ny = (long long)g.nplanes[1] * K0;
-  const long long L = nx + ny + K0 * K1;
-  if (w >= K2 * L) return g.face_off[2] + K2 * K1 * K0 + (w - K2 * L);
-  const long long k = w / L;
-  long long r = w - k * L;
+// Face indices fit in 32 bits (es_dg_create admits at most 2^30 elements, so
+// fewer than 2^32 faces): the divisions by runtime extents are 32-bit unsigned
+// ones, several times cheaper than 64-bit divisions on an issue-bound kernel.
+__device__ __forceinline__ long long face_layered(const EsdgGrid& g, long long w64) {
+  const unsigned w = (unsigned)w64;
+  const unsigned K0 = g.K[0], K1 = g.K[1], K2 = g.K[2];
+  const unsigned nx = (unsigned)g.nplanes[0] * K1, ny = (unsigned)g.nplanes[1] * K0;
+  const unsigned L = nx + ny + K0 * K1;
+  if (w >= K2 * L) return g.face_off[2] + (long long)K2 * K1 * K0 + (w - K2 * L);
+  const unsigned k = w / L;
+  unsigned r = w - k * L;
   if (r < nx) {
-    const long long P = r / K1;
-    return g.face_off[0] + (P * K2 + k) * K1 + (r - P * K1);
+    const unsigned P = r / K1;
+    return g.face_off[0] + ((long long)P * K2 + k) * K1 + (r - P * K1);
   }
   r -= nx;
   if (r < ny) {
-    const long long P = r / K0;
-    return g.face_off[1] + (P * K2 + k) * K0 + (r - P * K0);
+    const unsigned P = r / K0;
+    return g.face_off[1] + ((long long)P * K2 + k) * K0 + (r - P * K0);
   }
   r -= ny;
-  const long long b = r / K0;
-  return g.face_off[2] + (k * K1 + b) * K0 + (r - b * K0);
+  const unsigned b = r / K0;
+  return g.face_off[2] + ((long long)k * K1 + b) * K0 + (r - b * K0);
 }
 
+// mixed: at most 64 registers, four 256-thread CTAs per SM
 template <typename R, int N, int BG>
-__global__ void __launch_bounds__(256) k_face(EsdgGrid g, EsdgPhys P, const double* __restrict__ q,
+__global__ void __launch_bounds__(256, sizeof(R) == sizeof(float) ? 4 : 1)
+    k_face(EsdgGrid g, EsdgPhys P, const double* __restrict__ q,
                                               const double* __restrict__ fgeo,
                                               R* __restrict__ fflux,
                                               const double* __restrict__ bg, EsdgTraces tr,
