@@ -95,7 +95,8 @@ typedef struct {
 /* Create a solver on the current CUDA device.  `cuda_stream` is a cudaStream_t
  * (NULL = the legacy default stream).  Builds node coordinates, curl-form
  * metric terms (Kopriva), face normals and the LGL operators on the device.
- * N in 1..7.  On error *out is NULL. */
+ * N in 1..7; at most 2^30 elements (so face indices fit in 32 bits) and a
+ * warp amplitude in [0, 0.15), else ES_DG_EINVAL.  On error *out is NULL. */
 int es_dg_create(const es_dg_mesh* mesh, int N, es_dg_precision precision,
                  const es_dg_physics* physics, const es_dg_allocator* allocator,
                  void* cuda_stream, es_dg_t** out);
