@@ -47,7 +47,9 @@ def test_strerror(lib):
     assert lib.es_dg_strerror(12345) == b"unknown status"
 
 
-@pytest.mark.parametrize("kx,N,warp", [(0, 3, 0.0), (2, 0, 0.0), (2, 8, 0.0), (2, 3, 0.5)])
+# (1 << 28) + 1 elements along x (times 2 x 2): more than the 2^30 elements a handle admits
+@pytest.mark.parametrize("kx,N,warp", [(0, 3, 0.0), (2, 0, 0.0), (2, 8, 0.0), (2, 3, 0.5),
+                                       ((1 << 28) + 1, 3, 0.0)])
 def test_create_rejects_bad_arguments_before_touching_cuda(lib, kx, N, warp):
     m = _lib.es_dg_mesh(kx, 2, 2, (C.c_double * 3)(0, 0, 0), (C.c_double * 3)(1, 1, 1),
                         (C.c_int * 3)(1, 1, 0), warp)
