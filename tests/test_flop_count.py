@@ -41,3 +41,20 @@ def test_count_structure():
     # per node: primitives, then for each of the five values its volume value
     # (one division) and its stage update
     assert c["node"] == c["primitives"] + 5 * (1 + c["stage_update"])
+
+
+def test_memory_side_byte_counts():
+    # the algorithmic bytes behind the bench's achieved-bandwidth figures: the mixed
+    # volume kernel moves 240 B per node at N = 4 (29.3 KB per element: FP64 state in
+    # and out, FP32 increment in and out, 11 FP32 geometry values, the background's
+    # 3 FP64 + 4 FP32 values and 3 FP32 momentum right-hand-side values, and the FP32
+    # fluxes of the element's six faces); a face node costs two 5-value traces, its
+    # geometry and the flux write (FP64 160 B, mixed 140 B with an FP32 flux)
+    b = bench_module()
+    assert b.mixed_volume_bytes_per_node(4) == pytest.approx(240.0)
+    assert b.mixed_volume_bytes_per_node(4) * 125 == pytest.approx(30000.0)
+    assert b.FACE_BYTES_PER_NODE == {"fp64": 160, "mixed": 140}
+    # pairs of the half sweep: N_q^2 pencils per direction, N_q (N_q - 1) / 2 pairs each
+    for N in range(1, 8):
+        nq = N + 1
+        assert b.pairs_per_element(N) == 3 * nq * nq * nq * (nq - 1) // 2
